@@ -1,0 +1,223 @@
+/*
+ * dses.h - C ABI of the B300 (sm_103a) implementation of Direct Semi-Exhaustive
+ * Search (DSES) for partial-to-full point-cloud registration, arXiv 2502.00115.
+ *
+ * The method (Section IV-B, Algorithm 2): for every rotation R of a rotation
+ * grid, the translation that maximises inliers is the mode of the rotated
+ * pairwise differences y_j - R x_i on a delta_t lattice (Lemma 1, Eq. 5); the
+ * inlier count M of Eq. 3 is taken at that translation; candidates whose M is
+ * at least q times the best M* are scored under a robust distance metric (the
+ * norm p of Eq. 1: Sum_i rho(min_j ||y_j - R x_i - t||)); the lowest-cost
+ * candidate is returned.
+ *
+ * Conventions shared by every entry point:
+ *  - Points are FP32, xyz interleaved, row-major (n x 3). A pointer is a host
+ *    pointer unless the call's "is_device" flag says it is a device pointer of
+ *    the context's device; device pointers are read in the order of the
+ *    context's stream.
+ *  - The caller owns every buffer it passes; no call keeps a caller pointer
+ *    after it returns (dses_submit copies the source cloud before returning).
+ *  - Targets belong to the library from dses_create_target until
+ *    dses_destroy_target.
+ *  - No C++ exception crosses this boundary. Every call returns a dses_status;
+ *    dses_last_error(ctx) gives a one-line description of the last failure on
+ *    that context (overwritten by the next failure).
+ *  - A context serialises its calls with a mutex; dses_poll may be called from
+ *    any thread.
+ *  - A CUDA error inside a call is reported as DSES_ERR_CUDA; after a sticky
+ *    CUDA error the context must be destroyed and recreated.
+ */
+#ifndef DSES_H_
+#define DSES_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dses_ctx dses_ctx;
+typedef struct dses_target dses_target;
+
+typedef enum {
+  DSES_OK = 0,
+  DSES_NOT_READY = 1,            /* dses_poll: the request is still running */
+  DSES_ERR_INVALID_ARG = -1,     /* bad pointer, size, parameter or handle */
+  DSES_ERR_OOM = -2,             /* device or pinned-host allocation failed */
+  DSES_ERR_CUDA = -3,            /* a CUDA runtime call failed */
+  DSES_ERR_QUEUE_FULL = -4,      /* dses_submit: the request queue is at capacity */
+  DSES_ERR_TIMEOUT = -5,         /* a bounded wait ran out */
+  DSES_ERR_NO_CANDIDATE = -6,    /* no point pair voted inside the translation box */
+  DSES_ERR_UNKNOWN_TICKET = -7   /* dses_poll: ticket never issued or already collected */
+} dses_status;
+
+/* Robust per-point error rho(d) on the nearest-target distance d (the norm p of
+ * Eq. 1 and the ERROR of Algorithm 2; Section IV-B names the truncated L1):
+ *   INLIER    rho = [d >= epsilon]           (cost = N - M, the saturated L0 of Eq. 3)
+ *   TRUNC_L1  rho = min(d, tau)
+ *   TRUNC_L2  rho = min(d, tau)^2
+ *   HUBER     e = min(d, tau); rho = e^2/2 if e <= h else h (e - h/2)
+ *   LP        rho = d^p, p in (0, 1]                                        */
+typedef enum {
+  DSES_METRIC_INLIER = 0,
+  DSES_METRIC_TRUNC_L1 = 1,
+  DSES_METRIC_TRUNC_L2 = 2,
+  DSES_METRIC_HUBER = 3,
+  DSES_METRIC_LP = 4
+} dses_metric;
+
+typedef enum {
+  /* Dense SO(3) grid of 72 n^3 rotations: Hopf coordinates from the HEALPix
+   * RING pixel centres at N_side = n (theta, phi) and psi_k = 2 pi (k + 1/2)/(6n);
+   * quaternion (cos(t/2)cos(s/2), cos(t/2)sin(s/2), sin(t/2)cos(f+s/2),
+   * sin(t/2)sin(f+s/2)); index = pixel * 6n + k.                            */
+  DSES_GRID_HOPF = 0,
+  /* Euler box of Algorithm 2's rotation loops: R = R0 Rz(a) Ry(b) Rx(c), each
+   * angle in {-K, ..., K} * delta_r, index ((a (2K+1)) + b)(2K+1) + c.       */
+  DSES_GRID_EULER_BOX = 1,
+  /* Caller-supplied FP32 row-major 3x3 matrices (host memory, n_explicit x 9). */
+  DSES_GRID_EXPLICIT = 2
+} dses_grid_kind;
+
+typedef enum {
+  DSES_NN_GRID = 0,  /* trilinear lookup in the target's truncated distance grid */
+  DSES_NN_BRUTE = 1  /* exact brute-force nearest neighbour over all target points */
+} dses_nn_mode;
+
+typedef struct {
+  int32_t kind;             /* dses_grid_kind */
+  int32_t hopf_n;           /* HOPF: N_side >= 1 */
+  int32_t K;                /* EULER_BOX: half-size >= 0 */
+  double delta_r;           /* EULER_BOX: angular step, radians */
+  double R0[9];             /* EULER_BOX: centre rotation, row-major */
+  const float* explicit_R;  /* EXPLICIT: host pointer, n_explicit x 9 */
+  int64_t n_explicit;       /* EXPLICIT: number of rotations */
+} dses_rotation_grid;
+
+typedef struct {
+  int32_t metric;           /* dses_metric */
+  float epsilon;            /* inlier threshold of Eq. 3 (> 0) */
+  float delta_t;            /* lattice step of the translation mode; 0 => epsilon */
+  float tau;                /* truncation of TRUNC_L1/TRUNC_L2/HUBER; 0 => 2 epsilon */
+  float huber_h;            /* Huber knee; 0 => epsilon */
+  float p;                  /* LP exponent in (0, 1] */
+  float t_center[3];        /* translation search range [c - s, c + s] per axis ... */
+  float t_half[3];          /* ... (s > 0); the lattice points k delta_t inside it */
+  int32_t q_milli;          /* candidate filter 1000 M >= q_milli M*, 0..1000 (0: all) */
+  int32_t top_k;            /* > 0: candidates are the top_k by (M desc, index asc) */
+  int32_t nn_mode;          /* dses_nn_mode */
+  int32_t refine_top_k;     /* > 0: second pass on Euler boxes around this many best */
+  int32_t refine_K;         /* Euler box half-size of the second pass */
+  double refine_delta_r;    /* Euler box step of the second pass, radians */
+} dses_params;
+
+typedef struct {
+  float R[9];               /* best rotation, row-major: y ~ R x + t */
+  float t[3];               /* its translation t* = k* delta_t */
+  int64_t rot_index;        /* index in the grid; a second-pass rotation has index
+                               n_grid + c (2K+1)^3 + local, c = rank of its centre */
+  uint32_t inliers;         /* M at the best rotation (Eq. 3) */
+  uint32_t votes;           /* V: the mode's frequency at the best rotation */
+  float cost;               /* Sum_i rho(d_i) at the best pose */
+  int32_t status;           /* dses_status of this registration */
+} dses_result;
+
+typedef struct {
+  const dses_target* target; /* resident target (full model) Y */
+  const float* src;          /* source (partial observation) X, n_src x 3 */
+  int64_t n_src;             /* N >= 1 */
+  int32_t src_is_device;     /* 1: src is a device pointer */
+  dses_rotation_grid grid;
+  dses_params params;
+} dses_problem;
+
+/* Context on `device`. cuda_stream: a cudaStream_t to run on (NULL: the context
+ * creates its own non-blocking stream). Errors: INVALID_ARG (bad device or out
+ * NULL), CUDA. */
+dses_status dses_create(int device, void* cuda_stream, dses_ctx** out);
+
+/* Stops the serving worker, frees every target and buffer of the context. */
+dses_status dses_destroy(dses_ctx* ctx);
+
+/* Resident target (Section III's reference cloud Y, the full model): copies the
+ * m x 3 points to the device and builds its truncated distance grid of
+ * grid_res^3 FP32 voxels (grid_res in [8, 512]; 0 => 128), truncated at
+ * grid_cap (> 0; the TRUNC/HUBER metrics need grid_cap >= tau). Voxel size per
+ * axis h = (extent + 2 cap)/(grid_res - 2), origin min - cap - h; voxel centre
+ * values are min(cap, exact nearest-target distance). Errors: INVALID_ARG
+ * (m < 1, non-finite point, bad size), OOM, CUDA. */
+dses_status dses_create_target(dses_ctx* ctx, const float* xyz, int64_t m, int32_t ptr_is_device,
+                               float grid_cap, int32_t grid_res, dses_target** out);
+
+/* Frees a target. INVALID_ARG while a submitted request still uses it. */
+dses_status dses_destroy_target(dses_ctx* ctx, dses_target* target);
+
+/* One registration (Algorithm 2), blocking until the result is written to
+ * *out (host memory). Errors: INVALID_ARG, OOM, CUDA, NO_CANDIDATE (the result
+ * is still filled, with votes = 0). */
+dses_status dses_register(dses_ctx* ctx, const dses_problem* problem, dses_result* out);
+
+/* n registrations run as one persistent launch over a (problem, rotation-tile)
+ * work queue; out[i] (host) receives problem i's result. Each result equals the
+ * result of dses_register on the same problem. Returns the first non-OK
+ * per-problem status, or OK. */
+dses_status dses_register_batch(dses_ctx* ctx, const dses_problem* problems, int32_t n, dses_result* out);
+
+/* Asynchronous registration: copies the problem (and the source cloud) and
+ * queues it for the serving worker, which admits requests when device memory
+ * and batch slots free up and runs admitted requests together (continuous
+ * batching). *ticket identifies the request. Errors: INVALID_ARG, QUEUE_FULL. */
+dses_status dses_submit(dses_ctx* ctx, const dses_problem* problem, uint64_t* ticket);
+
+/* DSES_NOT_READY while the request runs; otherwise copies the result to *out,
+ * forgets the ticket and returns the registration's status. UNKNOWN_TICKET for
+ * a ticket never issued or already collected. */
+dses_status dses_poll(dses_ctx* ctx, uint64_t ticket, dses_result* out);
+
+/* Test hook: runs the registration and copies per-rotation intermediates to
+ * host arrays of length n_rot (grid size, plus the second pass if any): k_star
+ * (n_rot x 3, lattice index of t*), votes (V), inliers (M) and cost (NaN for a
+ * rotation that was not a candidate). Any output pointer may be NULL. out
+ * (optional) receives the result. */
+dses_status dses_debug_per_rotation(dses_ctx* ctx, const dses_problem* problem, int32_t* k_star,
+                                    uint32_t* votes, uint32_t* inliers, float* cost, dses_result* out);
+
+/* Builds a rotation grid on the device and copies it to out_R (host,
+ * capacity x 9 floats). *count receives the grid size; INVALID_ARG if it
+ * exceeds capacity (out_R may be NULL to query the size). */
+dses_status dses_rotation_grid_build(dses_ctx* ctx, const dses_rotation_grid* grid, float* out_R,
+                                     int64_t capacity, int64_t* count);
+
+/* Copies a target's distance grid (res^3 floats, index (a res + b) res + c)
+ * and its geometry to host memory. D may be NULL to query res. */
+dses_status dses_target_distance_grid(dses_ctx* ctx, const dses_target* target, float* D, float lo[3],
+                                      float h[3], int32_t* res, float* cap);
+
+/* Tuning and engine options (key = value). Keys:
+ *   "hist_mode"            0 auto, 1 force 32-bit counters, 2 force packed 16-bit
+ *   "hist_budget_bytes"    shared-memory bytes for the vote histogram (slabs below it)
+ *   "points_per_thread"    0 auto, or 1, 2, 4, 8 target points held per lane
+ *   "fuse_score"           1 (default) score inside the rotation pass when every
+ *                          rotation is a candidate; 0 always score in a second kernel
+ *   "tile_rotations"       rotations per work item of the persistent launch (0 auto)
+ *   "autotune"             1 time the launch shapes once per problem-size bucket
+ *   "use_graphs"           1 (default) replay repeated batches through CUDA graphs
+ *   "serve_max_batch"      requests the serving worker runs together
+ *   "serve_queue_cap"      submitted requests waiting for admission
+ *   "serve_mem_budget"     device bytes the serving worker may hold for requests
+ *   "serve_tile_rotations" rotations per request per serving iteration
+ * INVALID_ARG for an unknown key or a value out of range. */
+dses_status dses_set_option(dses_ctx* ctx, const char* key, int64_t value);
+dses_status dses_get_option(dses_ctx* ctx, const char* key, int64_t* value);
+
+/* Last error text of the context (empty string if none; never NULL). */
+const char* dses_last_error(dses_ctx* ctx);
+
+/* Static name of a status code. */
+const char* dses_status_string(dses_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DSES_H_ */

@@ -1,0 +1,163 @@
+// Device-side data structures and kernel launchers of the DSES library.
+// Host code (engine.cu) fills these descriptors; the kernels in pass.cu and
+// aux.cu read them. Nothing here is part of the public C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dses {
+
+// Threads of the rotation-pass CTA (one CTA per SM, 32 warps).
+constexpr int kPassThreads = 1024;
+// Source points staged per chunk in shared memory (float4 each).
+constexpr int kSrcChunk = 2048;
+// Largest dynamic shared memory a CTA may request on sm_103a (227 KB).
+constexpr int kMaxSmem = 232448;
+// Static shared memory of the pass kernel plus headroom.
+constexpr int kPassStaticSmem = 2048;
+// Histogram budget: what is left after the source chunk and static storage.
+constexpr int kHistBudget = kMaxSmem - kSrcChunk * 16 - kPassStaticSmem;
+
+// Everything the rotation pass needs for one registration problem.
+struct PassDesc {
+  // inputs (device)
+  const float* X;        // N x 3 source points
+  const float4* Y;       // M target points (cell-sorted; .w unused)
+  const float* rot;      // rotations of this pass, 9 floats each (row-major)
+  int N, M;
+  int n_rot;             // rotations in this pass
+  uint32_t rot_base;     // global rotation index of rot[0]
+  // translation lattice (Lemma 1 discretised): k = floor((y - R x)/delta + 1/2)
+  float inv_delta, delta;
+  int lo[3];             // lattice box lower corner
+  int E[3];              // lattice box extent per axis
+  int slab_x;            // x-planes per histogram slab
+  int n_slabs;
+  int hist_u16;          // 1: two 16-bit counters per 32-bit word
+  // vote work decomposition per rotation: items = n_tchunks x n_sgroups
+  int n_tchunks;         // target chunks of 32 * P points
+  int n_sgroups;         // source groups
+  // inlier count of Eq. 3 through the target cell list (cell size >= epsilon)
+  float eps2;
+  const int* cell_start; // ncells + 1 prefix offsets into Y
+  float cell_lo[3];
+  float cell_inv;
+  int cell_dim[3];
+  // robust cost
+  int fuse_score;        // 1: score every rotation inside the pass (grid path)
+  int metric;            // dses_metric
+  float eps, tau, huber_h, p_exp;
+  const float* D;        // G^3 truncated distance grid
+  int G;
+  float glo[3], ginv_h[3], gcap;
+  // outputs, indexed by (global rotation index - out_base)
+  uint32_t out_base;
+  int4* kv;              // (kx, ky, kz, V)
+  uint32_t* Mout;        // inlier count M
+  float* cost;           // robust cost (fused path)
+  // per-problem accumulators
+  uint32_t* acc;         // [0] = M*, [1] = max V
+  unsigned long long* best;  // argmin key (cost bits << 32 | rotation index)
+};
+
+struct PassLaunch {
+  const PassDesc* probs;   // device array
+  const int* tile_prefix;  // device, n_probs + 1 prefix sums of tiles
+  int n_probs;
+  int tile_rot;            // rotations per work item
+  int* work_counter;       // device, zeroed before the launch
+  int hist_bytes;          // histogram bytes of shared memory (max over problems)
+};
+
+// Hot path: vote -> argmax -> inlier count -> (fused) grid score per rotation.
+cudaError_t launch_rotation_pass(const PassLaunch& L, int points_per_thread, int grid_ctas, cudaStream_t s);
+int pass_smem_bytes(int hist_bytes);
+
+// --- rotation grids (FP64 arithmetic, FP32 output) -------------------------
+cudaError_t launch_hopf_grid(int n, float* out, cudaStream_t s);
+// Euler boxes around `count` centres given as FP32 matrices (centres[c*9]).
+cudaError_t launch_euler_boxes(const float* centres, int count, int K, double delta_r, float* out, cudaStream_t s);
+// Euler boxes around Hopf-grid centres named by the low 32 bits of sorted keys
+// (recomputed in FP64); all-ones padding keys repeat the previous centre.
+cudaError_t launch_euler_boxes_hopf(int n, const unsigned long long* keys, int count, int K, double delta_r,
+                                    float* out, cudaStream_t s);
+// Euler boxes around centres picked from an FP32 rotation array by key.
+cudaError_t launch_euler_boxes_keyed(const float* rot, const unsigned long long* keys, int count, int K,
+                                     double delta_r, float* out, cudaStream_t s);
+// Euler box around one FP64 centre held in device memory.
+cudaError_t launch_euler_box_single(const double* R0_dev, int K, double delta_r, float* out, cudaStream_t s);
+
+// --- target preprocessing ---------------------------------------------------
+cudaError_t launch_pack_points(const float* xyz, int m, float4* out, cudaStream_t s);
+cudaError_t launch_dist_grid(const float4* Y, int m, int G, const float* lo, const float* h, float cap, float* D,
+                             cudaStream_t s);
+// cell list: counts -> prefix -> scatter. counts: ncells ints; scratch: ncells + m ints.
+cudaError_t launch_cell_list(const float4* Y, int m, const float* cell_lo, float cell_inv, const int* dim,
+                             int* counts, int* cell_start, int* scratch, float4* sorted, cudaStream_t s);
+
+// --- candidate stage ----------------------------------------------------------
+struct ScoreDesc {
+  const float* X;
+  const float4* Y;
+  const float* rot;       // rotations of the pass (indexed by global index - rot_base)
+  int N, M;
+  float delta;
+  int metric;
+  float eps, tau, huber_h, p_exp;
+  const float* D;
+  int G;
+  float glo[3], ginv_h[3], gcap;
+  const int4* kv;         // per-rotation outputs, indexed by global index - out_base
+  const uint32_t* Mout;
+  float* cost;
+  uint32_t rot_base;
+  uint32_t out_base;
+};
+
+// candidates (output slots, i.e. global index - out_base) with 1000 M >= q_milli M*
+cudaError_t launch_select_q(const uint32_t* Mout, uint32_t first, int n, const uint32_t* acc, int q_milli,
+                            uint32_t* cand, uint32_t* n_cand, cudaStream_t s);
+// keys (0xffffffff - M) << 32 | global index for slots [first, first + n)
+cudaError_t launch_keys_from_M(const uint32_t* Mout, uint32_t first, int n, uint32_t out_base,
+                               unsigned long long* keys, cudaStream_t s);
+// keys cost_bits << 32 | global index over a candidate list (cand == NULL:
+// every slot of [0, n_max))
+cudaError_t launch_keys_from_cost(const float* cost, const uint32_t* cand, const uint32_t* n_cand, int n_max,
+                                  uint32_t out_base, unsigned long long* keys, cudaStream_t s);
+// the k smallest of n keys (n read from n_dev when not NULL, else n_max), ascending into out[k];
+// scratch holds 2 * ceil(n_max / 4096) * k keys
+cudaError_t launch_k_smallest(const unsigned long long* keys, int n_max, const uint32_t* n_dev, int k,
+                              unsigned long long* scratch, unsigned long long* out, cudaStream_t s);
+size_t k_smallest_scratch(int n_max, int k);
+// candidate slots from keys (global index - out_base), skipping padding keys
+cudaError_t launch_cand_from_keys(const unsigned long long* keys, int k, uint32_t out_base, uint32_t* cand,
+                                  uint32_t* n_cand, cudaStream_t s);
+cudaError_t launch_score_grid(const ScoreDesc& d, const uint32_t* cand, const uint32_t* n_cand, int n_max,
+                              cudaStream_t s);
+cudaError_t launch_score_brute(const ScoreDesc& d, const uint32_t* cand, const uint32_t* n_cand, int n_max,
+                               cudaStream_t s);
+// argmin over candidates of (cost bits << 32 | global index); INLIER metric uses N - M
+cudaError_t launch_argmin(float* cost, const uint32_t* Mout, int N, int metric, const uint32_t* cand,
+                          const uint32_t* n_cand, int n_max, uint32_t out_base, unsigned long long* best,
+                          cudaStream_t s);
+
+struct FinalDesc {
+  const unsigned long long* best;
+  const uint32_t* acc;    // [1]: max V of the first pass, [3]: of the second pass
+  const int4* kv;         // indexed by global index - out_base
+  const uint32_t* Mout;
+  const float* rot;       // first-pass rotations (global index < n_first)
+  const float* rot_fine;  // second-pass rotations (global index - n_first)
+  uint32_t n_first;
+  uint32_t out_base;
+  float delta;
+  void* result;           // device dses_result
+};
+cudaError_t launch_finalize(const FinalDesc* d_dev, int count, cudaStream_t s);
+
+cudaError_t launch_fill_u32(uint32_t* p, uint32_t v, size_t n, cudaStream_t s);
+cudaError_t launch_fill_f32(float* p, float v, size_t n, cudaStream_t s);
+cudaError_t launch_fill_u64(unsigned long long* p, unsigned long long v, size_t n, cudaStream_t s);
+
+}  // namespace dses
