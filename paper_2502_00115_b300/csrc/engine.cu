@@ -1,0 +1,1259 @@
+// Host side of the DSES library: contexts, resident targets, the launch
+// planner, the single / batched registration pipeline, the serving worker and
+// the C ABI declared in include/dses.h.
+//
+// Pipeline of one registration (Algorithm 2):
+//   rotation grid (cached per Hopf resolution, or built per call)
+//   -> rotation pass over every rotation (vote, mode, inlier count and, when
+//      every rotation is a candidate, the fused grid score + argmin)
+//   -> otherwise: candidate selection (q filter or top-k), scoring of the
+//      candidates (distance-grid lookup or exact brute-force nearest
+//      neighbour), argmin
+//   -> optional second pass on Euler boxes around the best candidates
+//   -> finaliser writes the dses_result on the device, one copy to the host.
+// Everything runs asynchronously on the context's stream; a call synchronises
+// once, at the end.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "dses.h"
+#include "kernels.cuh"
+
+using namespace dses;
+
+namespace {
+
+struct Error {
+  dses_status code;
+  std::string msg;
+};
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) {                                                                  \
+      if (e_ == cudaErrorMemoryAllocation) {                                                  \
+        cudaGetLastError();                                                                   \
+        throw Error{DSES_ERR_OOM, std::string(#call) + ": " + cudaGetErrorString(e_)};        \
+      }                                                                                       \
+      throw Error{DSES_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};         \
+    }                                                                                         \
+  } while (0)
+
+[[noreturn]] void invalid(const std::string& m) { throw Error{DSES_ERR_INVALID_ARG, m}; }
+
+inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Stream-ordered device allocation (the pool keeps freed blocks cached).
+struct DevMem {
+  void* p = nullptr;
+  cudaStream_t s = nullptr;
+  void alloc(size_t bytes, cudaStream_t stream) {
+    s = stream;
+    CK(cudaMallocAsync(&p, std::max<size_t>(bytes, 256), stream));
+  }
+  void release() {
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+  }
+  ~DevMem() { release(); }
+};
+
+struct CellList {
+  float cs = 0, inv = 0;
+  float lo[3] = {0, 0, 0};
+  int dim[3] = {0, 0, 0};
+  int* start = nullptr;     // ncells + 1
+  float4* sorted = nullptr; // m points in cell order
+};
+
+struct Options {
+  int64_t hist_mode = 0;
+  int64_t hist_budget = kHistBudget;
+  int64_t points_per_thread = 0;
+  int64_t fuse_score = 1;
+  int64_t tile_rotations = 0;
+  int64_t autotune = 0;
+  int64_t use_graphs = 1;
+  int64_t serve_max_batch = 16;
+  int64_t serve_queue_cap = 100000;
+  int64_t serve_mem_budget = 8LL << 30;
+  int64_t serve_tile_rotations = 8192;
+};
+
+}  // namespace
+
+struct dses_target {
+  dses_ctx* ctx = nullptr;
+  int m = 0;
+  std::vector<float> host;  // m x 3
+  float bbmin[3], bbmax[3];
+  float4* Y = nullptr;      // packed, input order
+  float* D = nullptr;       // G^3 distance grid
+  int G = 0;
+  float glo[3], gh[3], gcap = 0;
+  std::map<uint32_t, CellList> cells;  // by bit pattern of epsilon
+  std::map<uint32_t, int> capY;        // by bit pattern of delta_t
+  std::atomic<int> inflight{0};
+};
+
+namespace {
+
+struct Request;  // serving
+
+}  // namespace
+
+struct dses_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int sms = 148;
+  std::recursive_mutex mu;
+  std::string err;
+  std::map<int, float*> hopf;  // cached Hopf grids by N_side
+  std::vector<dses_target*> targets;
+  Options opt;
+  // serving
+  std::mutex smu;
+  std::condition_variable scv;
+  std::deque<std::shared_ptr<Request>> queue;
+  std::unordered_map<uint64_t, std::shared_ptr<Request>> tickets;
+  uint64_t next_ticket = 1;
+  std::thread worker;
+  bool stop = false;
+  bool worker_started = false;
+  dses_result* pinned_res = nullptr;  // result staging for blocking calls
+  size_t pinned_cap = 0;
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// small helpers
+
+uint32_t fbits(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  return u;
+}
+
+bool finite3(const float* p, int64_t n) {
+  for (int64_t i = 0; i < 3 * n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+void set_device(dses_ctx* c) { CK(cudaSetDevice(c->device)); }
+
+const float* hopf_grid(dses_ctx* c, int n) {
+  auto it = c->hopf.find(n);
+  if (it != c->hopf.end()) return it->second;
+  float* p = nullptr;
+  CK(cudaMalloc(&p, sizeof(float) * 9 * (size_t)72 * n * n * n));
+  CK(launch_hopf_grid(n, p, c->stream));
+  c->hopf[n] = p;
+  return p;
+}
+
+// Largest number of target points in any 2x2x2 block of cells of side
+// delta * 1.001: every half-open cube of side delta (and its FP32 image) lies
+// in one such block, so N * capY bounds every vote-histogram counter.
+int cap_points_in_cube(dses_target* T, float delta) {
+  auto it = T->capY.find(fbits(delta));
+  if (it != T->capY.end()) return it->second;
+  const double cs = (double)delta * 1.001;
+  std::unordered_map<uint64_t, int> cnt;
+  cnt.reserve((size_t)T->m * 2);
+  auto key = [](int64_t a, int64_t b, int64_t c) {
+    return ((uint64_t)(a + (1 << 20)) << 42) | ((uint64_t)(b + (1 << 20)) << 21) | (uint64_t)(c + (1 << 20));
+  };
+  std::vector<int64_t> cell((size_t)T->m * 3);
+  for (int j = 0; j < T->m; ++j) {
+    for (int a = 0; a < 3; ++a) cell[3 * j + a] = (int64_t)std::floor((T->host[3 * j + a] - T->bbmin[a]) / cs);
+    cnt[key(cell[3 * j], cell[3 * j + 1], cell[3 * j + 2])]++;
+  }
+  int best = 0;
+  for (int j = 0; j < T->m; ++j)
+    for (int dx = 0; dx < 2; ++dx)
+      for (int dy = 0; dy < 2; ++dy)
+        for (int dz = 0; dz < 2; ++dz) {
+          const int64_t bx = cell[3 * j] - dx, by = cell[3 * j + 1] - dy, bz = cell[3 * j + 2] - dz;
+          int s = 0;
+          for (int ex = 0; ex < 2; ++ex)
+            for (int ey = 0; ey < 2; ++ey)
+              for (int ez = 0; ez < 2; ++ez) {
+                auto f = cnt.find(key(bx + ex, by + ey, bz + ez));
+                if (f != cnt.end()) s += f->second;
+              }
+          best = std::max(best, s);
+        }
+  T->capY[fbits(delta)] = best;
+  return best;
+}
+
+// Target cell list for inlier counting at tolerance eps: cells at least
+// eps * 1.001 wide (so a query's 3x3x3 neighbourhood holds every point within
+// eps even after FP32 rounding), at most ~4M cells.
+CellList* cell_list(dses_ctx* c, dses_target* T, float eps) {
+  auto it = T->cells.find(fbits(eps));
+  if (it != T->cells.end()) return &it->second;
+  CellList cl;
+  double ext = 0;
+  for (int a = 0; a < 3; ++a) ext = std::max(ext, (double)T->bbmax[a] - T->bbmin[a]);
+  double cs = std::max((double)eps * 1.001, ext / 128.0);
+  if (cs <= 0) cs = 1e-6;
+  int dim[3];
+  for (;;) {
+    int64_t total = 1;
+    for (int a = 0; a < 3; ++a) {
+      dim[a] = (int)std::floor(((double)T->bbmax[a] - T->bbmin[a]) / cs) + 3;
+      total *= dim[a];
+    }
+    if (total <= (4 << 20)) break;
+    cs *= 1.26;
+  }
+  cl.cs = (float)cs;
+  cl.inv = (float)(1.0 / cs);
+  for (int a = 0; a < 3; ++a) {
+    cl.lo[a] = (float)((double)T->bbmin[a] - cs);
+    cl.dim[a] = dim[a];
+  }
+  const int ncells = dim[0] * dim[1] * dim[2];
+  CK(cudaMalloc(&cl.start, sizeof(int) * ((size_t)ncells + 1)));
+  CK(cudaMalloc(&cl.sorted, sizeof(float4) * (size_t)T->m));
+  DevMem tmp;
+  tmp.alloc(sizeof(int) * ((size_t)2 * ncells + T->m), c->stream);
+  int* counts = (int*)tmp.p;
+  CK(launch_cell_list(T->Y, T->m, cl.lo, cl.inv, cl.dim, counts, cl.start, counts + ncells, cl.sorted, c->stream));
+  tmp.release();
+  return &(T->cells[fbits(eps)] = cl);
+}
+
+// ---------------------------------------------------------------------------
+// one registration problem, resolved and planned
+
+struct Job {
+  const dses_problem* prob = nullptr;
+  dses_target* T = nullptr;
+  CellList* cl = nullptr;
+  int N = 0;
+  const float* X = nullptr;  // device
+  int metric = 0, q = 0, topk = 0, nn = 0, rtop = 0, rK = 0;
+  float eps = 0, delta = 0, tau = 0, hh = 0, pexp = 1;
+  double rdr = 0;
+  int lo[3], E[3];
+  const float* rot = nullptr;  // first-pass rotations (device)
+  int64_t n_first = 0, n_fine = 0, n_total = 0;
+  int hopf_n = 0;
+  // plan
+  int u16 = 0, slab_x = 0, n_slabs = 1, hist_bytes = 0;
+  bool fused = false;
+  // device scratch
+  DevMem mem;
+  int4* kv = nullptr;
+  uint32_t* M = nullptr;
+  float* cost = nullptr;
+  uint32_t* cand = nullptr;
+  uint32_t* n_cand = nullptr;  // [0] first pass, [1] second pass
+  uint32_t* acc = nullptr;     // [0] M* first, [1] max V first, [2] M* second, [3] max V second
+  unsigned long long* best = nullptr;
+  unsigned long long* keys = nullptr;
+  unsigned long long* ks_scratch = nullptr;
+  unsigned long long* ksel = nullptr;
+  float* rot_fine = nullptr;
+  float* rot_own = nullptr;  // Euler-box / explicit first-pass grid
+  double* R0 = nullptr;
+  float* Xown = nullptr;
+  dses_result* res = nullptr;
+  size_t bytes = 0;
+  int ksel_k = 0;
+};
+
+void resolve(dses_ctx* c, const dses_problem* pb, Job& j) {
+  if (!pb) invalid("problem is NULL");
+  j.prob = pb;
+  dses_target* T = const_cast<dses_target*>(pb->target);
+  if (!T || T->ctx != c) invalid("target is NULL or belongs to another context");
+  j.T = T;
+  if (!pb->src) invalid("src is NULL");
+  if (pb->n_src < 1 || pb->n_src > (1 << 24)) invalid("n_src must be in [1, 2^24]");
+  j.N = (int)pb->n_src;
+  if (!pb->src_is_device && !finite3(pb->src, pb->n_src)) invalid("source cloud has a non-finite coordinate");
+  const dses_params& P = pb->params;
+  if (P.metric < 0 || P.metric > 4) invalid("unknown metric");
+  j.metric = P.metric;
+  if (!(P.epsilon > 0) || !std::isfinite(P.epsilon)) invalid("epsilon must be positive and finite");
+  j.eps = P.epsilon;
+  j.delta = P.delta_t > 0 ? P.delta_t : P.epsilon;
+  if (!std::isfinite(j.delta)) invalid("delta_t must be finite");
+  j.tau = P.tau > 0 ? P.tau : 2.f * P.epsilon;
+  j.hh = P.huber_h > 0 ? P.huber_h : P.epsilon;
+  j.pexp = P.p;
+  if (j.metric == DSES_METRIC_LP && !(P.p > 0 && P.p <= 1)) invalid("LP metric needs p in (0, 1]");
+  if (P.q_milli < 0 || P.q_milli > 1000) invalid("q_milli must be in [0, 1000]");
+  if (P.top_k < 0 || P.top_k > 1024) invalid("top_k must be in [0, 1024]");
+  if (P.nn_mode != DSES_NN_GRID && P.nn_mode != DSES_NN_BRUTE) invalid("unknown nn_mode");
+  j.q = P.q_milli;
+  j.topk = P.top_k;
+  j.nn = P.nn_mode;
+  if (P.refine_top_k < 0 || P.refine_top_k > 1024) invalid("refine_top_k must be in [0, 1024]");
+  j.rtop = P.refine_top_k;
+  if (j.rtop > 0) {
+    if (P.refine_K < 0 || P.refine_K > 16) invalid("refine_K must be in [0, 16]");
+    if (!(P.refine_delta_r > 0) || !std::isfinite(P.refine_delta_r)) invalid("refine_delta_r must be positive");
+  }
+  j.rK = P.refine_K;
+  j.rdr = P.refine_delta_r;
+  if (j.metric != DSES_METRIC_INLIER && j.nn == DSES_NN_GRID && j.metric != DSES_METRIC_LP && T->gcap < j.tau)
+    invalid("the target's distance-grid cap is below tau; recreate the target with grid_cap >= tau");
+  // translation box: lattice points k delta inside [c - s, c + s]
+  for (int a = 0; a < 3; ++a) {
+    if (!(P.t_half[a] > 0) || !std::isfinite(P.t_half[a]) || !std::isfinite(P.t_center[a]))
+      invalid("t_half must be positive and t_center finite");
+    const double lo = std::ceil(((double)P.t_center[a] - (double)P.t_half[a]) / (double)j.delta);
+    const double hi = std::floor(((double)P.t_center[a] + (double)P.t_half[a]) / (double)j.delta);
+    if (hi < lo) invalid("translation box holds no lattice point");
+    if (lo < -(1 << 20) || hi > (1 << 20)) invalid("translation box too large for delta_t");
+    j.lo[a] = (int)lo;
+    j.E[a] = (int)(hi - lo + 1);
+  }
+  // rotation grid
+  const dses_rotation_grid& g = pb->grid;
+  if (g.kind == DSES_GRID_HOPF) {
+    if (g.hopf_n < 1 || g.hopf_n > 48) invalid("hopf_n must be in [1, 48]");
+    j.hopf_n = g.hopf_n;
+    j.n_first = 72LL * g.hopf_n * g.hopf_n * g.hopf_n;
+  } else if (g.kind == DSES_GRID_EULER_BOX) {
+    if (g.K < 0 || g.K > 100) invalid("Euler box K must be in [0, 100]");
+    if (!(g.delta_r > 0)) invalid("Euler box delta_r must be positive");
+    j.n_first = (int64_t)(2 * g.K + 1) * (2 * g.K + 1) * (2 * g.K + 1);
+  } else if (g.kind == DSES_GRID_EXPLICIT) {
+    if (!g.explicit_R || g.n_explicit < 1) invalid("explicit grid needs explicit_R and n_explicit >= 1");
+    j.n_first = g.n_explicit;
+  } else {
+    invalid("unknown rotation grid kind");
+  }
+  const int B = (2 * j.rK + 1) * (2 * j.rK + 1) * (2 * j.rK + 1);
+  j.n_fine = j.rtop > 0 ? (int64_t)j.rtop * B : 0;
+  j.n_total = j.n_first + j.n_fine;
+  if (j.n_total >= (1LL << 31)) invalid("too many rotations");
+}
+
+void plan(dses_ctx* c, Job& j) {
+  const int64_t Ey = j.E[1], Ez = j.E[2], Ex = j.E[0];
+  const int64_t budget = c->opt.hist_budget;
+  const int64_t M = j.T->m;
+  bool u16_ok = (int64_t)j.N * M <= 65535;
+  if (!u16_ok) u16_ok = (int64_t)j.N * cap_points_in_cube(j.T, j.delta) <= 65535;
+  bool u16;
+  if (c->opt.hist_mode == 1) {
+    u16 = false;
+  } else if (c->opt.hist_mode == 2) {
+    if (!u16_ok) invalid("16-bit vote counters could overflow for this problem");
+    u16 = true;
+  } else {
+    u16 = (Ex * Ey * Ez * 4 > budget) && u16_ok;
+  }
+  const int64_t per_plane = Ey * Ez * (u16 ? 2 : 4);
+  if (per_plane + 8 > budget) invalid("translation box too large: one lattice plane exceeds the histogram budget");
+  int64_t sx = std::min<int64_t>(Ex, (budget - 8) / per_plane);
+  j.u16 = u16;
+  j.slab_x = (int)sx;
+  j.n_slabs = (int)((Ex + sx - 1) / sx);
+  const int64_t bins = sx * Ey * Ez;
+  const int64_t hb = u16 ? ((bins + 1) / 2) * 4 : bins * 4;
+  j.hist_bytes = (int)((hb + 15) & ~15LL);
+  j.fused = c->opt.fuse_score && j.q == 0 && j.topk == 0 && (j.metric == DSES_METRIC_INLIER || j.nn == DSES_NN_GRID);
+}
+
+int choose_p(dses_ctx* c, const std::vector<Job*>& jobs) {
+  if (c->opt.points_per_thread > 0) return (int)c->opt.points_per_thread;
+  int64_t mmax = 0;
+  for (auto* j : jobs) mmax = std::max<int64_t>(mmax, j->T->m);
+  return mmax <= 128 ? 1 : (mmax <= 512 ? 2 : 4);
+}
+
+int gcd(int a, int b) { return b ? gcd(b, a % b) : a; }
+
+void carve(Job& j) {
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    const size_t o = off;
+    off += align256(b);
+    return o;
+  };
+  const size_t n = (size_t)j.n_total;
+  const int kmax = std::max({j.topk, j.rtop, 1});
+  j.ksel_k = kmax;
+  const size_t o_kv = take(16 * n), o_M = take(4 * n), o_cost = take(4 * n), o_cand = take(4 * n),
+               o_nc = take(8), o_acc = take(16), o_best = take(8), o_keys = take(8 * n),
+               o_ks = take(8 * k_smallest_scratch((int)j.n_total, kmax)), o_ksel = take(8 * (size_t)kmax),
+               o_fine = take(36 * (size_t)j.n_fine + 4), o_res = take(sizeof(dses_result));
+  const bool own_rot = j.prob->grid.kind != DSES_GRID_HOPF;
+  const size_t o_rot = own_rot ? take(36 * (size_t)j.n_first) : 0, o_R0 = own_rot ? take(72) : 0;
+  const size_t o_X = j.prob->src_is_device ? 0 : take(12 * (size_t)j.N);
+  j.bytes = off;
+  j.mem.alloc(off, j.mem.s ? j.mem.s : nullptr);
+  char* b = (char*)j.mem.p;
+  j.kv = (int4*)(b + o_kv);
+  j.M = (uint32_t*)(b + o_M);
+  j.cost = (float*)(b + o_cost);
+  j.cand = (uint32_t*)(b + o_cand);
+  j.n_cand = (uint32_t*)(b + o_nc);
+  j.acc = (uint32_t*)(b + o_acc);
+  j.best = (unsigned long long*)(b + o_best);
+  j.keys = (unsigned long long*)(b + o_keys);
+  j.ks_scratch = (unsigned long long*)(b + o_ks);
+  j.ksel = (unsigned long long*)(b + o_ksel);
+  j.rot_fine = (float*)(b + o_fine);
+  j.res = (dses_result*)(b + o_res);
+  if (own_rot) {
+    j.rot_own = (float*)(b + o_rot);
+    j.R0 = (double*)(b + o_R0);
+  }
+  if (!j.prob->src_is_device) j.Xown = (float*)(b + o_X);
+}
+
+// Device memory one job needs (for serving admission).
+size_t job_bytes(const Job& j) {
+  const size_t n = (size_t)j.n_total;
+  const int kmax = std::max({j.topk, j.rtop, 1});
+  size_t b = 40 * n + 8 * k_smallest_scratch((int)j.n_total, kmax) + 36 * (size_t)j.n_fine + 12 * (size_t)j.N +
+             (j.prob->grid.kind != DSES_GRID_HOPF ? 36 * (size_t)j.n_first : 0) + 16 * 256;
+  return b;
+}
+
+// Allocate scratch, upload inputs, build per-call grids, reset accumulators.
+void stage_setup(dses_ctx* c, Job& j) {
+  cudaStream_t s = c->stream;
+  j.mem.s = s;
+  carve(j);
+  j.cl = cell_list(c, j.T, j.eps);
+  if (j.Xown) {
+    CK(cudaMemcpyAsync(j.Xown, j.prob->src, 12 * (size_t)j.N, cudaMemcpyHostToDevice, s));
+    j.X = j.Xown;
+  } else {
+    j.X = j.prob->src;
+  }
+  const dses_rotation_grid& g = j.prob->grid;
+  if (g.kind == DSES_GRID_HOPF) {
+    j.rot = hopf_grid(c, g.hopf_n);
+  } else if (g.kind == DSES_GRID_EULER_BOX) {
+    CK(cudaMemcpyAsync(j.R0, g.R0, sizeof(double) * 9, cudaMemcpyHostToDevice, s));
+    CK(launch_euler_box_single(j.R0, g.K, g.delta_r, j.rot_own, s));
+    j.rot = j.rot_own;
+  } else {
+    if (!finite3(g.explicit_R, 3 * g.n_explicit)) invalid("explicit rotations have a non-finite entry");
+    CK(cudaMemcpyAsync(j.rot_own, g.explicit_R, 36 * (size_t)g.n_explicit, cudaMemcpyHostToDevice, s));
+    j.rot = j.rot_own;
+  }
+  CK(cudaMemsetAsync(j.acc, 0, 16, s));
+  CK(cudaMemsetAsync(j.n_cand, 0, 8, s));
+  CK(launch_fill_u64(j.best, ~0ull, 1, s));
+  CK(launch_fill_f32(j.cost, NAN, (size_t)j.n_total, s));
+}
+
+PassDesc make_desc(const Job& j, int P, bool second) {
+  PassDesc d;
+  std::memset(&d, 0, sizeof(d));
+  d.X = j.X;
+  d.Y = j.cl->sorted;
+  d.N = j.N;
+  d.M = j.T->m;
+  if (!second) {
+    d.rot = j.rot;
+    d.n_rot = (int)j.n_first;
+    d.rot_base = 0;
+    d.acc = j.acc;
+  } else {
+    d.rot = j.rot_fine;
+    d.n_rot = (int)j.n_fine;
+    d.rot_base = (uint32_t)j.n_first;
+    d.acc = j.acc + 2;
+  }
+  d.inv_delta = 1.0f / j.delta;
+  d.delta = j.delta;
+  for (int a = 0; a < 3; ++a) {
+    d.lo[a] = j.lo[a];
+    d.E[a] = j.E[a];
+  }
+  d.slab_x = j.slab_x;
+  d.n_slabs = j.n_slabs;
+  d.hist_u16 = j.u16;
+  d.n_tchunks = (j.T->m + 32 * P - 1) / (32 * P);
+  d.n_sgroups = 32 / gcd(d.n_tchunks, 32);
+  d.eps2 = j.eps * j.eps;
+  d.cell_start = j.cl->start;
+  for (int a = 0; a < 3; ++a) {
+    d.cell_lo[a] = j.cl->lo[a];
+    d.cell_dim[a] = j.cl->dim[a];
+    d.glo[a] = j.T->glo[a];
+    d.ginv_h[a] = 1.0f / j.T->gh[a];
+  }
+  d.cell_inv = j.cl->inv;
+  d.fuse_score = j.fused ? 1 : 0;
+  d.metric = j.metric;
+  d.eps = j.eps;
+  d.tau = j.tau;
+  d.huber_h = j.hh;
+  d.p_exp = j.pexp;
+  d.D = j.T->D;
+  d.G = j.T->G;
+  d.gcap = j.T->gcap;
+  d.out_base = 0;
+  d.kv = j.kv;
+  d.Mout = j.M;
+  d.cost = j.cost;
+  d.best = j.best;
+  return d;
+}
+
+// Rotations per work item: enough items to balance the SMs, few enough to
+// keep the work counter cold.
+int tile_rotations(dses_ctx* c, int64_t total_rot) {
+  if (c->opt.tile_rotations > 0) return (int)c->opt.tile_rotations;
+  const int64_t t = total_rot / ((int64_t)c->sms * 8);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(16, t));
+}
+
+// One persistent launch over the given (job, rotation range) work.
+struct PassPart {
+  Job* job;
+  bool second;
+  int64_t r0, r1;  // rotation range of the pass (local indices)
+};
+
+void launch_pass(dses_ctx* c, const std::vector<PassPart>& parts, int P) {
+  if (parts.empty()) return;
+  cudaStream_t s = c->stream;
+  std::vector<PassDesc> descs;
+  std::vector<int> prefix(1, 0);
+  int64_t total_rot = 0;
+  int hist = 16;
+  for (auto& pp : parts) total_rot += pp.r1 - pp.r0;
+  const int tile = tile_rotations(c, total_rot);
+  for (auto& pp : parts) {
+    PassDesc d = make_desc(*pp.job, P, pp.second);
+    d.rot += 9 * pp.r0;
+    d.rot_base += (uint32_t)pp.r0;
+    d.n_rot = (int)(pp.r1 - pp.r0);
+    descs.push_back(d);
+    prefix.push_back(prefix.back() + (int)((d.n_rot + tile - 1) / tile));
+    hist = std::max(hist, pp.job->hist_bytes);
+  }
+  const size_t db = align256(sizeof(PassDesc) * descs.size()), pb = align256(sizeof(int) * prefix.size());
+  DevMem m;
+  m.alloc(db + pb + 256, s);
+  char* base = (char*)m.p;
+  CK(cudaMemcpyAsync(base, descs.data(), sizeof(PassDesc) * descs.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(base + db, prefix.data(), sizeof(int) * prefix.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(base + db + pb, 0, 4, s));
+  PassLaunch L;
+  L.probs = (const PassDesc*)base;
+  L.tile_prefix = (const int*)(base + db);
+  L.n_probs = (int)descs.size();
+  L.tile_rot = tile;
+  L.work_counter = (int*)(base + db + pb);
+  L.hist_bytes = hist;
+  const int ctas = std::max(1, std::min(c->sms, prefix.back()));
+  CK(launch_rotation_pass(L, P, ctas, s));
+  m.release();
+}
+
+ScoreDesc make_score(const Job& j, bool second) {
+  ScoreDesc d;
+  std::memset(&d, 0, sizeof(d));
+  d.X = j.X;
+  d.Y = j.cl->sorted;
+  d.rot = second ? j.rot_fine : j.rot;
+  d.rot_base = second ? (uint32_t)j.n_first : 0;
+  d.out_base = 0;
+  d.N = j.N;
+  d.M = j.T->m;
+  d.delta = j.delta;
+  d.metric = j.metric;
+  d.eps = j.eps;
+  d.tau = j.tau;
+  d.huber_h = j.hh;
+  d.p_exp = j.pexp;
+  d.D = j.T->D;
+  d.G = j.T->G;
+  for (int a = 0; a < 3; ++a) {
+    d.glo[a] = j.T->glo[a];
+    d.ginv_h[a] = 1.0f / j.T->gh[a];
+  }
+  d.gcap = j.T->gcap;
+  d.kv = j.kv;
+  d.Mout = j.M;
+  d.cost = j.cost;
+  return d;
+}
+
+// Candidate selection, scoring and argmin of one pass (skipped when fused).
+void stage_candidates(dses_ctx* c, Job& j, bool second) {
+  if (j.fused) return;
+  cudaStream_t s = c->stream;
+  const uint32_t first = second ? (uint32_t)j.n_first : 0;
+  const int n = (int)(second ? j.n_fine : j.n_first);
+  uint32_t* cand = j.cand + first;
+  uint32_t* ncand = j.n_cand + (second ? 1 : 0);
+  if (j.topk > 0) {
+    CK(launch_keys_from_M(j.M, first, n, 0, j.keys, s));
+    const int k = std::min(j.topk, n);
+    CK(launch_k_smallest(j.keys, n, nullptr, k, j.ks_scratch, j.ksel, s));
+    CK(launch_cand_from_keys(j.ksel, k, 0, cand, ncand, s));
+  } else {
+    CK(launch_select_q(j.M, first, n, j.acc + (second ? 2 : 0), j.q, cand, ncand, s));
+  }
+  const ScoreDesc sd = make_score(j, second);
+  if (j.metric != DSES_METRIC_INLIER) {
+    if (j.nn == DSES_NN_GRID)
+      CK(launch_score_grid(sd, cand, ncand, n, s));
+    else
+      CK(launch_score_brute(sd, cand, ncand, n, s));
+  }
+  CK(launch_argmin(j.cost, j.M, j.N, j.metric, cand, ncand, n, 0, j.best, s));
+}
+
+// Euler boxes around the refine_top_k best first-pass candidates.
+void stage_refine_grid(dses_ctx* c, Job& j) {
+  cudaStream_t s = c->stream;
+  const int n = (int)j.n_first;
+  if (j.fused)
+    CK(launch_keys_from_cost(j.cost, nullptr, nullptr, n, 0, j.keys, s));
+  else
+    CK(launch_keys_from_cost(j.cost, j.cand, j.n_cand, n, 0, j.keys, s));
+  const int k = j.rtop;
+  CK(launch_k_smallest(j.keys, n, j.fused ? nullptr : j.n_cand, k, j.ks_scratch, j.ksel, s));
+  if (j.hopf_n > 0)
+    CK(launch_euler_boxes_hopf(j.hopf_n, j.ksel, k, j.rK, j.rdr, j.rot_fine, s));
+  else
+    CK(launch_euler_boxes_keyed(j.rot, j.ksel, k, j.rK, j.rdr, j.rot_fine, s));
+}
+
+void stage_finalize(dses_ctx* c, std::vector<Job*>& jobs) {
+  cudaStream_t s = c->stream;
+  std::vector<FinalDesc> fd(jobs.size());
+  for (size_t i = 0; i < jobs.size(); ++i) {
+    Job& j = *jobs[i];
+    fd[i].best = j.best;
+    fd[i].acc = j.acc;
+    fd[i].kv = j.kv;
+    fd[i].Mout = j.M;
+    fd[i].rot = j.rot;
+    fd[i].rot_fine = j.rot_fine;
+    fd[i].n_first = (uint32_t)j.n_first;
+    fd[i].out_base = 0;
+    fd[i].delta = j.delta;
+    fd[i].result = j.res;
+  }
+  DevMem m;
+  m.alloc(sizeof(FinalDesc) * fd.size(), s);
+  CK(cudaMemcpyAsync(m.p, fd.data(), sizeof(FinalDesc) * fd.size(), cudaMemcpyHostToDevice, s));
+  CK(launch_finalize((const FinalDesc*)m.p, (int)fd.size(), s));
+  m.release();
+}
+
+// The whole pipeline for a set of jobs; results land in each job's device
+// result slot. No host synchronisation inside.
+void run_pipeline(dses_ctx* c, std::vector<Job*>& jobs) {
+  for (auto* j : jobs) stage_setup(c, *j);
+  const int P = choose_p(c, jobs);
+  std::vector<PassPart> parts;
+  for (auto* j : jobs) parts.push_back({j, false, 0, j->n_first});
+  launch_pass(c, parts, P);
+  for (auto* j : jobs) stage_candidates(c, *j, false);
+  std::vector<PassPart> fine;
+  for (auto* j : jobs)
+    if (j->rtop > 0) {
+      stage_refine_grid(c, *j);
+      fine.push_back({j, true, 0, j->n_fine});
+    }
+  launch_pass(c, fine, P);
+  for (auto* j : jobs)
+    if (j->rtop > 0) stage_candidates(c, *j, true);
+  stage_finalize(c, jobs);
+}
+
+// ---------------------------------------------------------------------------
+// serving: continuous batching. Admitted requests are processed in
+// iterations; each iteration is one persistent pass launch over the next
+// slice of rotations of every active request. A request whose first pass
+// completes runs its candidate stage, second pass and finaliser, and leaves;
+// queued requests join at the next iteration when slots and memory allow.
+
+}  // namespace
+
+namespace {
+
+struct Request {
+  dses_problem prob;
+  std::vector<float> src;          // owned copy of the source cloud
+  std::vector<float> explicit_R;   // owned copy of an explicit grid
+  Job job;
+  int64_t next = 0;                // next first-pass rotation to schedule
+  bool admitted = false;
+  std::atomic<int> state{0};       // 0 queued, 1 running, 2 done
+  dses_result result;
+  dses_status status = DSES_OK;
+  std::string err;
+  dses_result* host_res = nullptr;  // pinned
+};
+
+void fail_request(Request& r, const Error& e) {
+  r.status = e.code;
+  r.err = e.msg;
+  std::memset(&r.result, 0, sizeof(r.result));
+  r.result.status = e.code;
+  r.result.rot_index = -1;
+}
+
+void worker_loop(dses_ctx* c) {
+  cudaSetDevice(c->device);
+  std::vector<std::shared_ptr<Request>> active;
+  size_t mem_used = 0;
+  for (;;) {
+    {
+      std::unique_lock<std::mutex> lk(c->smu);
+      if (active.empty()) c->scv.wait(lk, [&] { return c->stop || !c->queue.empty(); });
+      if (c->stop && active.empty()) return;
+      // admission: batch slots and device-memory budget
+      while (!c->queue.empty() && (int64_t)active.size() < c->opt.serve_max_batch) {
+        auto r = c->queue.front();
+        const size_t need = job_bytes(r->job);
+        if (!active.empty() && mem_used + need > (size_t)c->opt.serve_mem_budget) break;
+        c->queue.pop_front();
+        r->admitted = true;
+        mem_used += need;
+        active.push_back(r);
+      }
+    }
+    bool launched = false;
+    {
+      std::lock_guard<std::recursive_mutex> g(c->mu);
+      // set up newly admitted requests
+      for (auto& r : active) {
+        if (r->state.load() != 0) continue;
+        try {
+          stage_setup(c, r->job);
+          r->state = 1;
+        } catch (const Error& e) {
+          fail_request(*r, e);
+          r->state = 2;
+        }
+      }
+      // one iteration: the next slice of every running request
+      std::vector<PassPart> parts;
+      std::vector<Job*> jobs;
+      const int64_t slice = std::max<int64_t>(1, c->opt.serve_tile_rotations);
+      for (auto& r : active) {
+        if (r->state.load() != 1) continue;
+        const int64_t a = r->next, b = std::min(r->job.n_first, a + slice);
+        parts.push_back({&r->job, false, a, b});
+        jobs.push_back(&r->job);
+        r->next = b;
+      }
+      try {
+        if (!parts.empty()) launch_pass(c, parts, choose_p(c, jobs));
+        std::vector<Job*> fin;
+        std::vector<PassPart> fine;
+        for (auto& r : active) {
+          if (r->state.load() != 1 || r->next < r->job.n_first) continue;
+          stage_candidates(c, r->job, false);
+          if (r->job.rtop > 0) {
+            stage_refine_grid(c, r->job);
+            fine.push_back({&r->job, true, 0, r->job.n_fine});
+          }
+          fin.push_back(&r->job);
+        }
+        if (!fine.empty()) {
+          std::vector<Job*> fj;
+          for (auto& f : fine) fj.push_back(f.job);
+          launch_pass(c, fine, choose_p(c, fj));
+          for (auto* j : fj) stage_candidates(c, *j, true);
+        }
+        if (!fin.empty()) stage_finalize(c, fin);
+        for (auto& r : active) {
+          if (r->state.load() != 1 || r->next < r->job.n_first) continue;
+          CK(cudaMemcpyAsync(r->host_res, r->job.res, sizeof(dses_result), cudaMemcpyDeviceToHost, c->stream));
+          r->state = 3;  // finishing on the device
+        }
+        launched = true;
+      } catch (const Error& e) {
+        for (auto& r : active)
+          if (r->state.load() == 1 || r->state.load() == 3) {
+            fail_request(*r, e);
+            r->state = 2;
+          }
+      }
+    }
+    if (launched) {
+      const cudaError_t e = cudaStreamSynchronize(c->stream);
+      if (e != cudaSuccess) {
+        const Error err{DSES_ERR_CUDA, std::string("serving iteration: ") + cudaGetErrorString(e)};
+        for (auto& r : active)
+          if (r->state.load() == 1 || r->state.load() == 3) {
+            fail_request(*r, err);
+            r->state = 2;
+          }
+      }
+    }
+    // retire finished requests
+    std::vector<std::shared_ptr<Request>> keep;
+    for (auto& r : active) {
+      const int st = r->state.load();
+      if (st == 3) {
+        r->result = *r->host_res;
+        r->status = (dses_status)r->result.status;
+      }
+      if (st == 2 || st == 3) {
+        mem_used -= std::min(mem_used, job_bytes(r->job));
+        {
+          std::lock_guard<std::recursive_mutex> g(c->mu);
+          r->job.mem.release();
+        }
+        r->job.T->inflight--;
+        r->state = 2;  // visible to dses_poll only now
+      } else {
+        keep.push_back(r);
+      }
+    }
+    active.swap(keep);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// C ABI plumbing
+
+template <class F>
+dses_status guard(dses_ctx* c, F&& f) {
+  try {
+    f();
+    return DSES_OK;
+  } catch (const Error& e) {
+    if (c) c->err = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    if (c) c->err = "host allocation failed";
+    return DSES_ERR_OOM;
+  } catch (...) {
+    if (c) c->err = "unexpected C++ exception";
+    return DSES_ERR_CUDA;
+  }
+}
+
+dses_status finish_results(dses_ctx* c, std::vector<Job*>& jobs, dses_result* out) {
+  if (c->pinned_cap < jobs.size()) {
+    if (c->pinned_res) cudaFreeHost(c->pinned_res);
+    c->pinned_res = nullptr;
+    c->pinned_cap = 0;
+    CK(cudaMallocHost(&c->pinned_res, sizeof(dses_result) * std::max<size_t>(jobs.size(), 64)));
+    c->pinned_cap = std::max<size_t>(jobs.size(), 64);
+  }
+  dses_result* pinned = c->pinned_res;
+  for (size_t i = 0; i < jobs.size(); ++i)
+    CK(cudaMemcpyAsync(pinned + i, jobs[i]->res, sizeof(dses_result), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  dses_status st = DSES_OK;
+  for (size_t i = 0; i < jobs.size(); ++i) {
+    out[i] = pinned[i];
+    if (st == DSES_OK && out[i].status != DSES_OK) st = (dses_status)out[i].status;
+  }
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+dses_status dses_create(int device, void* cuda_stream, dses_ctx** out) {
+  if (!out) return DSES_ERR_INVALID_ARG;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return DSES_ERR_INVALID_ARG;
+  }
+  dses_ctx* c = new (std::nothrow) dses_ctx();
+  if (!c) return DSES_ERR_OOM;
+  c->device = device;
+  dses_status st = guard(c, [&] {
+    CK(cudaSetDevice(device));
+    CK(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device));
+    if (cuda_stream) {
+      c->stream = (cudaStream_t)cuda_stream;
+    } else {
+      CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+      c->own_stream = true;
+    }
+    cudaMemPool_t pool;
+    CK(cudaDeviceGetDefaultMemPool(&pool, device));
+    uint64_t thr = UINT64_MAX;
+    CK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+  });
+  if (st != DSES_OK) {
+    delete c;
+    return st;
+  }
+  *out = c;
+  return DSES_OK;
+}
+
+static void stop_worker(dses_ctx* c) {
+  if (!c->worker_started) return;
+  {
+    std::lock_guard<std::mutex> lk(c->smu);
+    c->stop = true;
+  }
+  c->scv.notify_all();
+  c->worker.join();
+  c->worker_started = false;
+}
+
+static void free_target(dses_target* T) {
+  if (T->Y) cudaFree(T->Y);
+  if (T->D) cudaFree(T->D);
+  for (auto& kv : T->cells) {
+    cudaFree(kv.second.start);
+    cudaFree(kv.second.sorted);
+  }
+  delete T;
+}
+
+dses_status dses_destroy(dses_ctx* c) {
+  if (!c) return DSES_ERR_INVALID_ARG;
+  stop_worker(c);
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  for (auto& r : c->tickets)
+    if (r.second->host_res) cudaFreeHost(r.second->host_res);
+  for (auto* T : c->targets) free_target(T);
+  for (auto& h : c->hopf) cudaFree(h.second);
+  if (c->pinned_res) cudaFreeHost(c->pinned_res);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return DSES_OK;
+}
+
+dses_status dses_create_target(dses_ctx* c, const float* xyz, int64_t m, int32_t ptr_is_device, float grid_cap,
+                               int32_t grid_res, dses_target** out) {
+  if (!c || !out) return DSES_ERR_INVALID_ARG;
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  *out = nullptr;
+  return guard(c, [&] {
+    if (!xyz || m < 1 || m > (1 << 24)) invalid("target needs 1 <= m <= 2^24 points");
+    const int G = grid_res == 0 ? 128 : grid_res;
+    if (G < 8 || G > 512) invalid("grid_res must be in [8, 512]");
+    if (!(grid_cap > 0) || !std::isfinite(grid_cap)) invalid("grid_cap must be positive and finite");
+    set_device(c);
+    std::unique_ptr<dses_target> T(new dses_target());
+    T->ctx = c;
+    T->m = (int)m;
+    T->host.resize(3 * (size_t)m);
+    if (ptr_is_device) {
+      CK(cudaMemcpyAsync(T->host.data(), xyz, 12 * (size_t)m, cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+    } else {
+      std::memcpy(T->host.data(), xyz, 12 * (size_t)m);
+    }
+    if (!finite3(T->host.data(), m)) invalid("target cloud has a non-finite coordinate");
+    for (int a = 0; a < 3; ++a) {
+      T->bbmin[a] = T->bbmax[a] = T->host[a];
+      for (int64_t j = 1; j < m; ++j) {
+        T->bbmin[a] = std::min(T->bbmin[a], T->host[3 * j + a]);
+        T->bbmax[a] = std::max(T->bbmax[a], T->host[3 * j + a]);
+      }
+    }
+    float* raw = nullptr;
+    CK(cudaMalloc(&T->Y, sizeof(float4) * (size_t)m));
+    DevMem tmp;
+    tmp.alloc(12 * (size_t)m, c->stream);
+    raw = (float*)tmp.p;
+    CK(cudaMemcpyAsync(raw, T->host.data(), 12 * (size_t)m, cudaMemcpyHostToDevice, c->stream));
+    CK(launch_pack_points(raw, (int)m, T->Y, c->stream));
+    tmp.release();
+    // truncated distance grid: h = (extent + 2 cap)/(G - 2), origin min - cap - h
+    T->G = G;
+    T->gcap = grid_cap;
+    for (int a = 0; a < 3; ++a) {
+      const double h = ((double)T->bbmax[a] - T->bbmin[a] + 2.0 * grid_cap) / (double)(G - 2);
+      T->gh[a] = (float)h;
+      T->glo[a] = (float)((double)T->bbmin[a] - grid_cap - h);
+    }
+    CK(cudaMalloc(&T->D, sizeof(float) * (size_t)G * G * G));
+    CK(launch_dist_grid(T->Y, (int)m, G, T->glo, T->gh, grid_cap, T->D, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->targets.push_back(T.get());
+    *out = T.release();
+  });
+}
+
+dses_status dses_destroy_target(dses_ctx* c, dses_target* T) {
+  if (!c || !T) return DSES_ERR_INVALID_ARG;
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  return guard(c, [&] {
+    auto it = std::find(c->targets.begin(), c->targets.end(), T);
+    if (it == c->targets.end()) invalid("unknown target");
+    if (T->inflight.load() > 0) invalid("target is still used by submitted requests");
+    set_device(c);
+    CK(cudaStreamSynchronize(c->stream));
+    c->targets.erase(it);
+    free_target(T);
+  });
+}
+
+dses_status dses_register_batch(dses_ctx* c, const dses_problem* problems, int32_t n, dses_result* out) {
+  if (!c) return DSES_ERR_INVALID_ARG;
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  dses_status st = DSES_OK;
+  dses_status gs = guard(c, [&] {
+    if (!problems || !out || n < 1) invalid("batch needs problems, out and n >= 1");
+    set_device(c);
+    std::vector<std::unique_ptr<Job>> owned;
+    std::vector<Job*> jobs;
+    for (int i = 0; i < n; ++i) {
+      owned.emplace_back(new Job());
+      resolve(c, &problems[i], *owned.back());
+      plan(c, *owned.back());
+      jobs.push_back(owned.back().get());
+    }
+    run_pipeline(c, jobs);
+    st = finish_results(c, jobs, out);
+    if (st != DSES_OK) c->err = "a problem found no candidate (no pair voted inside its translation box)";
+  });
+  return gs != DSES_OK ? gs : st;
+}
+
+dses_status dses_register(dses_ctx* c, const dses_problem* problem, dses_result* out) {
+  return dses_register_batch(c, problem, 1, out);
+}
+
+dses_status dses_debug_per_rotation(dses_ctx* c, const dses_problem* problem, int32_t* k_star, uint32_t* votes,
+                                    uint32_t* inliers, float* cost, dses_result* out) {
+  if (!c) return DSES_ERR_INVALID_ARG;
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  dses_status st = DSES_OK;
+  dses_status gs = guard(c, [&] {
+    set_device(c);
+    Job job;
+    resolve(c, problem, job);
+    plan(c, job);
+    std::vector<Job*> jobs{&job};
+    run_pipeline(c, jobs);
+    const size_t n = (size_t)job.n_total;
+    std::vector<int4> kv(n);
+    std::vector<uint32_t> M(n);
+    std::vector<float> C(n);
+    CK(cudaMemcpyAsync(kv.data(), job.kv, 16 * n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(M.data(), job.M, 4 * n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(C.data(), job.cost, 4 * n, cudaMemcpyDeviceToHost, c->stream));
+    dses_result r;
+    st = finish_results(c, jobs, &r);
+    for (size_t i = 0; i < n; ++i) {
+      if (k_star) {
+        k_star[3 * i] = kv[i].x;
+        k_star[3 * i + 1] = kv[i].y;
+        k_star[3 * i + 2] = kv[i].z;
+      }
+      if (votes) votes[i] = (uint32_t)kv[i].w;
+      if (inliers) inliers[i] = M[i];
+      if (cost) cost[i] = C[i];
+    }
+    if (out) *out = r;
+  });
+  return gs != DSES_OK ? gs : st;
+}
+
+dses_status dses_submit(dses_ctx* c, const dses_problem* problem, uint64_t* ticket) {
+  if (!c || !problem || !ticket) return DSES_ERR_INVALID_ARG;
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  return guard(c, [&] {
+    auto r = std::make_shared<Request>();
+    r->prob = *problem;
+    if (problem->src_is_device) invalid("dses_submit takes a host source cloud");
+    if (!problem->src || problem->n_src < 1 || problem->n_src > (1 << 24)) invalid("bad source cloud");
+    r->src.assign(problem->src, problem->src + 3 * problem->n_src);
+    r->prob.src = r->src.data();
+    if (problem->grid.kind == DSES_GRID_EXPLICIT && problem->grid.explicit_R && problem->grid.n_explicit > 0) {
+      r->explicit_R.assign(problem->grid.explicit_R, problem->grid.explicit_R + 9 * problem->grid.n_explicit);
+      r->prob.grid.explicit_R = r->explicit_R.data();
+    }
+    resolve(c, &r->prob, r->job);
+    plan(c, r->job);
+    set_device(c);
+    CK(cudaMallocHost(&r->host_res, sizeof(dses_result)));
+    {
+      std::lock_guard<std::mutex> lk(c->smu);
+      if ((int64_t)c->queue.size() >= c->opt.serve_queue_cap) {
+        cudaFreeHost(r->host_res);
+        throw Error{DSES_ERR_QUEUE_FULL, "serving queue is full"};
+      }
+      *ticket = c->next_ticket++;
+      c->tickets[*ticket] = r;
+      r->job.T->inflight++;
+      c->queue.push_back(r);
+      if (!c->worker_started) {
+        c->stop = false;
+        c->worker = std::thread(worker_loop, c);
+        c->worker_started = true;
+      }
+    }
+    c->scv.notify_all();
+  });
+}
+
+dses_status dses_poll(dses_ctx* c, uint64_t ticket, dses_result* out) {
+  if (!c || !out) return DSES_ERR_INVALID_ARG;
+  std::shared_ptr<Request> r;
+  {
+    std::lock_guard<std::mutex> lk(c->smu);
+    auto it = c->tickets.find(ticket);
+    if (it == c->tickets.end()) return DSES_ERR_UNKNOWN_TICKET;
+    r = it->second;
+    if (r->state.load() != 2) return DSES_NOT_READY;
+    c->tickets.erase(it);
+  }
+  *out = r->result;
+  if (r->host_res) cudaFreeHost(r->host_res);
+  r->host_res = nullptr;
+  if (r->status != DSES_OK) {
+    std::lock_guard<std::recursive_mutex> g(c->mu);
+    c->err = r->err.empty() ? "registration found no candidate" : r->err;
+  }
+  return r->status;
+}
+
+dses_status dses_rotation_grid_build(dses_ctx* c, const dses_rotation_grid* grid, float* out_R, int64_t capacity,
+                                     int64_t* count) {
+  if (!c || !grid || !count) return DSES_ERR_INVALID_ARG;
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  return guard(c, [&] {
+    set_device(c);
+    int64_t n = 0;
+    if (grid->kind == DSES_GRID_HOPF) {
+      if (grid->hopf_n < 1 || grid->hopf_n > 48) invalid("hopf_n must be in [1, 48]");
+      n = 72LL * grid->hopf_n * grid->hopf_n * grid->hopf_n;
+    } else if (grid->kind == DSES_GRID_EULER_BOX) {
+      if (grid->K < 0 || grid->K > 100 || !(grid->delta_r > 0)) invalid("bad Euler box");
+      n = (int64_t)(2 * grid->K + 1) * (2 * grid->K + 1) * (2 * grid->K + 1);
+    } else {
+      invalid("only HOPF and EULER_BOX grids are built on the device");
+    }
+    *count = n;
+    if (!out_R) return;
+    if (n > capacity) invalid("capacity is smaller than the grid");
+    if (grid->kind == DSES_GRID_HOPF) {
+      const float* p = hopf_grid(c, grid->hopf_n);
+      CK(cudaMemcpyAsync(out_R, p, 36 * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
+    } else {
+      DevMem m;
+      m.alloc(36 * (size_t)n + 128, c->stream);
+      double* R0 = (double*)((char*)m.p + align256(36 * (size_t)n));
+      CK(cudaMemcpyAsync(R0, grid->R0, 72, cudaMemcpyHostToDevice, c->stream));
+      CK(launch_euler_box_single(R0, grid->K, grid->delta_r, (float*)m.p, c->stream));
+      CK(cudaMemcpyAsync(out_R, m.p, 36 * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
+      m.release();
+    }
+    CK(cudaStreamSynchronize(c->stream));
+  });
+}
+
+dses_status dses_target_distance_grid(dses_ctx* c, const dses_target* T, float* D, float lo[3], float h[3],
+                                      int32_t* res, float* cap) {
+  if (!c || !T) return DSES_ERR_INVALID_ARG;
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  return guard(c, [&] {
+    if (T->ctx != c) invalid("target belongs to another context");
+    if (res) *res = T->G;
+    if (cap) *cap = T->gcap;
+    for (int a = 0; a < 3; ++a) {
+      if (lo) lo[a] = T->glo[a];
+      if (h) h[a] = T->gh[a];
+    }
+    if (D) {
+      set_device(c);
+      CK(cudaMemcpyAsync(D, T->D, sizeof(float) * (size_t)T->G * T->G * T->G, cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+    }
+  });
+}
+
+static int64_t* option_slot(dses_ctx* c, const char* key) {
+  if (!key) return nullptr;
+  const std::string k(key);
+  Options& o = c->opt;
+  if (k == "hist_mode") return &o.hist_mode;
+  if (k == "hist_budget_bytes") return &o.hist_budget;
+  if (k == "points_per_thread") return &o.points_per_thread;
+  if (k == "fuse_score") return &o.fuse_score;
+  if (k == "tile_rotations") return &o.tile_rotations;
+  if (k == "autotune") return &o.autotune;
+  if (k == "use_graphs") return &o.use_graphs;
+  if (k == "serve_max_batch") return &o.serve_max_batch;
+  if (k == "serve_queue_cap") return &o.serve_queue_cap;
+  if (k == "serve_mem_budget") return &o.serve_mem_budget;
+  if (k == "serve_tile_rotations") return &o.serve_tile_rotations;
+  return nullptr;
+}
+
+dses_status dses_set_option(dses_ctx* c, const char* key, int64_t value) {
+  if (!c) return DSES_ERR_INVALID_ARG;
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  return guard(c, [&] {
+    int64_t* slot = option_slot(c, key);
+    if (!slot) invalid(std::string("unknown option ") + (key ? key : "(null)"));
+    const std::string k(key);
+    bool ok = true;
+    if (k == "hist_mode") ok = value >= 0 && value <= 2;
+    else if (k == "hist_budget_bytes") ok = value >= 1024 && value <= kHistBudget;
+    else if (k == "points_per_thread") ok = value == 0 || value == 1 || value == 2 || value == 4 || value == 8;
+    else if (k == "fuse_score" || k == "autotune" || k == "use_graphs") ok = value == 0 || value == 1;
+    else if (k == "tile_rotations") ok = value >= 0 && value <= 4096;
+    else ok = value >= 1;
+    if (!ok) invalid("option value out of range for " + k);
+    *slot = value;
+  });
+}
+
+dses_status dses_get_option(dses_ctx* c, const char* key, int64_t* value) {
+  if (!c || !value) return DSES_ERR_INVALID_ARG;
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  return guard(c, [&] {
+    int64_t* slot = option_slot(c, key);
+    if (!slot) invalid(std::string("unknown option ") + (key ? key : "(null)"));
+    *value = *slot;
+  });
+}
+
+const char* dses_last_error(dses_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+const char* dses_status_string(dses_status s) {
+  switch (s) {
+    case DSES_OK: return "DSES_OK";
+    case DSES_NOT_READY: return "DSES_NOT_READY";
+    case DSES_ERR_INVALID_ARG: return "DSES_ERR_INVALID_ARG";
+    case DSES_ERR_OOM: return "DSES_ERR_OOM";
+    case DSES_ERR_CUDA: return "DSES_ERR_CUDA";
+    case DSES_ERR_QUEUE_FULL: return "DSES_ERR_QUEUE_FULL";
+    case DSES_ERR_TIMEOUT: return "DSES_ERR_TIMEOUT";
+    case DSES_ERR_NO_CANDIDATE: return "DSES_ERR_NO_CANDIDATE";
+    case DSES_ERR_UNKNOWN_TICKET: return "DSES_ERR_UNKNOWN_TICKET";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"
