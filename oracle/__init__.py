@@ -98,6 +98,10 @@ def _load():
                 "orc_register": (i32, [pd, i64, pd, i64, pd, i64, P(Params), P(ctypes.c_int32), pi64, pi64, pd,
                                        pi64, pi64, P(Result)]),
                 "orc_register_threads": (i32, [pd, i64, pd, i64, pd, i64, P(Params), i32, P(Result)]),
+                "orc_field_create": (ctypes.c_void_p, [pd, i64, i32, d]),
+                "orc_field_free": (None, [ctypes.c_void_p]),
+                "orc_register_field_threads": (i32, [pd, i64, pd, i64, pd, i64, P(Params), ctypes.c_void_p, i32,
+                                                     P(Result)]),
                 "orc_eval_rotation": (None, [pd, i64, pd, i64, pd, P(Params), pi32, pi64, pi64, pi64, pi64]),
             }
             for name, (res, args) in sig.items():
@@ -318,6 +322,31 @@ def register_threads(X, Y, rotations, P: Params, threads: int) -> Registration:
     res = Result()
     _load().orc_register_threads(_pd(X), len(X), _pd(Y), len(Y), _pd(Rl), len(Rl), ctypes.byref(P), threads,
                                  ctypes.byref(res))
+    return _result(res)
+
+
+class Field:
+    """A target's distance field built once (the resident-target setting)."""
+
+    def __init__(self, Y, G: int, cap: float):
+        self.Y = _f64(Y)
+        self.h = _load().orc_field_create(_pd(self.Y), len(self.Y), G, cap)
+
+    def close(self):
+        if self.h:
+            _load().orc_field_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+
+def register_field_threads(X, Y, rotations, P: Params, field: Field | None, threads: int) -> Registration:
+    """register_threads() reusing a prebuilt distance field (None: metrics that need none)."""
+    X, Y, Rl = _f64(X), _f64(Y), _f64(rotations)
+    res = Result()
+    _load().orc_register_field_threads(_pd(X), len(X), _pd(Y), len(Y), _pd(Rl), len(Rl), ctypes.byref(P),
+                                       field.h if field is not None else None, threads, ctypes.byref(res))
     return _result(res)
 
 

@@ -539,20 +539,24 @@ static void select_candidates(std::vector<RotOut>& o, size_t begin, size_t end, 
 
 extern "C" {
 
+static void build_field(const double* Y, int64_t M, int G, double cap, Field* F) {
+  F->G = G;
+  F->cap = cap;
+  F->D.resize((size_t)G * G * G);
+  orc_dist_grid(Y, M, G, cap, F->D.data());
+  orc_dist_grid_geometry(Y, M, G, cap, F->lo, F->h);
+}
+
+// `prebuilt`: the target's distance field built beforehand (or NULL to build it here).
 static int run_register(const double* X, int64_t N, const double* Y, int64_t M, const double* Rlist,
                         int64_t nR, const orc_params* P, int threads, int32_t* out_k, int64_t* out_V,
                         int64_t* out_M, double* out_cost, int64_t* out_nbp, int64_t* out_nbm,
-                        orc_result* res) {
+                        orc_result* res, const Field* prebuilt = nullptr) {
   int lo[3], hi[3];
   orc_lattice_box(P->t_center, P->t_half, P->delta_t, lo, hi);
-  Field F;
-  if (P->metric != 0 && P->nn_mode == 0) {
-    F.G = P->grid_res;
-    F.cap = P->grid_cap;
-    F.D.resize((size_t)F.G * F.G * F.G);
-    orc_dist_grid(Y, M, F.G, F.cap, F.D.data());
-    orc_dist_grid_geometry(Y, M, F.G, F.cap, F.lo, F.h);
-  }
+  Field Fown;
+  if (!prebuilt && P->metric != 0 && P->nn_mode == 0) build_field(Y, M, P->grid_res, P->grid_cap, &Fown);
+  const Field& F = prebuilt ? *prebuilt : Fown;
   const int B = P->refine_top_k > 0 ? (2 * P->refine_K + 1) * (2 * P->refine_K + 1) * (2 * P->refine_K + 1) : 0;
   const int64_t total = nR + (int64_t)P->refine_top_k * B;
   std::vector<RotOut> o((size_t)total);
@@ -624,6 +628,22 @@ int orc_register_threads(const double* X, int64_t N, const double* Y, int64_t M,
                          int64_t nR, const orc_params* P, int threads, orc_result* res) {
   return run_register(X, N, Y, M, Rlist, nR, P, threads, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                       res);
+}
+
+// A target's distance field, built once and reused by orc_register_field_threads
+// (the resident-target setting: the field is not part of a registration).
+void* orc_field_create(const double* Y, int64_t M, int G, double cap) {
+  Field* F = new Field();
+  build_field(Y, M, G, cap, F);
+  return F;
+}
+
+void orc_field_free(void* f) { delete static_cast<Field*>(f); }
+
+int orc_register_field_threads(const double* X, int64_t N, const double* Y, int64_t M, const double* Rlist,
+                               int64_t nR, const orc_params* P, const void* field, int threads, orc_result* res) {
+  return run_register(X, N, Y, M, Rlist, nR, P, threads, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, res,
+                      static_cast<const Field*>(field));
 }
 
 // Per-rotation evaluation at a given rotation (used by the sampled parity

@@ -11,7 +11,13 @@
 #include "dses.h"
 #include "kernels.cuh"
 
+#include <atomic>
+
 namespace dses {
+
+std::atomic<long long> g_launches{0};
+long long kernel_launch_count() { return g_launches.load(); }
+
 namespace {
 
 constexpr double kPi = 3.14159265358979323846264338327950288;
@@ -494,6 +500,7 @@ inline int blocks_for(long long n, int t) { return (int)std::max<long long>(1, (
 
 cudaError_t launch_hopf_grid(int n, float* out, cudaStream_t s) {
   const long long total = 72LL * n * n * n;
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   hopf_grid_kernel<<<blocks_for(total, 256), 256, 0, s>>>(n, total, out);
   return cudaGetLastError();
 }
@@ -501,6 +508,7 @@ cudaError_t launch_hopf_grid(int n, float* out, cudaStream_t s) {
 static long long box_total(int count, int K) { return (long long)count * (2 * K + 1) * (2 * K + 1) * (2 * K + 1); }
 
 cudaError_t launch_euler_boxes(const float* centres, int count, int K, double dr, float* out, cudaStream_t s) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   euler_boxes_kernel<<<blocks_for(box_total(count, K), 128), 128, 0, s>>>(centres, 0, nullptr, nullptr, nullptr,
                                                                           count, K, dr, out);
   return cudaGetLastError();
@@ -508,6 +516,7 @@ cudaError_t launch_euler_boxes(const float* centres, int count, int K, double dr
 
 cudaError_t launch_euler_boxes_hopf(int n, const unsigned long long* keys, int count, int K, double dr, float* out,
                                     cudaStream_t s) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   euler_boxes_kernel<<<blocks_for(box_total(count, K), 128), 128, 0, s>>>(nullptr, n, keys, nullptr, nullptr, count,
                                                                           K, dr, out);
   return cudaGetLastError();
@@ -515,18 +524,21 @@ cudaError_t launch_euler_boxes_hopf(int n, const unsigned long long* keys, int c
 
 cudaError_t launch_euler_boxes_keyed(const float* rot, const unsigned long long* keys, int count, int K, double dr,
                                      float* out, cudaStream_t s) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   euler_boxes_kernel<<<blocks_for(box_total(count, K), 128), 128, 0, s>>>(nullptr, 0, keys, rot, nullptr, count, K,
                                                                           dr, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_euler_box_single(const double* R0_dev, int K, double dr, float* out, cudaStream_t s) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   euler_boxes_kernel<<<blocks_for(box_total(1, K), 128), 128, 0, s>>>(nullptr, 0, nullptr, nullptr, R0_dev, 1, K,
                                                                       dr, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pack_points(const float* xyz, int m, float4* out, cudaStream_t s) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   pack_points_kernel<<<blocks_for(m, 256), 256, 0, s>>>(xyz, m, out);
   return cudaGetLastError();
 }
@@ -534,6 +546,7 @@ cudaError_t launch_pack_points(const float* xyz, int m, float4* out, cudaStream_
 cudaError_t launch_dist_grid(const float4* Y, int m, int G, const float* lo, const float* h, float cap, float* D,
                              cudaStream_t s) {
   const long long total = (long long)G * G * G;
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   dist_grid_kernel<<<blocks_for(total, 256), 256, 0, s>>>(Y, m, G, lo[0], lo[1], lo[2], h[0], h[1], h[2], cap, D);
   return cudaGetLastError();
 }
@@ -545,28 +558,35 @@ cudaError_t launch_cell_list(const float4* Y, int m, const float* cell_lo, float
   if (e != cudaSuccess) return e;
   int* cursor = scratch;
   int* cell_of_pt = scratch + ncells;
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   cell_count_kernel<<<blocks_for(m, 256), 256, 0, s>>>(Y, m, cell_lo[0], cell_lo[1], cell_lo[2], cell_inv, dim[0],
                                                         dim[1], dim[2], counts, cell_of_pt);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   exclusive_scan_kernel<<<1, 1024, 0, s>>>(counts, ncells, cell_start);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   copy_int_kernel<<<blocks_for(ncells, 256), 256, 0, s>>>(cell_start, ncells, cursor);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   cell_scatter_kernel<<<blocks_for(m, 256), 256, 0, s>>>(Y, m, cell_of_pt, cursor, sorted);
   return cudaGetLastError();
 }
 
 cudaError_t launch_select_q(const uint32_t* Mout, uint32_t first, int n, const uint32_t* acc, int q_milli,
                             uint32_t* cand, uint32_t* n_cand, cudaStream_t s) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   select_q_kernel<<<blocks_for(n, 256), 256, 0, s>>>(Mout, first, n, acc, q_milli, cand, n_cand);
   return cudaGetLastError();
 }
 
 cudaError_t launch_keys_from_M(const uint32_t* Mout, uint32_t first, int n, uint32_t out_base,
                                unsigned long long* keys, cudaStream_t s) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   keys_from_M_kernel<<<blocks_for(n, 256), 256, 0, s>>>(Mout, first, n, out_base, keys);
   return cudaGetLastError();
 }
 
 cudaError_t launch_keys_from_cost(const float* cost, const uint32_t* cand, const uint32_t* n_cand, int n_max,
                                   uint32_t out_base, unsigned long long* keys, cudaStream_t s) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   keys_from_cost_kernel<<<blocks_for(n_max, 256), 256, 0, s>>>(cost, cand, n_cand, n_max, out_base, keys);
   return cudaGetLastError();
 }
@@ -583,18 +603,21 @@ cudaError_t launch_k_smallest(const unsigned long long* keys, int n_max, const u
   int which = 0;
   while (n_cur > kSortN) {
     const int blocks = (n_cur + kSortN - 1) / kSortN;
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     block_k_smallest_kernel<<<blocks, 1024, 0, s>>>(src, n_cur, nd, k, bufs[which]);
     src = bufs[which];
     n_cur = blocks * k;
     nd = nullptr;
     which ^= 1;
   }
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   block_k_smallest_kernel<<<1, 1024, 0, s>>>(src, n_cur, nd, k, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cand_from_keys(const unsigned long long* keys, int k, uint32_t out_base, uint32_t* cand,
                                   uint32_t* n_cand, cudaStream_t s) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   cand_from_keys_kernel<<<blocks_for(k, 256), 256, 0, s>>>(keys, k, out_base, cand, n_cand);
   return cudaGetLastError();
 }
@@ -602,6 +625,7 @@ cudaError_t launch_cand_from_keys(const unsigned long long* keys, int k, uint32_
 cudaError_t launch_score_grid(const ScoreDesc& d, const uint32_t* cand, const uint32_t* n_cand, int n_max,
                               cudaStream_t s) {
   const int blocks = std::min(blocks_for((long long)n_max * 32, 256), 148 * 16);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   score_grid_kernel<<<blocks, 256, 0, s>>>(d, cand, n_cand);
   return cudaGetLastError();
 }
@@ -609,6 +633,7 @@ cudaError_t launch_score_grid(const ScoreDesc& d, const uint32_t* cand, const ui
 cudaError_t launch_score_brute(const ScoreDesc& d, const uint32_t* cand, const uint32_t* n_cand, int n_max,
                                cudaStream_t s) {
   const int blocks = std::min(std::max(n_max, 1), 148 * 8);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   score_brute_kernel<<<blocks, kBruteThreads, 0, s>>>(d, cand, n_cand);
   return cudaGetLastError();
 }
@@ -617,27 +642,35 @@ cudaError_t launch_argmin(float* cost, const uint32_t* Mout, int N, int metric, 
                           const uint32_t* n_cand, int n_max, uint32_t out_base, unsigned long long* best,
                           cudaStream_t s) {
   const int blocks = std::min(blocks_for(n_max, 256), 148 * 4);
-  if (metric == 0) inlier_cost_kernel<<<blocks, 256, 0, s>>>(Mout, N, cand, n_cand, cost);
+  if (metric == 0) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    inlier_cost_kernel<<<blocks, 256, 0, s>>>(Mout, N, cand, n_cand, cost);
+  }
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   argmin_kernel<<<blocks, 256, 0, s>>>(cost, cand, n_cand, out_base, best);
   return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(const FinalDesc* d_dev, int count, cudaStream_t s) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   finalize_kernel<<<blocks_for(count, 64), 64, 0, s>>>(d_dev, count);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fill_u32(uint32_t* p, uint32_t v, size_t n, cudaStream_t s) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   fill_u32_kernel<<<std::min(blocks_for((long long)n, 256), 4096), 256, 0, s>>>(p, v, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fill_f32(float* p, float v, size_t n, cudaStream_t s) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   fill_f32_kernel<<<std::min(blocks_for((long long)n, 256), 4096), 256, 0, s>>>(p, v, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fill_u64(unsigned long long* p, unsigned long long v, size_t n, cudaStream_t s) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   fill_u64_kernel<<<std::min(blocks_for((long long)n, 256), 4096), 256, 0, s>>>(p, v, n);
   return cudaGetLastError();
 }

@@ -93,6 +93,7 @@ struct Options {
   int64_t serve_queue_cap = 100000;
   int64_t serve_mem_budget = 8LL << 30;
   int64_t serve_tile_rotations = 8192;
+  int64_t record_timing = 0;
 };
 
 }  // namespace
@@ -138,6 +139,11 @@ struct dses_ctx {
   bool worker_started = false;
   dses_result* pinned_res = nullptr;  // result staging for blocking calls
   size_t pinned_cap = 0;
+  // optional event timing of rotation-pass launches (record_timing = 1)
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pass_events;
+  int64_t pass_ns = 0;     // summed duration of the last call's pass launches
+  int64_t pass_launches = 0;
+  int64_t launch_snapshot = 0;
 };
 
 namespace {
@@ -570,7 +576,17 @@ void launch_pass(dses_ctx* c, const std::vector<PassPart>& parts, int P) {
   L.work_counter = (int*)(base + db + pb);
   L.hist_bytes = hist;
   const int ctas = std::max(1, std::min(c->sms, prefix.back()));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->opt.record_timing) {
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, s));
+  }
   CK(launch_rotation_pass(L, P, ctas, s));
+  if (e0) {
+    CK(cudaEventRecord(e1, s));
+    c->pass_events.push_back({e0, e1});
+  }
   m.release();
 }
 
@@ -856,6 +872,21 @@ dses_status guard(dses_ctx* c, F&& f) {
   }
 }
 
+// Sum the recorded pass-launch durations (after the stream has drained).
+void collect_timing(dses_ctx* c) {
+  if (c->pass_events.empty()) return;
+  double ms_total = 0;
+  for (auto& e : c->pass_events) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, e.first, e.second) == cudaSuccess) ms_total += ms;
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  c->pass_ns = (int64_t)(ms_total * 1e6);
+  c->pass_launches = (int64_t)c->pass_events.size();
+  c->pass_events.clear();
+}
+
 dses_status finish_results(dses_ctx* c, std::vector<Job*>& jobs, dses_result* out) {
   if (c->pinned_cap < jobs.size()) {
     if (c->pinned_res) cudaFreeHost(c->pinned_res);
@@ -868,6 +899,7 @@ dses_status finish_results(dses_ctx* c, std::vector<Job*>& jobs, dses_result* ou
   for (size_t i = 0; i < jobs.size(); ++i)
     CK(cudaMemcpyAsync(pinned + i, jobs[i]->res, sizeof(dses_result), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  collect_timing(c);
   dses_status st = DSES_OK;
   for (size_t i = 0; i < jobs.size(); ++i) {
     out[i] = pinned[i];
@@ -1207,6 +1239,13 @@ static int64_t* option_slot(dses_ctx* c, const char* key) {
   if (k == "serve_queue_cap") return &o.serve_queue_cap;
   if (k == "serve_mem_budget") return &o.serve_mem_budget;
   if (k == "serve_tile_rotations") return &o.serve_tile_rotations;
+  if (k == "record_timing") return &o.record_timing;
+  if (k == "last_pass_ns") return &c->pass_ns;
+  if (k == "last_pass_launches") return &c->pass_launches;
+  if (k == "kernel_launches") {
+    c->launch_snapshot = kernel_launch_count();
+    return &c->launch_snapshot;
+  }
   return nullptr;
 }
 
@@ -1221,7 +1260,10 @@ dses_status dses_set_option(dses_ctx* c, const char* key, int64_t value) {
     if (k == "hist_mode") ok = value >= 0 && value <= 2;
     else if (k == "hist_budget_bytes") ok = value >= 1024 && value <= kHistBudget;
     else if (k == "points_per_thread") ok = value == 0 || value == 1 || value == 2 || value == 4 || value == 8;
-    else if (k == "fuse_score" || k == "autotune" || k == "use_graphs") ok = value == 0 || value == 1;
+    else if (k == "fuse_score" || k == "autotune" || k == "use_graphs" || k == "record_timing")
+      ok = value == 0 || value == 1;
+    else if (k == "last_pass_ns" || k == "last_pass_launches" || k == "kernel_launches")
+      ok = false;  // read-only
     else if (k == "tile_rotations") ok = value >= 0 && value <= 4096;
     else ok = value >= 1;
     if (!ok) invalid("option value out of range for " + k);

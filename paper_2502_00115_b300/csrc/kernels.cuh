@@ -156,6 +156,9 @@ struct FinalDesc {
 };
 cudaError_t launch_finalize(const FinalDesc* d_dev, int count, cudaStream_t s);
 
+// Kernels launched by this library since it was loaded (all launch sites count).
+long long kernel_launch_count();
+
 cudaError_t launch_fill_u32(uint32_t* p, uint32_t v, size_t n, cudaStream_t s);
 cudaError_t launch_fill_f32(float* p, float v, size_t n, cudaStream_t s);
 cudaError_t launch_fill_u64(unsigned long long* p, unsigned long long v, size_t n, cudaStream_t s);

@@ -22,7 +22,12 @@
 
 #include "kernels.cuh"
 
+#include <atomic>
+
 namespace dses {
+
+extern std::atomic<long long> g_launches;
+
 namespace {
 
 // floor(v) for |v| < 2^22: adding 1.5 * 2^23 rounding toward -inf leaves
@@ -340,6 +345,7 @@ cudaError_t launch_p(const PassLaunch& L, int grid_ctas, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     configured = smem;
   }
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   rotation_pass_kernel<P><<<grid_ctas, kPassThreads, smem, s>>>(L);
   return cudaGetLastError();
 }

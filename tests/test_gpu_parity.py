@@ -1,0 +1,411 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Small cases compare every rotation; the full-size ModelNet-shaped problem
+(294,912 rotations, the benchmark's launch configuration) compares sampled
+rotations the oracle can evaluate one by one. See tests/parity.py for the
+tolerance rules.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2502_00115_b300 import build, capi, synth
+from parity import Report, check_rotations, cost_close
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    build.build()
+    c = capi.Context(0)
+    yield c
+    c.close()
+
+
+def gpu_params(p, **over):
+    kw = dict(metric=p.metric, epsilon=p.epsilon, delta_t=p.delta_t, tau=p.tau, huber_h=p.huber_h,
+              t_center=p.t_center, t_half=p.t_half, q_milli=p.q_milli, top_k=p.top_k,
+              refine_top_k=p.refine_top_k, refine_K=p.refine_K, refine_delta_r=p.refine_delta_r)
+    kw.update(over)
+    return capi.make_params(**kw)
+
+
+def oracle_params(p, gp, grid_cap):
+    """Oracle parameters from the exact FP32 values the GPU received."""
+    return oracle.make_params(
+        metric=gp.metric, epsilon=float(np.float32(gp.epsilon)),
+        delta_t=float(np.float32(gp.delta_t if gp.delta_t > 0 else gp.epsilon)),
+        tau=float(np.float32(gp.tau if gp.tau > 0 else 2 * gp.epsilon)),
+        huber_h=float(np.float32(gp.huber_h if gp.huber_h > 0 else gp.epsilon)), p=float(np.float32(gp.p)),
+        t_center=[float(v) for v in gp.t_center], t_half=[float(v) for v in gp.t_half], q_milli=gp.q_milli,
+        top_k=gp.top_k, nn_mode=gp.nn_mode, grid_res=128, grid_cap=float(np.float32(grid_cap)),
+        refine_top_k=gp.refine_top_k, refine_K=gp.refine_K, refine_delta_r=gp.refine_delta_r)
+
+
+# ---------------------------------------------------------------------------
+# grids and target preprocessing
+
+
+@pytest.mark.parametrize("n", [1, 2, 4, 10, 16])
+def test_hopf_grid_matches_oracle(ctx, n):
+    Rg = ctx.rotation_grid(capi.hopf_grid(n)).astype(np.float64)
+    Ro = oracle.hopf_grid(n)
+    assert Rg.shape == Ro.shape
+    assert np.abs(Rg - Ro).max() <= 1e-6
+
+
+def test_euler_box_matches_oracle(ctx):
+    from scipy.spatial.transform import Rotation
+
+    R0 = Rotation.random(random_state=3).as_matrix()
+    Rg = ctx.rotation_grid(capi.euler_box_grid(R0, 3, math.radians(0.3125))).astype(np.float64)
+    Ro = oracle.euler_box(R0, 3, math.radians(0.3125))
+    assert np.abs(Rg - Ro).max() <= 1e-6
+
+
+def test_distance_grid_matches_oracle(ctx):
+    p = synth.tiny_problem(2)
+    cap = 0.08
+    t = ctx.create_target(p.Y, grid_cap=cap, grid_res=40)
+    D, lo, h, gcap = ctx.distance_grid(t)
+    g = oracle.dist_grid(p.Y, 40, float(np.float32(cap)))
+    np.testing.assert_allclose(lo, g.lo, rtol=0, atol=1e-6)
+    np.testing.assert_allclose(h, g.h, rtol=1e-6)
+    assert np.abs(D - g.D).max() <= 2e-6
+    assert gcap == np.float32(cap)
+    ctx.destroy_target(t)
+
+
+# ---------------------------------------------------------------------------
+# every rotation of the tiny problem
+
+
+def _run_tiny(ctx, seed, metric, nn_mode, hopf_n=4, **over):
+    p = synth.tiny_problem(seed, hopf_n=hopf_n)
+    cap = 2 * p.tau
+    t = ctx.create_target(p.Y, grid_cap=cap)
+    gp = gpu_params(p, metric=metric, nn_mode=nn_mode, **over)
+    pb = ctx.problem(t, p.X, capi.hopf_grid(hopf_n), gp)
+    P = oracle_params(p, gp, cap)
+    n_rot = 72 * hopf_n**3
+    if gp.refine_top_k:
+        n_rot += gp.refine_top_k * (2 * gp.refine_K + 1) ** 3
+    k, V, M, C, r = ctx.debug(pb, n_rot)
+    return p, t, pb, P, k, V, M, C, r
+
+
+@pytest.mark.parametrize("metric,nn", [("trunc_l1", "grid"), ("inlier", "grid"), ("trunc_l2", "brute"),
+                                       ("huber", "grid"), ("lp", "brute")])
+def test_tiny_every_rotation_matches_oracle(ctx, metric, nn):
+    p, t, pb, P, k, V, M, C, r = _run_tiny(ctx, 0, metric, nn, p=0.5)
+    grid = oracle.hopf_grid(p.hopf_n)
+    ref = oracle.register(p.X, p.Y, grid, P)
+    g = oracle.dist_grid(p.Y, 128, P.grid_cap) if nn == "grid" and metric != "inlier" else None
+    rep = check_rotations(p.X, p.Y, grid, P, k, V, M, C, range(len(grid)), ref=ref, dist_grid=g)
+    assert rep.ok(), rep.summary()
+    assert rep.vote_exact >= 0.98 * rep.checked, rep.summary()
+    assert np.all(np.isfinite(C))  # every rotation is a candidate (q = 0)
+    # best rotation: exact, or a near-tie of the oracle's costs
+    assert r.status == 0
+    if r.rot_index != ref.rot_index:
+        assert cost_close(ref.costs[r.rot_index], ref.costs[ref.rot_index], 1), (r.rot_index, ref.rot_index)
+    ctx.destroy_target(t)
+
+
+@pytest.mark.parametrize("over", [dict(q_milli=900), dict(top_k=20), dict(q_milli=500, nn_mode="brute")])
+def test_tiny_candidate_filters_match_oracle(ctx, over):
+    nn = over.pop("nn_mode", "grid")
+    p, t, pb, P, k, V, M, C, r = _run_tiny(ctx, 1, "trunc_l1", nn, **over)
+    grid = oracle.hopf_grid(p.hopf_n)
+    ref = oracle.register(p.X, p.Y, grid, P)
+    g = oracle.dist_grid(p.Y, 128, P.grid_cap) if nn == "grid" else None
+    rep = check_rotations(p.X, p.Y, grid, P, k, V, M, C, range(len(grid)), ref=ref, dist_grid=g)
+    assert rep.ok(), rep.summary()
+    cand_gpu = set(np.flatnonzero(np.isfinite(C)).tolist())
+    cand_ref = set(np.flatnonzero(np.isfinite(ref.costs)).tolist())
+    if rep.m_excused == 0 and rep.vote_excused == 0:
+        assert cand_gpu == cand_ref
+    else:
+        assert len(cand_gpu ^ cand_ref) <= rep.m_excused + rep.vote_excused
+    if r.rot_index != ref.rot_index:
+        assert cost_close(ref.costs[r.rot_index], ref.costs[ref.rot_index], 1)
+    ctx.destroy_target(t)
+
+
+def test_tiny_refinement_pass_matches_oracle(ctx):
+    over = dict(refine_top_k=4, refine_K=1, refine_delta_r=math.radians(3.0))
+    p, t, pb, P, k, V, M, C, r = _run_tiny(ctx, 2, "trunc_l1", "brute", hopf_n=2, **over)
+    grid = oracle.hopf_grid(2)
+    ref = oracle.register(p.X, p.Y, grid, P)
+    # the oracle's second-pass rotations, rebuilt from its own coarse ranking
+    order = sorted(np.flatnonzero(np.isfinite(ref.costs[: len(grid)])), key=lambda i: (ref.costs[i], i))[:4]
+    fine = np.concatenate([oracle.euler_box(grid[c], 1, math.radians(3.0)) for c in order])
+    allR = np.concatenate([grid, fine])
+    rep = check_rotations(p.X, p.Y, allR, P, k, V, M, C, range(len(allR)), ref=ref)
+    assert rep.ok(), rep.summary()
+    assert r.rot_index == ref.rot_index or cost_close(ref.costs[r.rot_index], ref.costs[ref.rot_index], 1)
+    assert r.cost <= np.nanmin(C[: len(grid)]) + 1e-7
+    ctx.destroy_target(t)
+
+
+def test_histogram_modes_and_launch_shapes_agree(ctx):
+    # dense 32-bit, packed 16-bit and slabbed histograms, every points-per-thread
+    # variant and fused / separate scoring give identical per-rotation results
+    p = synth.modelnet_like_problem(5, m=300, keep=0.7, hopf_n=3)
+    t = ctx.create_target(p.Y, grid_cap=2 * p.tau)
+    gp = gpu_params(p, nn_mode="grid")
+    pb = ctx.problem(t, p.X, capi.hopf_grid(3), gp)
+    n = 72 * 27
+    base = ctx.debug(pb, n)
+    variants = [dict(hist_mode=1), dict(hist_mode=2), dict(hist_mode=1, hist_budget_bytes=20000),
+                dict(hist_mode=2, hist_budget_bytes=9000), dict(points_per_thread=1), dict(points_per_thread=2),
+                dict(points_per_thread=8), dict(fuse_score=0), dict(tile_rotations=1)]
+    defaults = {k: ctx.get_option(k) for k in ("hist_mode", "hist_budget_bytes", "points_per_thread", "fuse_score",
+                                               "tile_rotations")}
+    try:
+        for v in variants:
+            for key, val in v.items():
+                ctx.set_option(key, val)
+            k, V, M, C, r = ctx.debug(pb, n)
+            assert np.array_equal(k, base[0]) and np.array_equal(V, base[1]) and np.array_equal(M, base[2]), v
+            np.testing.assert_allclose(C, base[3], rtol=2e-6, err_msg=str(v))
+            assert r.rot_index == base[4].rot_index, v
+            for key, val in defaults.items():
+                ctx.set_option(key, val)
+    finally:
+        for key, val in defaults.items():
+            ctx.set_option(key, val)
+    ctx.destroy_target(t)
+
+
+# ---------------------------------------------------------------------------
+# the full-size ModelNet-shaped problem (benchmark configuration), sampled
+
+
+def test_modelnet_full_size_sampled_rotations(ctx):
+    p = synth.modelnet_like_problem(0)
+    cap = 2 * p.tau
+    t = ctx.create_target(p.Y, grid_cap=cap)
+    gp = gpu_params(p, nn_mode="grid")
+    pb = ctx.problem(t, p.X, capi.hopf_grid(p.hopf_n), gp)
+    n = 72 * p.hopf_n**3
+    k, V, M, C, r = ctx.debug(pb, n)
+    assert r.status == 0 and np.all(np.isfinite(C))
+    assert r.rot_index == int(np.lexsort((np.arange(n), C))[0])  # argmin of (cost, index)
+    P = oracle_params(p, gp, cap)
+    rng = np.random.default_rng(0)
+    idx = sorted(set(rng.choice(n, size=40, replace=False).tolist()) | {r.rot_index, int(np.argmax(M))})
+    Rs = np.stack([oracle.hopf_rotation(p.hopf_n, i) for i in idx])
+    g = oracle.dist_grid(p.Y, 128, P.grid_cap)
+    rep = check_rotations(p.X, p.Y, Rs, P, k, V, M, C, idx, dist_grid=g)
+    assert rep.ok(), rep.summary()
+    # the winner is a plausible pose (grid resolution ~3.75 degrees)
+    ang = np.degrees(np.arccos(np.clip((np.trace(np.array(r.R[:]).reshape(3, 3).T @ p.R_true) - 1) / 2, -1, 1)))
+    assert ang < 10.0, ang
+    ctx.destroy_target(t)
+
+
+# ---------------------------------------------------------------------------
+# batching, special cases, invariances
+
+
+def test_batch_equals_solo(ctx):
+    probs = [synth.tiny_problem(s, hopf_n=2 + (s % 2)) for s in range(3)]
+    probs.append(synth.modelnet_like_problem(9, m=517, keep=0.55, hopf_n=2))
+    targets = [ctx.create_target(p.Y, grid_cap=2 * p.tau) for p in probs]
+    pbs = [ctx.problem(t, p.X, capi.hopf_grid(p.hopf_n), gpu_params(p, nn_mode="grid"))
+           for t, p in zip(targets, probs)]
+    solo = [capi.result_dict(ctx.register(pb)) for pb in pbs]
+    batch = [capi.result_dict(r) for r in ctx.register_batch(pbs)]
+    for a, b in zip(solo, batch):
+        assert a["rot_index"] == b["rot_index"] and a["inliers"] == b["inliers"] and a["votes"] == b["votes"]
+        assert np.array_equal(a["t"], b["t"]) and a["cost"] == b["cost"] and a["status"] == b["status"] == 0
+    for t in targets:
+        ctx.destroy_target(t)
+
+
+def test_theorem_case_exact_recovery_on_gpu(ctx):
+    rng = np.random.default_rng(8)
+    delta = 0.05
+    Y = synth.dyadic_cloud(rng, 80, extent=0.8, min_sep_inf=delta)
+    grid = oracle.hopf_grid(3)
+    r_true = int(rng.integers(len(grid)))
+    k_true = np.array([2, -3, 4])
+    sub = Y[rng.choice(80, size=30, replace=False)]
+    X = (sub - k_true * delta) @ grid[r_true]
+    t = ctx.create_target(Y, grid_cap=0.2)
+    for metric in ("inlier", "trunc_l1"):
+        gp = capi.make_params(metric=metric, epsilon=delta, tau=0.1, t_half=(0.5, 0.5, 0.5))
+        r = ctx.register(ctx.problem(t, X, capi.hopf_grid(3), gp))
+        assert r.status == 0 and r.rot_index == r_true and r.inliers == 30 and r.votes == 30
+        np.testing.assert_allclose(r.t[:], k_true * delta, atol=1e-6)
+    ctx.destroy_target(t)
+
+
+def test_single_source_point_and_ragged_sizes(ctx):
+    rng = np.random.default_rng(3)
+    for N, M in [(1, 40), (3, 129), (257, 1000), (1500, 2050)]:
+        Y = rng.uniform(-0.6, 0.6, size=(M, 3)).astype(np.float32)
+        X = rng.uniform(-0.4, 0.4, size=(N, 3)).astype(np.float32)
+        t = ctx.create_target(Y, grid_cap=0.1)
+        gp = capi.make_params(metric="trunc_l1", epsilon=0.05, tau=0.05, t_half=(0.4, 0.4, 0.4), nn_mode="brute")
+        pb = ctx.problem(t, X, capi.hopf_grid(1), gp)
+        k, V, Mg, C, r = ctx.debug(pb, 72)
+        P = oracle_params(None, gp, 0.1)
+        grid = oracle.hopf_grid(1)
+        ref = oracle.register(X, Y, grid, P)
+        rep = check_rotations(X, Y, grid, P, k, V, Mg, C, range(72), ref=ref)
+        assert rep.ok(), (N, M, rep.summary())
+        if N == 1:
+            assert V.max() == 1
+        ctx.destroy_target(t)
+
+
+def test_no_vote_inside_the_box_reports_no_candidate(ctx):
+    Y = np.array([[5.0, 5.0, 5.0], [6.0, 5.0, 5.0], [5.0, 6.0, 5.0]], dtype=np.float32)
+    X = np.zeros((4, 3), dtype=np.float32) + np.arange(4, dtype=np.float32)[:, None] * 0.01
+    t = ctx.create_target(Y, grid_cap=0.1)
+    gp = capi.make_params(metric="trunc_l1", epsilon=0.05, tau=0.05, t_half=(0.2, 0.2, 0.2))
+    r = ctx.register(ctx.problem(t, X, capi.hopf_grid(1), gp))
+    assert r.status == capi.DSES_ERR_NO_CANDIDATE and r.votes == 0
+    ctx.destroy_target(t)
+
+
+def test_explicit_and_euler_grids_match_oracle(ctx):
+    p = synth.tiny_problem(4, hopf_n=2)
+    t = ctx.create_target(p.Y, grid_cap=2 * p.tau)
+    gp = gpu_params(p, nn_mode="brute")
+    P = oracle_params(p, gp, 2 * p.tau)
+    from scipy.spatial.transform import Rotation
+
+    Rx = Rotation.random(50, random_state=1).as_matrix()
+    g, keep = capi.explicit_grid(Rx)
+    k, V, M, C, r = ctx.debug(ctx.problem(t, p.X, g, gp), 50)
+    ref = oracle.register(p.X, p.Y, Rx.astype(np.float32).astype(np.float64), P)
+    rep = check_rotations(p.X, p.Y, Rx.astype(np.float32).astype(np.float64), P, k, V, M, C, range(50), ref=ref)
+    assert rep.ok(), rep.summary()
+    eg = capi.euler_box_grid(p.R_true, 2, math.radians(4))
+    k, V, M, C, r = ctx.debug(ctx.problem(t, p.X, eg, gp), 125)
+    Re = oracle.euler_box(p.R_true, 2, math.radians(4))
+    ref = oracle.register(p.X, p.Y, Re, P)
+    rep = check_rotations(p.X, p.Y, Re, P, k, V, M, C, range(125), ref=ref)
+    assert rep.ok(), rep.summary()
+    ctx.destroy_target(t)
+
+
+def test_device_pointers_match_host_pointers(ctx):
+    torch = pytest.importorskip("torch")
+    p = synth.tiny_problem(6, hopf_n=2)
+    Yd = torch.from_numpy(p.Y).cuda()
+    Xd = torch.from_numpy(p.X).cuda()
+    torch.cuda.synchronize()
+    t1 = ctx.create_target(p.Y, grid_cap=2 * p.tau)
+    t2 = ctx.create_target_device(Yd.data_ptr(), len(p.Y), grid_cap=2 * p.tau)
+    gp = gpu_params(p, nn_mode="grid")
+    a = capi.result_dict(ctx.register(ctx.problem(t1, p.X, capi.hopf_grid(2), gp)))
+    b = capi.result_dict(ctx.register(ctx.problem(t2, None, capi.hopf_grid(2), gp, src_ptr=Xd.data_ptr(),
+                                                  n_src=len(p.X))))
+    assert a["rot_index"] == b["rot_index"] and a["cost"] == b["cost"] and np.array_equal(a["t"], b["t"])
+    ctx.destroy_target(t1)
+    ctx.destroy_target(t2)
+
+
+def test_translation_equivariance_and_permutation_invariance(ctx):
+    rng = np.random.default_rng(12)
+    delta = 2.0**-5
+    Y = synth.dyadic_cloud(rng, 200, extent=0.7).astype(np.float32)
+    X = synth.dyadic_cloud(rng, 60, extent=0.5).astype(np.float32)
+    m = np.array([3, -2, 5])
+    base = capi.make_params(metric="trunc_l1", epsilon=delta, tau=0.06, t_half=(0.5, 0.5, 0.5), nn_mode="brute")
+    shifted = capi.make_params(metric="trunc_l1", epsilon=delta, tau=0.06, t_center=tuple(m * delta),
+                               t_half=(0.5, 0.5, 0.5), nn_mode="brute")
+    t1 = ctx.create_target(Y, grid_cap=0.2)
+    t2 = ctx.create_target((Y + m * delta).astype(np.float32), grid_cap=0.2)
+    k1, V1, M1, C1, r1 = ctx.debug(ctx.problem(t1, X, capi.hopf_grid(2), base), 576)
+    k2, V2, M2, C2, r2 = ctx.debug(ctx.problem(t2, X, capi.hopf_grid(2), shifted), 576)
+    same = np.all(k2 - k1 == m, axis=1) & (V1 == V2)
+    assert same.mean() > 0.99
+    assert r1.rot_index == r2.rot_index
+    perm_x, perm_y = rng.permutation(len(X)), rng.permutation(len(Y))
+    t3 = ctx.create_target(Y[perm_y], grid_cap=0.2)
+    k3, V3, M3, C3, r3 = ctx.debug(ctx.problem(t3, X[perm_x], capi.hopf_grid(2), base), 576)
+    assert np.array_equal(k3, k1) and np.array_equal(V3, V1) and np.array_equal(M3, M1)
+    np.testing.assert_allclose(C3, C1, rtol=1e-5)
+    assert r3.rot_index == r1.rot_index
+    for t in (t1, t2, t3):
+        ctx.destroy_target(t)
+
+
+def test_invalid_arguments_leave_the_context_usable(ctx):
+    p = synth.tiny_problem(0, hopf_n=1)
+    t = ctx.create_target(p.Y, grid_cap=2 * p.tau)
+    bad = capi.make_params(metric="trunc_l1", epsilon=-1.0)
+    st, _ = capi.dses_register(ctx.h, ctx.problem(t, p.X, capi.hopf_grid(1), bad))
+    assert st == capi.DSES_ERR_INVALID_ARG and "epsilon" in capi.dses_last_error(ctx.h)
+    st, _ = capi.dses_register(ctx.h, ctx.problem(t, p.X, capi.hopf_grid(0), gpu_params(p)))
+    assert st == capi.DSES_ERR_INVALID_ARG
+    small_cap = capi.make_params(metric="trunc_l1", epsilon=0.02, tau=1.0)
+    st, _ = capi.dses_register(ctx.h, ctx.problem(t, p.X, capi.hopf_grid(1), small_cap))
+    assert st == capi.DSES_ERR_INVALID_ARG
+    assert capi.dses_set_option(ctx.h, "no_such_option", 1) == capi.DSES_ERR_INVALID_ARG
+    r = ctx.register(ctx.problem(t, p.X, capi.hopf_grid(1), gpu_params(p)))
+    assert r.status == 0
+    ctx.destroy_target(t)
+
+
+def test_forced_16bit_counters_refused_when_they_could_overflow(ctx):
+    rng = np.random.default_rng(0)
+    Y = (rng.normal(scale=0.001, size=(3000, 3))).astype(np.float32)  # every point in one voxel
+    X = (rng.normal(scale=0.001, size=(100, 3))).astype(np.float32)
+    t = ctx.create_target(Y, grid_cap=0.1)
+    ctx.set_option("hist_mode", 2)
+    try:
+        st, _ = capi.dses_register(ctx.h, ctx.problem(t, X, capi.hopf_grid(1),
+                                                      capi.make_params(epsilon=0.05, tau=0.05)))
+        assert st == capi.DSES_ERR_INVALID_ARG
+    finally:
+        ctx.set_option("hist_mode", 0)
+    r = ctx.register(ctx.problem(t, X, capi.hopf_grid(1), capi.make_params(epsilon=0.05, tau=0.05)))
+    assert r.status == 0 and r.votes == 100 * 3000 or r.votes > 60000  # 32-bit counters hold it
+    ctx.destroy_target(t)
+
+
+# ---------------------------------------------------------------------------
+# serving: results alone and in the mix
+
+
+def test_serving_results_equal_solo(ctx):
+    import time
+
+    probs = [synth.tiny_problem(s, hopf_n=2 + (s % 3)) for s in range(6)]
+    targets = [ctx.create_target(p.Y, grid_cap=2 * p.tau) for p in probs]
+    pbs = [ctx.problem(t, p.X, capi.hopf_grid(p.hopf_n), gpu_params(p, nn_mode="grid"))
+           for t, p in zip(targets, probs)]
+    solo = [capi.result_dict(ctx.register(pb)) for pb in pbs]
+    ctx.set_option("serve_tile_rotations", 300)
+    try:
+        tickets = [ctx.submit(pb) for pb in pbs]
+        out = {}
+        deadline = time.time() + 60
+        while len(out) < len(tickets) and time.time() < deadline:
+            for tk in tickets:
+                if tk in out:
+                    continue
+                st, r = ctx.poll(tk)
+                if st != capi.DSES_NOT_READY:
+                    assert st == capi.DSES_OK
+                    out[tk] = capi.result_dict(r)
+            time.sleep(0.002)
+        assert len(out) == len(tickets)
+        assert capi.dses_poll(ctx.h, tickets[0])[0] == capi.DSES_ERR_UNKNOWN_TICKET
+    finally:
+        ctx.set_option("serve_tile_rotations", 8192)
+    for tk, a in zip(tickets, solo):
+        b = out[tk]
+        assert a["rot_index"] == b["rot_index"] and a["inliers"] == b["inliers"] and a["votes"] == b["votes"]
+        assert np.array_equal(a["t"], b["t"]) and a["cost"] == b["cost"]
+    for t in targets:
+        ctx.destroy_target(t)
