@@ -1,0 +1,309 @@
+#!/usr/bin/env python3
+"""DSES registration benchmark on B300.
+
+One step = one full registration (Algorithm 2: every rotation of the grid
+votes, counts inliers, is scored, and the argmin is returned) of the
+ModelNet-shaped synthetic problem: 1,024-point target, 717-point source (70%
+half-space crop), 294,912-rotation Hopf grid (N_side 16, ~3.75 degrees),
+truncated-L2 metric read from the target's 128^3 FP32 distance grid.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank registers its own problem of the same shape (weak
+scaling, no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "rotation-candidates x source-points / s"
+UNIT = "rot*pts/s"
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# recipe unit counts: 148 SMs x 128 FP32 lanes at the 2032 MHz maximum SM clock
+ALU_PEAK_OPS = 148 * 128 * 2032e6
+# algorithmic work of the rotation pass: per (rotation, source point, target
+# point) pair 3 FP32 operations and one shared-memory histogram increment; per
+# (rotation, source point) 15 FP32 operations (the rotation R x_i)
+OPS_PER_PAIR = 4
+OPS_PER_ROT_SRC = 15
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--hopf-n", type=int, default=16, help="grid N_side (16 = the benchmark; smaller for profiling)")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(ngpu_flag):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = tempfile.mktemp(prefix="clocks", suffix=".csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = [r.split(", ") for r in open(self.path).read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        mx = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows)}
+
+
+def workload(seed, hopf_n=16):
+    from paper_2502_00115_b300 import synth
+
+    return synth.modelnet_like_problem(seed, hopf_n=hopf_n)
+
+
+def config_dict(p):
+    R = 72 * p.hopf_n**3
+    return {"workload": "modelnet_like_single_problem", "target_points": int(len(p.Y)),
+            "source_points": int(len(p.X)), "rotations": R, "rotation_grid": f"hopf N_side={p.hopf_n}",
+            "metric": p.metric, "tau": p.tau, "epsilon": p.epsilon, "delta_t": p.delta_t,
+            "translation_box": f"+-{p.t_half[0]} per axis", "distance_grid": "128^3 fp32",
+            "l2": "flushed between steps (512 MB write)"}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference arm)
+
+
+def oracle_sample(p, target_s, threads):
+    """Time the FP64 oracle (Algorithm 2 on a rotation subset, prebuilt field)."""
+    import oracle
+
+    oracle.build()
+    R_all_n = p.hopf_n
+    P = oracle.params_from_problem(p, nn_mode="grid", grid_cap=2 * p.tau)
+    field = oracle.Field(p.Y, P.grid_res, P.grid_cap)
+    n_all = 72 * R_all_n**3
+
+    def run(count, offset=0):
+        stride = max(1, n_all // count)
+        idx = (np.arange(count) * stride + offset) % n_all
+        Rs = np.stack([oracle.hopf_rotation(R_all_n, int(i)) for i in idx])
+        t0 = time.perf_counter()
+        oracle.register_field_threads(p.X, p.Y, Rs, P, field, threads)
+        return time.perf_counter() - t0
+
+    probe = 4 * threads
+    dt = run(probe)
+    per_rot = dt / probe
+    count = int(max(probe, min(n_all, target_s / per_rot)))
+    return run, count, per_rot, field
+
+
+def cpu_baseline(p, target_s):
+    threads = os.cpu_count() or 1
+    run, count, per_rot, field = oracle_sample(p, target_s, threads)
+    dt = run(count, offset=1)
+    field.close()
+    return {"value": count * len(p.X) / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{count} of {72 * p.hopf_n**3} rotations (even stride) of the same problem, FP64 "
+                      f"Algorithm 2 fanned over {threads} threads, distance field prebuilt (not timed), {dt:.1f} s"}
+
+
+def reference_arm(args, ws, rank):
+    if rank != 0:
+        return
+    p = workload(args.seed, args.hopf_n)
+    threads = os.cpu_count() or 1
+    # each step: a bounded rotation sample sized to ~4 s so K + W steps stay within minutes
+    run, count, per_rot, field = oracle_sample(p, 4.0, threads)
+    for w in range(args.warmup):
+        run(count, offset=w + 1)
+    times = [run(count, offset=100 + k) for k in range(args.steps)]
+    field.close()
+    tot = sum(times)
+    value = args.steps * count * len(p.X) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(p),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{count} rotations per step (even stride, shifted per step) of "
+                                       f"{72 * p.hopf_n**3}; distance field prebuilt"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+
+
+def ours(args, ws, rank, local):
+    import torch
+
+    from paper_2502_00115_b300 import build, capi
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group(backend="nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or ws > 1:
+        build.build()
+    if dist:
+        dist.barrier()
+    p = workload(args.seed + rank, args.hopf_n)
+    n_rot = 72 * p.hopf_n**3
+    units = n_rot * len(p.X)
+    stream = torch.cuda.Stream()
+    ctx = capi.Context(local, stream.cuda_stream)
+    tgt = ctx.create_target(p.Y, grid_cap=2 * p.tau)
+    params = capi.make_params(metric=p.metric, epsilon=p.epsilon, delta_t=p.delta_t, tau=p.tau,
+                              huber_h=p.huber_h, t_half=p.t_half, nn_mode="grid")
+    grid = capi.hopf_grid(p.hopf_n)
+    Xd = torch.from_numpy(p.X).cuda()
+    Xh = torch.from_numpy(p.X).pin_memory()
+    torch.cuda.synchronize()
+    pb_dev = ctx.problem(tgt, None, grid, params, src_ptr=Xd.data_ptr(), n_src=len(p.X))
+    pb_host = ctx.problem(tgt, Xh.numpy(), grid, params)
+    pb_host.src = Xh.data_ptr()  # pinned host buffer
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    ctx.set_option("record_timing", 1)
+
+    for _ in range(args.warmup):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ctx.register(pb_dev)
+        ctx.register(pb_host)
+
+    # device-resident inputs, CUDA events on the library's stream
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    pass_ns = []
+    results = []
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = ctx.get_option("kernel_launches")
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ev[k][0].record(stream)
+        r = ctx.register(pb_dev)
+        ev[k][1].record(stream)
+        results.append(capi.result_dict(r))
+        pass_ns.append(ctx.get_option("last_pass_ns"))
+    torch.cuda.synchronize()
+    launches = ctx.get_option("kernel_launches") - launches0
+    if dist:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+
+    # end to end through the public API: pinned host source in, result out
+    e2e_s = []
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        stream.synchronize()
+        t0 = time.perf_counter()
+        ctx.register(pb_host)
+        e2e_s.append(time.perf_counter() - t0)
+    clk = clocks.stop()
+
+    if dist:
+        t = torch.tensor([total_ms, sum(e2e_s)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, e2e_tot = t.tolist()
+    else:
+        e2e_tot = sum(e2e_s)
+    ctx.close()
+    if rank != 0:
+        return
+    value = ws * args.steps * units / (total_ms / 1000)
+    pass_s = statistics.mean(pass_ns) / 1e9
+    M = len(p.Y)
+    ops = n_rot * len(p.X) * (M * OPS_PER_PAIR + OPS_PER_ROT_SRC)
+    achieved = ops / pass_s
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic", "config": config_dict(p),
+        "registrations_per_s": ws * args.steps / (total_ms / 1000),
+        "latency_ms": {"p50": 1000 * float(np.percentile(e2e_s, 50)), "p99": 1000 * float(np.percentile(e2e_s, 99))},
+        "roofline": {"bound": "alu", "kernel": "rotation_pass_kernel", "achieved": achieved / 1e12,
+                     "peak": ALU_PEAK_OPS / 1e12, "unit": "Tops/s", "frac": achieved / ALU_PEAK_OPS,
+                     "traffic": None, "pass_ms": pass_s * 1000,
+                     "peak_source": "recipe unit counts: 148 SMs x 128 lanes x 2032 MHz",
+                     "ops_per_launch": ops},
+        "e2e": {"value": ws * args.steps * units / e2e_tot, "unit": UNIT, "h2d_bytes_per_step": int(p.X.nbytes),
+                "d2h_bytes_per_step": 72},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "result": {k: (v.tolist() if hasattr(v, "tolist") else v) for k, v in results[-1].items()},
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        reference_arm(args, ws, rank)
+        return
+    ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -369,7 +369,7 @@ def test_forced_16bit_counters_refused_when_they_could_overflow(ctx):
     finally:
         ctx.set_option("hist_mode", 0)
     r = ctx.register(ctx.problem(t, X, capi.hopf_grid(1), capi.make_params(epsilon=0.05, tau=0.05)))
-    assert r.status == 0 and r.votes == 100 * 3000 or r.votes > 60000  # 32-bit counters hold it
+    assert r.status == 0 and r.votes > 65535  # 32-bit counters hold it
     ctx.destroy_target(t)
 
 
