@@ -46,8 +46,8 @@ struct Error {
   do {                                                                                        \
     cudaError_t e_ = (call);                                                                  \
     if (e_ != cudaSuccess) {                                                                  \
+      cudaGetLastError(); /* a non-sticky error must not poison the next launch check */      \
       if (e_ == cudaErrorMemoryAllocation) {                                                  \
-        cudaGetLastError();                                                                   \
         throw Error{DSES_ERR_OOM, std::string(#call) + ": " + cudaGetErrorString(e_)};        \
       }                                                                                       \
       throw Error{DSES_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};         \
@@ -1193,7 +1193,7 @@ dses_status dses_rotation_grid_build(dses_ctx* c, const dses_rotation_grid* grid
       CK(cudaMemcpyAsync(out_R, p, 36 * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
     } else {
       DevMem m;
-      m.alloc(36 * (size_t)n + 128, c->stream);
+      m.alloc(align256(36 * (size_t)n) + 256, c->stream);
       double* R0 = (double*)((char*)m.p + align256(36 * (size_t)n));
       CK(cudaMemcpyAsync(R0, grid->R0, 72, cudaMemcpyHostToDevice, c->stream));
       CK(launch_euler_box_single(R0, grid->K, grid->delta_r, (float*)m.p, c->stream));

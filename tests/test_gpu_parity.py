@@ -25,10 +25,10 @@ def ctx():
     c.close()
 
 
-def gpu_params(p, **over):
-    kw = dict(metric=p.metric, epsilon=p.epsilon, delta_t=p.delta_t, tau=p.tau, huber_h=p.huber_h,
-              t_center=p.t_center, t_half=p.t_half, q_milli=p.q_milli, top_k=p.top_k,
-              refine_top_k=p.refine_top_k, refine_K=p.refine_K, refine_delta_r=p.refine_delta_r)
+def gpu_params(prob, **over):
+    kw = dict(metric=prob.metric, epsilon=prob.epsilon, delta_t=prob.delta_t, tau=prob.tau, huber_h=prob.huber_h,
+              t_center=prob.t_center, t_half=prob.t_half, q_milli=prob.q_milli, top_k=prob.top_k,
+              refine_top_k=prob.refine_top_k, refine_K=prob.refine_K, refine_delta_r=prob.refine_delta_r)
     kw.update(over)
     return capi.make_params(**kw)
 
