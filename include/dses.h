@@ -206,11 +206,12 @@ dses_status dses_target_distance_grid(dses_ctx* ctx, const dses_target* target, 
  *   "serve_queue_cap"      submitted requests waiting for admission
  *   "serve_mem_budget"     device bytes the serving worker may hold for requests
  *   "serve_tile_rotations" rotations per request per serving iteration
- *   "record_timing"        1: time every rotation-pass launch with CUDA events on
- *                          the context's stream
- *   "last_pass_ns"         (read-only) summed duration of the rotation-pass
- *                          launches of the last blocking call, in nanoseconds
- *   "last_pass_launches"   (read-only) how many pass launches that call made
+ *   "record_timing"        1: time every rotation pass with CUDA events on the
+ *                          context's stream
+ *   "last_pass_ns"         (read-only) summed duration of the vote kernels of the
+ *                          last blocking call, in nanoseconds
+ *   "last_count_ns"        (read-only) the same for its inlier-count / score kernels
+ *   "last_pass_launches"   (read-only) how many rotation passes that call made
  *   "kernel_launches"      (read-only) kernels this library has launched in the
  *                          process so far (all contexts)
  * INVALID_ARG for an unknown key or a value out of range. */

@@ -140,8 +140,12 @@ struct dses_ctx {
   dses_result* pinned_res = nullptr;  // result staging for blocking calls
   size_t pinned_cap = 0;
   // optional event timing of rotation-pass launches (record_timing = 1)
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pass_events;
-  int64_t pass_ns = 0;     // summed duration of the last call's pass launches
+  struct PassEvents {
+    cudaEvent_t start, voted, counted;
+  };
+  std::vector<PassEvents> pass_events;
+  int64_t pass_ns = 0;     // summed duration of the last call's vote launches
+  int64_t count_ns = 0;    // ... and of its inlier-count / score launches
   int64_t pass_launches = 0;
   int64_t launch_snapshot = 0;
 };
@@ -547,7 +551,7 @@ void launch_pass(dses_ctx* c, const std::vector<PassPart>& parts, int P) {
   if (parts.empty()) return;
   cudaStream_t s = c->stream;
   std::vector<PassDesc> descs;
-  std::vector<int> prefix(1, 0);
+  std::vector<int> prefix(1, 0), rprefix(1, 0);
   int64_t total_rot = 0;
   int hist = 16;
   for (auto& pp : parts) total_rot += pp.r1 - pp.r0;
@@ -559,33 +563,37 @@ void launch_pass(dses_ctx* c, const std::vector<PassPart>& parts, int P) {
     d.n_rot = (int)(pp.r1 - pp.r0);
     descs.push_back(d);
     prefix.push_back(prefix.back() + (int)((d.n_rot + tile - 1) / tile));
+    rprefix.push_back(rprefix.back() + d.n_rot);
     hist = std::max(hist, pp.job->hist_bytes);
   }
   const size_t db = align256(sizeof(PassDesc) * descs.size()), pb = align256(sizeof(int) * prefix.size());
   DevMem m;
-  m.alloc(db + pb + 256, s);
+  m.alloc(db + 2 * pb + 256, s);
   char* base = (char*)m.p;
   CK(cudaMemcpyAsync(base, descs.data(), sizeof(PassDesc) * descs.size(), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(base + db, prefix.data(), sizeof(int) * prefix.size(), cudaMemcpyHostToDevice, s));
-  CK(cudaMemsetAsync(base + db + pb, 0, 4, s));
+  CK(cudaMemcpyAsync(base + db + pb, rprefix.data(), sizeof(int) * rprefix.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(base + db + 2 * pb, 0, 4, s));
   PassLaunch L;
   L.probs = (const PassDesc*)base;
   L.tile_prefix = (const int*)(base + db);
+  L.rot_prefix = (const int*)(base + db + pb);
   L.n_probs = (int)descs.size();
   L.tile_rot = tile;
-  L.work_counter = (int*)(base + db + pb);
+  L.work_counter = (int*)(base + db + 2 * pb);
   L.hist_bytes = hist;
   const int ctas = std::max(1, std::min(c->sms, prefix.back()));
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   if (c->opt.record_timing) {
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
-    CK(cudaEventRecord(e0, s));
+    for (auto& e : ev) CK(cudaEventCreate(&e));
+    CK(cudaEventRecord(ev[0], s));
   }
-  CK(launch_rotation_pass(L, P, ctas, s));
-  if (e0) {
-    CK(cudaEventRecord(e1, s));
-    c->pass_events.push_back({e0, e1});
+  CK(launch_vote(L, P, ctas, s));
+  if (ev[0]) CK(cudaEventRecord(ev[1], s));
+  CK(launch_count(L, (int)total_rot, s));
+  if (ev[0]) {
+    CK(cudaEventRecord(ev[2], s));
+    c->pass_events.push_back({ev[0], ev[1], ev[2]});
   }
   m.release();
 }
@@ -875,14 +883,17 @@ dses_status guard(dses_ctx* c, F&& f) {
 // Sum the recorded pass-launch durations (after the stream has drained).
 void collect_timing(dses_ctx* c) {
   if (c->pass_events.empty()) return;
-  double ms_total = 0;
+  double vote_ms = 0, count_ms = 0;
   for (auto& e : c->pass_events) {
-    float ms = 0;
-    if (cudaEventElapsedTime(&ms, e.first, e.second) == cudaSuccess) ms_total += ms;
-    cudaEventDestroy(e.first);
-    cudaEventDestroy(e.second);
+    float a = 0, b = 0;
+    if (cudaEventElapsedTime(&a, e.start, e.voted) == cudaSuccess) vote_ms += a;
+    if (cudaEventElapsedTime(&b, e.voted, e.counted) == cudaSuccess) count_ms += b;
+    cudaEventDestroy(e.start);
+    cudaEventDestroy(e.voted);
+    cudaEventDestroy(e.counted);
   }
-  c->pass_ns = (int64_t)(ms_total * 1e6);
+  c->pass_ns = (int64_t)(vote_ms * 1e6);
+  c->count_ns = (int64_t)(count_ms * 1e6);
   c->pass_launches = (int64_t)c->pass_events.size();
   c->pass_events.clear();
 }
@@ -1242,6 +1253,7 @@ static int64_t* option_slot(dses_ctx* c, const char* key) {
   if (k == "record_timing") return &o.record_timing;
   if (k == "last_pass_ns") return &c->pass_ns;
   if (k == "last_pass_launches") return &c->pass_launches;
+  if (k == "last_count_ns") return &c->count_ns;
   if (k == "kernel_launches") {
     c->launch_snapshot = kernel_launch_count();
     return &c->launch_snapshot;
@@ -1262,7 +1274,7 @@ dses_status dses_set_option(dses_ctx* c, const char* key, int64_t value) {
     else if (k == "points_per_thread") ok = value == 0 || value == 1 || value == 2 || value == 4 || value == 8;
     else if (k == "fuse_score" || k == "autotune" || k == "use_graphs" || k == "record_timing")
       ok = value == 0 || value == 1;
-    else if (k == "last_pass_ns" || k == "last_pass_launches" || k == "kernel_launches")
+    else if (k == "last_pass_ns" || k == "last_pass_launches" || k == "kernel_launches" || k == "last_count_ns")
       ok = false;  // read-only
     else if (k == "tile_rotations") ok = value >= 0 && value <= 4096;
     else ok = value >= 1;

@@ -19,7 +19,7 @@ constexpr int kPassStaticSmem = 2048;
 // Histogram budget: what is left after the source chunk and static storage.
 constexpr int kHistBudget = kMaxSmem - kSrcChunk * 16 - kPassStaticSmem;
 
-// Everything the rotation pass needs for one registration problem.
+// Everything the rotation pass (vote + count kernels) needs for one problem.
 struct PassDesc {
   // inputs (device)
   const float* X;        // N x 3 source points
@@ -64,14 +64,17 @@ struct PassDesc {
 struct PassLaunch {
   const PassDesc* probs;   // device array
   const int* tile_prefix;  // device, n_probs + 1 prefix sums of tiles
+  const int* rot_prefix;   // device, n_probs + 1 prefix sums of rotations
   int n_probs;
   int tile_rot;            // rotations per work item
   int* work_counter;       // device, zeroed before the launch
   int hist_bytes;          // histogram bytes of shared memory (max over problems)
 };
 
-// Hot path: vote -> argmax -> inlier count -> (fused) grid score per rotation.
-cudaError_t launch_rotation_pass(const PassLaunch& L, int points_per_thread, int grid_ctas, cudaStream_t s);
+// Hot path, kernel 1: vote -> mode (k*, V) per rotation (persistent, one CTA per SM).
+cudaError_t launch_vote(const PassLaunch& L, int points_per_thread, int grid_ctas, cudaStream_t s);
+// Kernel 2: inlier count M at t* and, on the fused path, grid score + argmin.
+cudaError_t launch_count(const PassLaunch& L, int total_rot, cudaStream_t s);
 int pass_smem_bytes(int hist_bytes);
 
 // --- rotation grids (FP64 arithmetic, FP32 output) -------------------------

@@ -1,28 +1,29 @@
 // Rotation pass: the hot loop of Direct Semi-Exhaustive Search (Algorithm 2).
 //
-// For every rotation R of a work item, one CTA (32 warps, one CTA per SM):
-//   1. rotates the source cloud and stages per-point lattice offsets
-//      c_i = 1/2 - (R x_i)/delta - lo in shared memory;
-//   2. votes every pair (i, j): k = floor(y_j/delta + c_i) (the ROUND of
-//      Algorithm 2 relative to the box corner); pairs inside the lattice box
-//      increment a shared-memory histogram (Lemma 1, Eq. 5: the translation
-//      mode of the rotated pairwise differences);
+// vote_kernel -- one persistent CTA per SM (32 warps). For every rotation R of
+// a work item it
+//   1. rotates the source cloud and stages per-point lattice offsets in shared
+//      memory;
+//   2. votes every pair (i, j): the lattice index k = ROUND((y_j - R x_i)/delta)
+//      relative to the box corner; pairs inside the lattice box increment a
+//      shared-memory histogram (Lemma 1, Eq. 5: the translation mode of the
+//      rotated pairwise differences, discretised as in Section IV-B);
 //   3. scans and clears the histogram for the mode: V = max count, k* = the
-//      lexicographically smallest bin holding V;
-//   4. counts the inliers of Eq. 3 at t* = k* delta through the target cell
-//      list (exact Euclidean test against epsilon), and, when every rotation
-//      is a candidate, also sums the robust cost from the target's truncated
-//      distance grid;
-//   5. publishes (k*, V, M, cost) and folds M*, max V and the argmin key into
-//      per-problem accumulators.
+//      lexicographically smallest bin holding V; publishes (k*, V).
 // Work items are (problem, rotation tile) pairs taken from a global counter, so
 // one persistent launch serves one problem or a batch of uneven problems.
+//
+// count_kernel -- one warp per rotation: the inlier count M of Eq. 3 at
+// t* = k* delta through the target cell list (exact Euclidean test against
+// epsilon) and, when every rotation is a candidate, the robust cost from the
+// target's truncated distance grid; folds M* and the argmin key into
+// per-problem accumulators.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "kernels.cuh"
-
 #include <atomic>
+
+#include "kernels.cuh"
 
 namespace dses {
 
@@ -30,14 +31,13 @@ extern std::atomic<long long> g_launches;
 
 namespace {
 
-// floor(v) for |v| < 2^22: adding 1.5 * 2^23 rounding toward -inf leaves
-// floor(v) in the low mantissa bits. Out-of-range v map to huge unsigned
-// values, i.e. outside every box.
+// Adding 1.5 * 2^23 to |v| < 2^22 leaves an integer rounding of v in the low
+// mantissa bits; the float bit pattern of (1.5 * 2^23 + n) is kMagicBits + n.
 constexpr float kMagic = 12582912.0f;
-constexpr int kMagicBits = 0x4B400000;
+constexpr unsigned kMagicBits = 0x4B400000u;
 
 __device__ __forceinline__ unsigned floor_bits(float v) {
-  return (unsigned)(__float_as_int(__fadd_rd(v, kMagic)) - kMagicBits);
+  return (unsigned)(__float_as_int(__fadd_rd(v, kMagic)) - (int)kMagicBits);
 }
 
 __device__ __forceinline__ float rho(int metric, float d, float eps, float tau, float h, float p) {
@@ -74,10 +74,10 @@ __device__ __forceinline__ float grid_lookup(const PassDesc& d, float qx, float 
   const float fx = gx - (float)ix, fy = gy - (float)iy, fz = gz - (float)iz;
   const float* b = d.D + ((size_t)ix * d.G + iy) * d.G + iz;
   const size_t sy = d.G, sx = (size_t)d.G * d.G;
-  const float c00 = b[0] + fz * (b[1] - b[0]);
-  const float c01 = b[sy] + fz * (b[sy + 1] - b[sy]);
-  const float c10 = b[sx] + fz * (b[sx + 1] - b[sx]);
-  const float c11 = b[sx + sy] + fz * (b[sx + sy + 1] - b[sx + sy]);
+  const float c00 = __ldg(b) + fz * (__ldg(b + 1) - __ldg(b));
+  const float c01 = __ldg(b + sy) + fz * (__ldg(b + sy + 1) - __ldg(b + sy));
+  const float c10 = __ldg(b + sx) + fz * (__ldg(b + sx + 1) - __ldg(b + sx));
+  const float c11 = __ldg(b + sx + sy) + fz * (__ldg(b + sx + sy + 1) - __ldg(b + sx + sy));
   const float c0 = c00 + fy * (c01 - c00);
   const float c1 = c10 + fy * (c11 - c10);
   return c0 + fx * (c1 - c0);
@@ -119,33 +119,105 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
   return v;
 }
 
-// Vote all (source in this chunk) x (target) pairs of the CTA's items into the
-// slab histogram. Item = (target chunk of 32 P points, source group); a warp
-// holds its P targets per lane in registers and streams the source offsets
-// from shared memory (broadcast reads).
+// Shared-memory histogram increment, predicated (no branch) on the pair lying
+// inside the centred box: |w_a| < h_a on all three axes.
+__device__ __forceinline__ void red_if_inside(uint32_t addr, uint32_t inc, float wx, float wy, float wz, float hx,
+                                              float hy, float hz) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t.reg .f32 ax, ay, az;\n\t"
+      "abs.f32 ax, %2;\n\tabs.f32 ay, %3;\n\tabs.f32 az, %4;\n\t"
+      "setp.lt.f32 p, ax, %5;\n\t"
+      "setp.lt.and.f32 p, ay, %6, p;\n\t"
+      "setp.lt.and.f32 p, az, %7, p;\n\t"
+      "@p red.shared.add.u32 [%0], %1;\n\t}" ::"r"(addr),
+      "r"(inc), "f"(wx), "f"(wy), "f"(wz), "f"(hx), "f"(hy), "f"(hz));
+}
+
+// Next vote item of this CTA (dynamic balance across warps).
+__device__ __forceinline__ int next_item(int* counter, int lane) {
+  int it = 0;
+  if (lane == 0) it = atomicAdd(counter, 1);
+  return __shfl_sync(0xffffffffu, it, 0);
+}
+
+__device__ __forceinline__ void load_targets(const float4* __restrict__ Y, int M, int base, int lane, int P,
+                                             float (*ty)[3]) {
+  for (int p = 0; p < P; ++p) {
+    const int j = base + p * 32 + lane;
+    if (j < M) {
+      const float4 q = __ldg(Y + j);
+      ty[p][0] = q.x; ty[p][1] = q.y; ty[p][2] = q.z;
+    } else {  // padding lane: lands far outside every box
+      ty[p][0] = 1e30f; ty[p][1] = 1e30f; ty[p][2] = 1e30f;
+    }
+  }
+}
+
+// Centred fast path (odd slab extents on all axes). The staged offset makes
+// w_a = y_a/delta + c_a the box-relative lattice coordinate minus S_a/2, so
+// the box test is |w_a| < S_a/2 and, with h'_a = (S_a - 1)/2 an integer,
+// w_a + (1.5 * 2^23 + h'_a) rounded to nearest holds k_a in its low bits (a
+// tie means y_j - R x_i lies on a voxel face). The bin's shared address is
+// then three multiply-adds of those bit patterns.
 template <int P, bool U16>
-__device__ __forceinline__ void vote_chunk(const PassDesc& d, const float4* __restrict__ srcc, int nsrc,
-                                           unsigned SX, uint32_t* __restrict__ hist, int warp, int lane) {
+__device__ __forceinline__ void vote_centred(const PassDesc& d, const float4* __restrict__ srcc, int nsrc,
+                                             unsigned SX, uint32_t hist_base, int* item_ctr, int lane) {
+  const int n_tchunks = d.n_tchunks, n_sgroups = d.n_sgroups;
+  const int n_items = n_tchunks * n_sgroups;
+  const int spg = (nsrc + n_sgroups - 1) / n_sgroups;
+  const unsigned Ey = (unsigned)d.E[1], Ez = (unsigned)d.E[2], Eyz = Ey * Ez;
+  const float inv = d.inv_delta;
+  const float hx = 0.5f * (float)SX, hy = 0.5f * (float)Ey, hz = 0.5f * (float)Ez;
+  const float mx = kMagic + (float)((SX - 1) / 2), my = kMagic + (float)((Ey - 1) / 2),
+              mz = kMagic + (float)((Ez - 1) / 2);
+  // address = base + unit * (kx Eyz + ky Ez + kz), the kMagicBits offsets folded in
+  const uint32_t bias = kMagicBits * (Eyz + Ez + 1u);
+  const uint32_t abase32 = hist_base - 4u * bias;
+  const uint32_t abase16 = hist_base - 2u * bias;
+  for (int it = next_item(item_ctr, lane); it < n_items; it = next_item(item_ctr, lane)) {
+    const int tc = it % n_tchunks, sg = it / n_tchunks;
+    float ty[P][3];
+    load_targets(d.Y, d.M, tc * P * 32, lane, P, ty);
+    const int i0 = sg * spg, i1 = min(i0 + spg, nsrc);
+#pragma unroll 2
+    for (int i = i0; i < i1; ++i) {
+      const float4 c = srcc[i];
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const float wx = __fmaf_rn(ty[p][0], inv, c.x);
+        const float wy = __fmaf_rn(ty[p][1], inv, c.y);
+        const float wz = __fmaf_rn(ty[p][2], inv, c.z);
+        const uint32_t bx = __float_as_uint(__fadd_rn(wx, mx));
+        const uint32_t by = __float_as_uint(__fadd_rn(wy, my));
+        const uint32_t bz = __float_as_uint(__fadd_rn(wz, mz));
+        if (U16) {
+          const uint32_t b = bx * Eyz + (by * Ez + bz);  // bin + bias (bias even)
+          const uint32_t addr = abase16 + ((b >> 1) << 2);
+          const uint32_t inc = 1u + (b & 1u) * 0xffffu;
+          red_if_inside(addr, inc, wx, wy, wz, hx, hy, hz);
+        } else {
+          const uint32_t addr = abase32 + 4u * (bx * Eyz + (by * Ez + bz));
+          red_if_inside(addr, 1u, wx, wy, wz, hx, hy, hz);
+        }
+      }
+    }
+  }
+}
+
+// Generic path (any extents): k_a = floor(w_a) by a round-down add, box test on
+// the integer indices.
+template <int P, bool U16>
+__device__ __forceinline__ void vote_generic(const PassDesc& d, const float4* __restrict__ srcc, int nsrc,
+                                             unsigned SX, uint32_t* __restrict__ hist, int* item_ctr, int lane) {
   const int n_tchunks = d.n_tchunks, n_sgroups = d.n_sgroups;
   const int n_items = n_tchunks * n_sgroups;
   const int spg = (nsrc + n_sgroups - 1) / n_sgroups;
   const unsigned Ey = (unsigned)d.E[1], Ez = (unsigned)d.E[2];
   const float inv = d.inv_delta;
-  const int M = d.M;
-  const float4* __restrict__ Y = d.Y;
-  for (int it = warp; it < n_items; it += kPassThreads / 32) {
+  for (int it = next_item(item_ctr, lane); it < n_items; it = next_item(item_ctr, lane)) {
     const int tc = it % n_tchunks, sg = it / n_tchunks;
     float ty[P][3];
-#pragma unroll
-    for (int p = 0; p < P; ++p) {
-      const int j = (tc * P + p) * 32 + lane;
-      if (j < M) {
-        const float4 q = __ldg(Y + j);
-        ty[p][0] = q.x; ty[p][1] = q.y; ty[p][2] = q.z;
-      } else {  // padding lane: lands far outside every box
-        ty[p][0] = 1e30f; ty[p][1] = 1e30f; ty[p][2] = 1e30f;
-      }
-    }
+    load_targets(d.Y, d.M, tc * P * 32, lane, P, ty);
     const int i0 = sg * spg, i1 = min(i0 + spg, nsrc);
     for (int i = i0; i < i1; ++i) {
       const float4 c = srcc[i];
@@ -167,15 +239,14 @@ __device__ __forceinline__ void vote_chunk(const PassDesc& d, const float4* __re
 }
 
 template <int P>
-__global__ void __launch_bounds__(kPassThreads, 1) rotation_pass_kernel(PassLaunch L) {
+__global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ PassDesc sd;
   __shared__ unsigned long long red64[32];
-  __shared__ float redf[32];
-  __shared__ int redi[32];
-  __shared__ int s_item, s_prob;
+  __shared__ int s_item, s_prob, s_vote_item;
 
   uint32_t* hist = reinterpret_cast<uint32_t*>(smem);
+  const uint32_t hist_base = (uint32_t)__cvta_generic_to_shared(hist);
   float4* srcc = reinterpret_cast<float4*>(smem + L.hist_bytes);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -222,12 +293,23 @@ __global__ void __launch_bounds__(kPassThreads, 1) rotation_pass_kernel(PassLaun
       for (int s = 0; s < d.n_slabs; ++s) {
         const int x0 = s * d.slab_x;
         const unsigned SX = (unsigned)min(d.slab_x, d.E[0] - x0);
-        const float off0 = 0.5f - (float)(d.lo[0] + x0);
-        const float off1 = 0.5f - (float)d.lo[1];
-        const float off2 = 0.5f - (float)d.lo[2];
+        const bool centred = (SX & 1u) && (Ey & 1u) && (Ez & 1u);
+        // staged offsets: centred path c = -(lo + off) - (S - 1)/2 - u/delta,
+        // generic path c = 1/2 - (lo + off) - u/delta
+        float off0, off1, off2;
+        if (centred) {
+          off0 = -(float)(d.lo[0] + x0) - (float)((SX - 1) / 2);
+          off1 = -(float)d.lo[1] - (float)((Ey - 1) / 2);
+          off2 = -(float)d.lo[2] - (float)((Ez - 1) / 2);
+        } else {
+          off0 = 0.5f - (float)(d.lo[0] + x0);
+          off1 = 0.5f - (float)d.lo[1];
+          off2 = 0.5f - (float)d.lo[2];
+        }
         for (int c0 = 0; c0 < d.N; c0 += kSrcChunk) {
           const int c1 = min(c0 + kSrcChunk, d.N);
           __syncthreads();  // previous chunk's readers are done
+          if (tid == 0) s_vote_item = 0;
           for (int i = c0 + tid; i < c1; i += kPassThreads) {
             const float x = __ldg(d.X + 3 * (size_t)i), y = __ldg(d.X + 3 * (size_t)i + 1),
                         z = __ldg(d.X + 3 * (size_t)i + 2);
@@ -238,10 +320,17 @@ __global__ void __launch_bounds__(kPassThreads, 1) rotation_pass_kernel(PassLaun
                                        fmaf(-uz, d.inv_delta, off2), 0.f);
           }
           __syncthreads();
-          if (d.hist_u16)
-            vote_chunk<P, true>(d, srcc, c1 - c0, SX, hist, warp, lane);
-          else
-            vote_chunk<P, false>(d, srcc, c1 - c0, SX, hist, warp, lane);
+          if (centred) {
+            if (d.hist_u16)
+              vote_centred<P, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane);
+            else
+              vote_centred<P, false>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane);
+          } else {
+            if (d.hist_u16)
+              vote_generic<P, true>(d, srcc, c1 - c0, SX, hist, &s_vote_item, lane);
+            else
+              vote_generic<P, false>(d, srcc, c1 - c0, SX, hist, &s_vote_item, lane);
+          }
         }
         __syncthreads();
         // mode of this slab: scan and clear; each thread walks increasing bins
@@ -276,77 +365,80 @@ __global__ void __launch_bounds__(kPassThreads, 1) rotation_pass_kernel(PassLaun
         const unsigned long long sk = red64[0];
         // strict: an earlier slab holds smaller bins and keeps ties
         if (s == 0 || (sk >> 32) > (best >> 32)) best = sk;
-        __syncthreads();
       }
+      if (tid == 0) {
+        const unsigned V = (unsigned)(best >> 32);
+        const unsigned gbin = 0xffffffffu - (unsigned)(best & 0xffffffffull);
+        const int kx = d.lo[0] + (int)(gbin / (Ey * Ez));
+        const int ky = d.lo[1] + (int)((gbin / Ez) % Ey);
+        const int kz = d.lo[2] + (int)(gbin % Ez);
+        d.kv[d.rot_base + (uint32_t)r - d.out_base] = make_int4(kx, ky, kz, (int)V);
+        atomicMax(d.acc + 1, V);
+      }
+    }
+  }
+}
 
-      const unsigned V = (unsigned)(best >> 32);
-      const unsigned gbin = 0xffffffffu - (unsigned)(best & 0xffffffffull);
-      const int kx = d.lo[0] + (int)(gbin / (Ey * Ez));
-      const int ky = d.lo[1] + (int)((gbin / Ez) % Ey);
-      const int kz = d.lo[2] + (int)(gbin % Ez);
-      const float tx = (float)kx * d.delta, ty = (float)ky * d.delta, tz = (float)kz * d.delta;
-
-      // inlier count (Eq. 3) and, on the fused path, the robust cost
-      int cnt = 0;
-      float csum = 0.f;
-      const bool grid_cost = d.fuse_score && d.metric != 0;
-      for (int i = tid; i < d.N; i += kPassThreads) {
-        const float x = __ldg(d.X + 3 * (size_t)i), y = __ldg(d.X + 3 * (size_t)i + 1),
-                    z = __ldg(d.X + 3 * (size_t)i + 2);
-        const float qx = fmaf(R[0], x, fmaf(R[1], y, R[2] * z)) + tx;
-        const float qy = fmaf(R[3], x, fmaf(R[4], y, R[5] * z)) + ty;
-        const float qz = fmaf(R[6], x, fmaf(R[7], y, R[8] * z)) + tz;
-        cnt += has_inlier(d, qx, qy, qz) ? 1 : 0;
-        if (grid_cost) csum += rho(d.metric, grid_lookup(d, qx, qy, qz), d.eps, d.tau, d.huber_h, d.p_exp);
-      }
+// One warp per rotation: inlier count (Eq. 3) at t* and, on the fused path,
+// the robust cost from the distance grid and the argmin key.
+__global__ void __launch_bounds__(256) count_kernel(PassLaunch L) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  const int total = L.rot_prefix[L.n_probs];
+  for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < total; g += warps) {
+    int lo = 0, hi = L.n_probs - 1;  // last p with rot_prefix[p] <= g
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (__ldg(L.rot_prefix + mid) <= g) lo = mid; else hi = mid - 1;
+    }
+    const PassDesc& d = L.probs[lo];
+    const int r = g - __ldg(L.rot_prefix + lo);
+    const uint32_t gidx = d.rot_base + (uint32_t)r, o = gidx - d.out_base;
+    float R[9];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-        csum += __shfl_xor_sync(0xffffffffu, csum, o);
-      }
-      if (lane == 0) { redi[warp] = cnt; redf[warp] = csum; }
-      __syncthreads();
-      if (warp == 0) {
-        int c2 = redi[lane];
-        float f2 = redf[lane];
+    for (int k = 0; k < 9; ++k) R[k] = __ldg(d.rot + 9 * (size_t)r + k);
+    const int4 kv = d.kv[o];
+    const float tx = (float)kv.x * d.delta, ty = (float)kv.y * d.delta, tz = (float)kv.z * d.delta;
+    const bool grid_cost = d.fuse_score && d.metric != 0;
+    int cnt = 0;
+    float csum = 0.f;
+    for (int i = lane; i < d.N; i += 32) {
+      const float x = __ldg(d.X + 3 * (size_t)i), y = __ldg(d.X + 3 * (size_t)i + 1),
+                  z = __ldg(d.X + 3 * (size_t)i + 2);
+      const float qx = fmaf(R[0], x, fmaf(R[1], y, R[2] * z)) + tx;
+      const float qy = fmaf(R[3], x, fmaf(R[4], y, R[5] * z)) + ty;
+      const float qz = fmaf(R[6], x, fmaf(R[7], y, R[8] * z)) + tz;
+      cnt += has_inlier(d, qx, qy, qz) ? 1 : 0;
+      if (grid_cost) csum += rho(d.metric, grid_lookup(d, qx, qy, qz), d.eps, d.tau, d.huber_h, d.p_exp);
+    }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          c2 += __shfl_xor_sync(0xffffffffu, c2, o);
-          f2 += __shfl_xor_sync(0xffffffffu, f2, o);
-        }
-        if (lane == 0) {
-          const uint32_t gidx = d.rot_base + (uint32_t)r;
-          const uint32_t o = gidx - d.out_base;
-          d.kv[o] = make_int4(kx, ky, kz, (int)V);
-          d.Mout[o] = (uint32_t)c2;
-          atomicMax(d.acc + 0, (uint32_t)c2);
-          atomicMax(d.acc + 1, V);
-          if (d.fuse_score) {
-            const float cost = d.metric == 0 ? (float)(d.N - c2) : f2;
-            d.cost[o] = cost;
-            const unsigned long long bkey =
-                ((unsigned long long)__float_as_uint(cost) << 32) | (unsigned long long)gidx;
-            atomicMin(d.best, bkey);
-          }
-        }
+    for (int k = 16; k > 0; k >>= 1) {
+      cnt += __shfl_xor_sync(0xffffffffu, cnt, k);
+      csum += __shfl_xor_sync(0xffffffffu, csum, k);
+    }
+    if (lane == 0) {
+      d.Mout[o] = (uint32_t)cnt;
+      atomicMax(d.acc + 0, (uint32_t)cnt);
+      if (d.fuse_score) {
+        const float cost = d.metric == 0 ? (float)(d.N - cnt) : csum;
+        d.cost[o] = cost;
+        atomicMin(d.best, ((unsigned long long)__float_as_uint(cost) << 32) | (unsigned long long)gidx);
       }
-      __syncthreads();
     }
   }
 }
 
 template <int P>
-cudaError_t launch_p(const PassLaunch& L, int grid_ctas, cudaStream_t s) {
+cudaError_t launch_vote_p(const PassLaunch& L, int grid_ctas, cudaStream_t s) {
   const int smem = pass_smem_bytes(L.hist_bytes);
   static int configured = 0;
   if (configured < smem) {
-    cudaError_t e =
-        cudaFuncSetAttribute(rotation_pass_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(vote_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     configured = smem;
   }
   g_launches.fetch_add(1, std::memory_order_relaxed);
-  rotation_pass_kernel<P><<<grid_ctas, kPassThreads, smem, s>>>(L);
+  vote_kernel<P><<<grid_ctas, kPassThreads, smem, s>>>(L);
   return cudaGetLastError();
 }
 
@@ -354,14 +446,21 @@ cudaError_t launch_p(const PassLaunch& L, int grid_ctas, cudaStream_t s) {
 
 int pass_smem_bytes(int hist_bytes) { return hist_bytes + kSrcChunk * (int)sizeof(float4); }
 
-cudaError_t launch_rotation_pass(const PassLaunch& L, int points_per_thread, int grid_ctas, cudaStream_t s) {
+cudaError_t launch_vote(const PassLaunch& L, int points_per_thread, int grid_ctas, cudaStream_t s) {
   switch (points_per_thread) {
-    case 1: return launch_p<1>(L, grid_ctas, s);
-    case 2: return launch_p<2>(L, grid_ctas, s);
-    case 4: return launch_p<4>(L, grid_ctas, s);
-    case 8: return launch_p<8>(L, grid_ctas, s);
+    case 1: return launch_vote_p<1>(L, grid_ctas, s);
+    case 2: return launch_vote_p<2>(L, grid_ctas, s);
+    case 4: return launch_vote_p<4>(L, grid_ctas, s);
+    case 8: return launch_vote_p<8>(L, grid_ctas, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_count(const PassLaunch& L, int total_rot, cudaStream_t s) {
+  const int blocks = (int)std::min<long long>(((long long)total_rot * 32 + 255) / 256, 148LL * 16);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  count_kernel<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(L);
+  return cudaGetLastError();
 }
 
 }  // namespace dses
