@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--hopf-n", type=int, default=16, help="grid N_side (16 = the benchmark; smaller for profiling)")
+    ap.add_argument("--points-per-thread", type=int, default=0, help="vote launch shape (0: library default)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -216,6 +217,8 @@ def ours(args, ws, rank, local):
     pb_host.src = Xh.data_ptr()  # pinned host buffer
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     ctx.set_option("record_timing", 1)
+    if args.points_per_thread:
+        ctx.set_option("points_per_thread", args.points_per_thread)
 
     for _ in range(args.warmup):
         with torch.cuda.stream(stream):

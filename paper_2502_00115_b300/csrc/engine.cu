@@ -104,6 +104,9 @@ struct dses_target {
   std::vector<float> host;  // m x 3
   float bbmin[3], bbmax[3];
   float4* Y = nullptr;      // packed, input order
+  float4* Ym = nullptr;     // Morton order (vote)
+  float4* gbox = nullptr;   // per group of kGroup Morton-consecutive points: min, max
+  int n_groups = 0;
   float* D = nullptr;       // G^3 distance grid
   int G = 0;
   float glo[3], gh[3], gcap = 0;
@@ -213,6 +216,47 @@ int cap_points_in_cube(dses_target* T, float delta) {
         }
   T->capY[fbits(delta)] = best;
   return best;
+}
+
+// Morton (Z-order) ordering of the target points and the bounding box of every
+// run of kGroup consecutive points: the vote's culling groups.
+void build_morton_groups(dses_ctx* c, dses_target* T) {
+  const int m = T->m;
+  std::vector<std::pair<uint64_t, int>> code((size_t)m);
+  for (int j = 0; j < m; ++j) {
+    uint64_t q[3];
+    for (int a = 0; a < 3; ++a) {
+      const double ext = (double)T->bbmax[a] - T->bbmin[a];
+      const double u = ext > 0 ? ((double)T->host[3 * j + a] - T->bbmin[a]) / ext : 0.0;
+      q[a] = (uint64_t)std::min(1023.0, std::max(0.0, std::floor(u * 1024.0)));
+    }
+    uint64_t k = 0;
+    for (int b = 0; b < 10; ++b)
+      for (int a = 0; a < 3; ++a) k |= ((q[a] >> b) & 1ull) << (3 * b + a);
+    code[(size_t)j] = {k, j};
+  }
+  std::stable_sort(code.begin(), code.end());
+  std::vector<float4> ym((size_t)m);
+  for (int j = 0; j < m; ++j) {
+    const float* p = &T->host[3 * (size_t)code[(size_t)j].second];
+    ym[(size_t)j] = make_float4(p[0], p[1], p[2], 0.f);
+  }
+  T->n_groups = (m + kGroup - 1) / kGroup;
+  std::vector<float4> box(2 * (size_t)T->n_groups);
+  for (int g = 0; g < T->n_groups; ++g) {
+    float4 lo = ym[(size_t)g * kGroup], hi = lo;
+    for (int j = g * kGroup; j < std::min(m, (g + 1) * kGroup); ++j) {
+      lo.x = std::min(lo.x, ym[j].x); lo.y = std::min(lo.y, ym[j].y); lo.z = std::min(lo.z, ym[j].z);
+      hi.x = std::max(hi.x, ym[j].x); hi.y = std::max(hi.y, ym[j].y); hi.z = std::max(hi.z, ym[j].z);
+    }
+    box[2 * (size_t)g] = lo;
+    box[2 * (size_t)g + 1] = hi;
+  }
+  CK(cudaMalloc(&T->Ym, sizeof(float4) * (size_t)m));
+  CK(cudaMalloc(&T->gbox, sizeof(float4) * box.size()));
+  CK(cudaMemcpyAsync(T->Ym, ym.data(), sizeof(float4) * (size_t)m, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(T->gbox, box.data(), sizeof(float4) * box.size(), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
 }
 
 // Target cell list for inlier counting at tolerance eps: cells at least
@@ -482,6 +526,9 @@ PassDesc make_desc(const Job& j, int P, bool second) {
   std::memset(&d, 0, sizeof(d));
   d.X = j.X;
   d.Y = j.cl->sorted;
+  d.Yv = j.T->Ym;
+  d.gbox = j.T->gbox;
+  d.n_groups = j.T->n_groups;
   d.N = j.N;
   d.M = j.T->m;
   if (!second) {
@@ -524,6 +571,12 @@ PassDesc make_desc(const Job& j, int P, bool second) {
   d.D = j.T->D;
   d.G = j.T->G;
   d.gcap = j.T->gcap;
+  {
+    // sqrt(3) times the largest voxel edge, plus a margin far above the FP32
+    // error of the stored distances and of the interpolation
+    const double hmax = std::max({(double)j.T->gh[0], (double)j.T->gh[1], (double)j.T->gh[2]});
+    d.grid_err = (float)(std::sqrt(3.0) * hmax * 1.0001 + 1e-5 + 1e-5 * j.T->gcap);
+  }
   d.out_base = 0;
   d.kv = j.kv;
   d.Mout = j.M;
@@ -969,6 +1022,8 @@ static void stop_worker(dses_ctx* c) {
 
 static void free_target(dses_target* T) {
   if (T->Y) cudaFree(T->Y);
+  if (T->Ym) cudaFree(T->Ym);
+  if (T->gbox) cudaFree(T->gbox);
   if (T->D) cudaFree(T->D);
   for (auto& kv : T->cells) {
     cudaFree(kv.second.start);
@@ -1037,6 +1092,7 @@ dses_status dses_create_target(dses_ctx* c, const float* xyz, int64_t m, int32_t
       T->gh[a] = (float)h;
       T->glo[a] = (float)((double)T->bbmin[a] - grid_cap - h);
     }
+    build_morton_groups(c, T.get());
     CK(cudaMalloc(&T->D, sizeof(float) * (size_t)G * G * G));
     CK(launch_dist_grid(T->Y, (int)m, G, T->glo, T->gh, grid_cap, T->D, c->stream));
     CK(cudaStreamSynchronize(c->stream));

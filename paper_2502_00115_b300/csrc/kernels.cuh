@@ -11,10 +11,12 @@ namespace dses {
 // Threads of the rotation-pass CTA (one CTA per SM, 32 warps).
 constexpr int kPassThreads = 1024;
 // Source points staged per chunk in shared memory (float4 each).
-constexpr int kSrcChunk = 2048;
+constexpr int kSrcChunk = 1024;
+// Target points per bounding-box group of the Morton-ordered targets.
+constexpr int kGroup = 32;
 // Largest dynamic shared memory a CTA may request on sm_103a (227 KB).
 constexpr int kMaxSmem = 232448;
-// Static shared memory of the pass kernel plus headroom.
+// Static shared memory of the pass kernel (descriptor, reductions) plus headroom.
 constexpr int kPassStaticSmem = 2048;
 // Histogram budget: what is left after the source chunk and static storage.
 constexpr int kHistBudget = kMaxSmem - kSrcChunk * 16 - kPassStaticSmem;
@@ -23,7 +25,10 @@ constexpr int kHistBudget = kMaxSmem - kSrcChunk * 16 - kPassStaticSmem;
 struct PassDesc {
   // inputs (device)
   const float* X;        // N x 3 source points
-  const float4* Y;       // M target points (cell-sorted; .w unused)
+  const float4* Y;       // M target points (cell-sorted; .w unused), inlier count
+  const float4* Yv;      // M target points in Morton order (vote)
+  const float4* gbox;    // per group of kGroup Morton-consecutive targets: min, max
+  int n_groups;
   const float* rot;      // rotations of this pass, 9 floats each (row-major)
   int N, M;
   int n_rot;             // rotations in this pass
@@ -51,6 +56,7 @@ struct PassDesc {
   const float* D;        // G^3 truncated distance grid
   int G;
   float glo[3], ginv_h[3], gcap;
+  float grid_err;        // bound on |interpolated - exact capped distance| (sqrt(3) max h + margin)
   // outputs, indexed by (global rotation index - out_base)
   uint32_t out_base;
   int4* kv;              // (kx, ky, kz, V)

@@ -177,9 +177,9 @@ __device__ __forceinline__ void vote_centred(const PassDesc& d, const float4* __
   for (int it = next_item(item_ctr, lane); it < n_items; it = next_item(item_ctr, lane)) {
     const int tc = it % n_tchunks, sg = it / n_tchunks;
     float ty[P][3];
-    load_targets(d.Y, d.M, tc * P * 32, lane, P, ty);
+    load_targets(d.Yv, d.M, tc * P * 32, lane, P, ty);
     const int i0 = sg * spg, i1 = min(i0 + spg, nsrc);
-#pragma unroll 2
+#pragma unroll 4
     for (int i = i0; i < i1; ++i) {
       const float4 c = srcc[i];
 #pragma unroll
@@ -217,7 +217,7 @@ __device__ __forceinline__ void vote_generic(const PassDesc& d, const float4* __
   for (int it = next_item(item_ctr, lane); it < n_items; it = next_item(item_ctr, lane)) {
     const int tc = it % n_tchunks, sg = it / n_tchunks;
     float ty[P][3];
-    load_targets(d.Y, d.M, tc * P * 32, lane, P, ty);
+    load_targets(d.Yv, d.M, tc * P * 32, lane, P, ty);
     const int i0 = sg * spg, i1 = min(i0 + spg, nsrc);
     for (int i = i0; i < i1; ++i) {
       const float4 c = srcc[i];
@@ -408,8 +408,19 @@ __global__ void __launch_bounds__(256) count_kernel(PassLaunch L) {
       const float qx = fmaf(R[0], x, fmaf(R[1], y, R[2] * z)) + tx;
       const float qy = fmaf(R[3], x, fmaf(R[4], y, R[5] * z)) + ty;
       const float qz = fmaf(R[6], x, fmaf(R[7], y, R[8] * z)) + tz;
-      cnt += has_inlier(d, qx, qy, qz) ? 1 : 0;
-      if (grid_cost) csum += rho(d.metric, grid_lookup(d, qx, qy, qz), d.eps, d.tau, d.huber_h, d.p_exp);
+      // The capped distance field is 1-Lipschitz, so its trilinear interpolant
+      // between voxel centres is within grid_err of min(d, cap); only queries
+      // within that band of epsilon need the exact cell-list search.
+      const float dg = grid_lookup(d, qx, qy, qz);
+      bool inl;
+      if (dg >= d.eps + d.grid_err)
+        inl = false;
+      else if (dg < d.eps - d.grid_err && d.gcap > d.eps)
+        inl = true;
+      else
+        inl = has_inlier(d, qx, qy, qz);
+      cnt += inl ? 1 : 0;
+      if (grid_cost) csum += rho(d.metric, dg, d.eps, d.tau, d.huber_h, d.p_exp);
     }
 #pragma unroll
     for (int k = 16; k > 0; k >>= 1) {
