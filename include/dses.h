@@ -218,6 +218,29 @@ dses_status dses_target_distance_grid(dses_ctx* ctx, const dses_target* target, 
 dses_status dses_set_option(dses_ctx* ctx, const char* key, int64_t value);
 dses_status dses_get_option(dses_ctx* ctx, const char* key, int64_t* value);
 
+/* Rotation vote without any device allocation (the paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc while they
+ * run, e.g. a real-time loop driven by pre-built CUDA graphs, a host that
+ * reserves all device memory at start-up, or a plugin whose application owns
+ * the allocator). For every rotation it computes what dses_debug_per_rotation
+ * reports as k_star and votes: the lattice index k* of the translation mode
+ * and its frequency V. All inputs and outputs are device pointers of `device`
+ * owned by the caller: src_dev (n_src x 3), tgt_dev (n_tgt x 3), rot_dev
+ * (n_rot x 9 row-major FP32 rotations), kv_dev (n_rot x 4 int32: kx, ky, kz, V;
+ * 16-byte aligned). Only params->epsilon, delta_t, t_center and t_half are read.
+ * Work is queued on cuda_stream (NULL: the legacy default stream); outputs are
+ * valid once that stream has reached this point. Scratch lives in one static
+ * device array of about 129 KB per GPU (held until exit), so n_tgt is limited to
+ * 8192 points (larger: INVALID_ARG). The first call on a device looks up the
+ * array's device address with that device made current, then restores the
+ * caller's current device; make that first call before any stream capture.
+ * Calls share the array: calls that overlap on the GPU (other streams, other
+ * host threads) race and must be serialised by the caller. Each call clears
+ * the counters it needs. Errors: INVALID_ARG, CUDA. */
+dses_status dses_vote_static(int device, void* cuda_stream, const float* src_dev, int64_t n_src,
+                             const float* tgt_dev, int64_t n_tgt, const float* rot_dev, int64_t n_rot,
+                             const dses_params* params, int32_t* kv_dev);
+
 /* Last error text of the context (empty string if none; never NULL). */
 const char* dses_last_error(dses_ctx* ctx);
 

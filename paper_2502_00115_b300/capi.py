@@ -107,6 +107,7 @@ SIGNATURES = {
     "dses_target_distance_grid": (_i32, [_vp, _vp, _vp, _vp, _vp, _P(_i32), _P(_f32)]),
     "dses_set_option": (_i32, [_vp, ctypes.c_char_p, _i64]),
     "dses_get_option": (_i32, [_vp, ctypes.c_char_p, _P(_i64)]),
+    "dses_vote_static": (_i32, [_i32, _vp, _vp, _i64, _vp, _i64, _vp, _i64, _P(dses_params), _vp]),
     "dses_last_error": (ctypes.c_char_p, [_vp]),
     "dses_status_string": (ctypes.c_char_p, [_i32]),
 }
@@ -232,6 +233,13 @@ def dses_get_option(ctx, key: str):
     v = ctypes.c_int64()
     st = load().dses_get_option(ctx, key.encode(), ctypes.byref(v))
     return st, v.value
+
+
+def dses_vote_static(device: int, stream: int, src_ptr: int, n_src: int, tgt_ptr: int, n_tgt: int, rot_ptr: int,
+                     n_rot: int, params: dses_params, kv_ptr: int) -> int:
+    return load().dses_vote_static(device, ctypes.c_void_p(stream or 0), ctypes.c_void_p(src_ptr), n_src,
+                                   ctypes.c_void_p(tgt_ptr), n_tgt, ctypes.c_void_p(rot_ptr), n_rot,
+                                   ctypes.byref(params), ctypes.c_void_p(kv_ptr))
 
 
 def dses_last_error(ctx) -> str:
