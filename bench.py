@@ -52,6 +52,11 @@ def parse():
     ap.add_argument("--points-per-thread", type=int, default=0, help="vote launch shape (0: library default)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["modelnet_like", "batched", "serving"], default="modelnet_like",
+                    help="modelnet_like: the benchmark line; batched / serving: the other configurations")
+    ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: Poisson arrival rate (requests/s)")
+    ap.add_argument("--duration", type=float, default=60.0, help="serving: arrival window (s)")
     return ap.parse_args()
 
 
@@ -302,13 +307,114 @@ def ours(args, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# other configurations: batched problems, served requests
+
+
+def batched(args, ws, rank, local):
+    """64 uneven problems in one persistent launch vs one launch per problem."""
+    import torch
+
+    from paper_2502_00115_b300 import build, capi, synth
+
+    torch.cuda.set_device(local)
+    build.build()
+    probs = synth.batch_problems(args.seed, count=args.batch_count)
+    ctx = capi.Context(local)
+    targets = [ctx.create_target(p.Y, grid_cap=2 * p.tau) for p in probs]
+    pbs = [ctx.problem(t, p.X, capi.hopf_grid(p.hopf_n),
+                       capi.make_params(metric=p.metric, epsilon=p.epsilon, delta_t=p.delta_t, tau=p.tau,
+                                        t_half=p.t_half)) for t, p in zip(targets, probs)]
+    units = sum(72 * p.hopf_n**3 * len(p.X) for p in probs)
+    pairs = sum(72 * p.hopf_n**3 * len(p.X) * len(p.Y) for p in probs)
+    for _ in range(max(1, args.warmup)):
+        ctx.register_batch(pbs)
+    t_batch = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        rb = ctx.register_batch(pbs)
+        t_batch.append(time.perf_counter() - t0)
+    t_seq = []
+    for _ in range(max(1, args.steps // 2)):
+        t0 = time.perf_counter()
+        rs = [ctx.register(pb) for pb in pbs]
+        t_seq.append(time.perf_counter() - t0)
+    same = all(capi.result_dict(a)["rot_index"] == capi.result_dict(b)["rot_index"] for a, b in zip(rb, rs))
+    ctx.close()
+    tb, tsq = statistics.mean(t_batch), statistics.mean(t_seq)
+    print(json.dumps({
+        "workload": "batched", "metric": METRIC, "value": units / tb, "unit": UNIT, "problems": len(probs),
+        "registrations_per_s": len(probs) / tb, "sequential": {"value": units / tsq,
+                                                                "registrations_per_s": len(probs) / tsq},
+        "batch_over_sequential": tsq / tb, "pair_votes_per_s": pairs / tb, "s_per_batch": tb,
+        "steps": args.steps, "results_equal_sequential": same,
+        "config": {"targets": f"{min(len(p.Y) for p in probs)}..{max(len(p.Y) for p in probs)} pts",
+                   "sources": f"{min(len(p.X) for p in probs)}..{max(len(p.X) for p in probs)} pts",
+                   "rotations": f"{min(72 * p.hopf_n**3 for p in probs)}..{max(72 * p.hopf_n**3 for p in probs)}"},
+    }), flush=True)
+
+
+def serving(args, ws, rank, local):
+    """Poisson arrivals over resident targets through dses_submit / dses_poll."""
+    import torch
+
+    from paper_2502_00115_b300 import build, capi, synth
+
+    torch.cuda.set_device(local)
+    build.build()
+    wl = synth.serving_workload(args.seed, rate=args.rate, duration=args.duration)
+    ctx = capi.Context(local)
+    tmap = {}
+    for i, Y in enumerate(wl.targets):
+        tmap[i] = ctx.create_target(Y, grid_cap=0.1)
+    reqs = []
+    for (t_arr, ti, p) in wl.requests:
+        pb = ctx.problem(tmap[ti], p.X, capi.hopf_grid(p.hopf_n),
+                         capi.make_params(metric=p.metric, epsilon=p.epsilon, delta_t=p.delta_t, tau=p.tau,
+                                          t_half=p.t_half))
+        reqs.append((t_arr, pb, 72 * p.hopf_n**3 * len(p.X)))
+    # warm the path (grids, cell lists) outside the measurement
+    ctx.register(reqs[0][1])
+    pending = {}
+    lat = []
+    units = 0
+    t0 = time.perf_counter()
+    nxt = 0
+    while nxt < len(reqs) or pending:
+        now = time.perf_counter() - t0
+        while nxt < len(reqs) and reqs[nxt][0] <= now:
+            pending[ctx.submit(reqs[nxt][1])] = (t0 + reqs[nxt][0], reqs[nxt][2])
+            nxt += 1
+        for tk in list(pending):
+            st, r = ctx.poll(tk)
+            if st != capi.DSES_NOT_READY:
+                t_sub, u = pending.pop(tk)
+                lat.append(time.perf_counter() - t_sub)
+                units += u
+        time.sleep(0.0005)
+    wall = time.perf_counter() - t0
+    ctx.close()
+    print(json.dumps({
+        "workload": "serving", "metric": METRIC, "value": units / wall, "unit": UNIT,
+        "offered_rate": args.rate, "requests": len(reqs), "registrations_per_s": len(reqs) / wall,
+        "latency_ms": {"p50": 1000 * float(np.percentile(lat, 50)), "p99": 1000 * float(np.percentile(lat, 99)),
+                       "max": 1000 * max(lat)},
+        "wall_s": wall, "arrival_window_s": args.duration,
+    }), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args.gpus)
     if args.impl == "reference":
         reference_arm(args, ws, rank)
         return
-    ours(args, ws, rank, local)
+    if args.workload == "batched":
+        batched(args, ws, rank, local)
+    elif args.workload == "serving":
+        serving(args, ws, rank, local)
+    else:
+        ours(args, ws, rank, local)
 
 
 if __name__ == "__main__":
