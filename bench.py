@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--points-per-thread", type=int, default=0, help="vote launch shape (0: library default)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["modelnet_like", "batched", "serving"], default="modelnet_like",
+    ap.add_argument("--workload", choices=["modelnet_like", "batched", "serving", "robot_like"],
+                    default="modelnet_like",
                     help="modelnet_like: the benchmark line; batched / serving: the other configurations")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--rate", type=float, default=200.0, help="serving: Poisson arrival rate (requests/s)")
@@ -403,6 +404,47 @@ def serving(args, ws, rank, local):
     }), flush=True)
 
 
+def robot(args, ws, rank, local):
+    """The robot-pose-like problem: 2.36M-rotation grid plus Euler boxes around the best 32."""
+    import torch
+
+    from paper_2502_00115_b300 import build, capi, synth
+
+    torch.cuda.set_device(local)
+    build.build()
+    p = synth.robot_like_problem(args.seed, hopf_n=args.hopf_n if args.hopf_n != 16 else 32)
+    ctx = capi.Context(local)
+    ctx.set_option("record_timing", 1)
+    if args.points_per_thread:
+        ctx.set_option("points_per_thread", args.points_per_thread)
+    t = ctx.create_target(p.Y, grid_cap=p.grid_cap)
+    pb = ctx.problem(t, p.X, capi.hopf_grid(p.hopf_n),
+                     capi.make_params(metric=p.metric, epsilon=p.epsilon, delta_t=p.delta_t, tau=p.tau,
+                                      huber_h=p.huber_h, t_half=p.t_half, refine_top_k=p.refine_top_k,
+                                      refine_K=p.refine_K, refine_delta_r=p.refine_delta_r))
+    for _ in range(max(1, args.warmup)):
+        ctx.register(pb)
+    ts, vote_ms, count_ms = [], [], []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = ctx.register(pb)
+        ts.append(time.perf_counter() - t0)
+        vote_ms.append(ctx.get_option("last_pass_ns") / 1e6)
+        count_ms.append(ctx.get_option("last_count_ns") / 1e6)
+    ctx.close()
+    res = capi.result_dict(r)
+    ang = float(np.degrees(np.arccos(np.clip((np.trace(res["R"].astype(np.float64).T @ p.R_true) - 1) / 2, -1, 1))))
+    n_rot = p.n_rotations
+    tm = statistics.mean(ts)
+    print(json.dumps({
+        "workload": "robot_like", "metric": METRIC, "value": n_rot * len(p.X) / tm, "unit": UNIT,
+        "s_per_registration": tm, "vote_ms": statistics.mean(vote_ms), "count_ms": statistics.mean(count_ms),
+        "pair_votes_per_s": n_rot * len(p.X) * len(p.Y) / tm, "rotations": n_rot, "source_points": len(p.X),
+        "target_points": len(p.Y), "rotation_error_deg": ang,
+        "translation_error_m": float(np.linalg.norm(res["t"] - p.t_true)), "result": {k: (v.tolist() if hasattr(v, "tolist") else v) for k, v in res.items()},
+    }), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args.gpus)
@@ -413,6 +455,8 @@ def main():
         batched(args, ws, rank, local)
     elif args.workload == "serving":
         serving(args, ws, rank, local)
+    elif args.workload == "robot_like":
+        robot(args, ws, rank, local)
     else:
         ours(args, ws, rank, local)
 

@@ -206,6 +206,8 @@ dses_status dses_target_distance_grid(dses_ctx* ctx, const dses_target* target, 
  *   "serve_queue_cap"      submitted requests waiting for admission
  *   "serve_mem_budget"     device bytes the serving worker may hold for requests
  *   "serve_tile_rotations" rotations per request per serving iteration
+ *   "vote_sparse"          0 auto, 1 dense vote, 2 cull (source, target group) pairs
+ *                          outside the translation window (pays for small boxes)
  *   "record_timing"        1: time every rotation pass with CUDA events on the
  *                          context's stream
  *   "last_pass_ns"         (read-only) summed duration of the vote kernels of the

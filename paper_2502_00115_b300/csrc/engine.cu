@@ -94,6 +94,7 @@ struct Options {
   int64_t serve_mem_budget = 8LL << 30;
   int64_t serve_tile_rotations = 8192;
   int64_t record_timing = 0;
+  int64_t vote_sparse = 0;
 };
 
 }  // namespace
@@ -107,6 +108,7 @@ struct dses_target {
   float4* Ym = nullptr;     // Morton order (vote)
   float4* gbox = nullptr;   // per group of kGroup Morton-consecutive points: min, max
   int n_groups = 0;
+  float gext[3] = {0, 0, 0};  // mean group bounding-box extent per axis
   float* D = nullptr;       // G^3 distance grid
   int G = 0;
   float glo[3], gh[3], gcap = 0;
@@ -251,6 +253,9 @@ void build_morton_groups(dses_ctx* c, dses_target* T) {
     }
     box[2 * (size_t)g] = lo;
     box[2 * (size_t)g + 1] = hi;
+    T->gext[0] += (hi.x - lo.x) / T->n_groups;
+    T->gext[1] += (hi.y - lo.y) / T->n_groups;
+    T->gext[2] += (hi.z - lo.z) / T->n_groups;
   }
   CK(cudaMalloc(&T->Ym, sizeof(float4) * (size_t)m));
   CK(cudaMalloc(&T->gbox, sizeof(float4) * box.size()));
@@ -316,6 +321,7 @@ struct Job {
   // plan
   int u16 = 0, slab_x = 0, n_slabs = 1, hist_bytes = 0;
   bool fused = false;
+  bool sparse = false;
   // device scratch
   DevMem mem;
   int4* kv = nullptr;
@@ -432,6 +438,16 @@ void plan(dses_ctx* c, Job& j) {
   const int64_t hb = u16 ? ((bins + 1) / 2) * 4 : bins * 4;
   j.hist_bytes = (int)((hb + 15) & ~15LL);
   j.fused = c->opt.fuse_score && j.q == 0 && j.topk == 0 && (j.metric == DSES_METRIC_INLIER || j.nn == DSES_NN_GRID);
+  // Culling pays when the translation window (plus a target group's extent)
+  // covers a small part of the target: estimated fraction of (source, group)
+  // pairs that survive, per axis (window + group extent) / target extent.
+  double keep = 1.0;
+  for (int a = 0; a < 3; ++a) {
+    const double ext = (double)j.T->bbmax[a] - j.T->bbmin[a];
+    const double win = (double)j.E[a] * j.delta + j.T->gext[a];
+    keep *= ext > 0 ? std::min(1.0, win / ext) : 1.0;
+  }
+  j.sparse = c->opt.vote_sparse == 2 || (c->opt.vote_sparse == 0 && keep < 0.35);
 }
 
 int choose_p(dses_ctx* c, const std::vector<Job*>& jobs) {
@@ -551,6 +567,7 @@ PassDesc make_desc(const Job& j, int P, bool second) {
   d.slab_x = j.slab_x;
   d.n_slabs = j.n_slabs;
   d.hist_u16 = j.u16;
+  d.sparse = j.sparse ? 1 : 0;
   d.n_tchunks = (j.T->m + 32 * P - 1) / (32 * P);
   d.n_sgroups = 32 / gcd(d.n_tchunks, 32);
   d.eps2 = j.eps * j.eps;
@@ -641,7 +658,9 @@ void launch_pass(dses_ctx* c, const std::vector<PassPart>& parts, int P) {
     for (auto& e : ev) CK(cudaEventCreate(&e));
     CK(cudaEventRecord(ev[0], s));
   }
-  CK(launch_vote(L, P, ctas, s));
+  bool any_sparse = false;
+  for (auto& pp : parts) any_sparse |= pp.job->sparse;
+  CK(launch_vote(L, any_sparse && P == 8 ? 4 : P, any_sparse, ctas, s));
   if (ev[0]) CK(cudaEventRecord(ev[1], s));
   CK(launch_count(L, (int)total_rot, s));
   if (ev[0]) {
@@ -1307,6 +1326,7 @@ static int64_t* option_slot(dses_ctx* c, const char* key) {
   if (k == "serve_mem_budget") return &o.serve_mem_budget;
   if (k == "serve_tile_rotations") return &o.serve_tile_rotations;
   if (k == "record_timing") return &o.record_timing;
+  if (k == "vote_sparse") return &o.vote_sparse;
   if (k == "last_pass_ns") return &c->pass_ns;
   if (k == "last_pass_launches") return &c->pass_launches;
   if (k == "last_count_ns") return &c->count_ns;
@@ -1325,7 +1345,7 @@ dses_status dses_set_option(dses_ctx* c, const char* key, int64_t value) {
     if (!slot) invalid(std::string("unknown option ") + (key ? key : "(null)"));
     const std::string k(key);
     bool ok = true;
-    if (k == "hist_mode") ok = value >= 0 && value <= 2;
+    if (k == "hist_mode" || k == "vote_sparse") ok = value >= 0 && value <= 2;
     else if (k == "hist_budget_bytes") ok = value >= 1024 && value <= kHistBudget;
     else if (k == "points_per_thread") ok = value == 0 || value == 1 || value == 2 || value == 4 || value == 8;
     else if (k == "fuse_score" || k == "autotune" || k == "use_graphs" || k == "record_timing")

@@ -16,8 +16,9 @@ constexpr int kSrcChunk = 1024;
 constexpr int kGroup = 32;
 // Largest dynamic shared memory a CTA may request on sm_103a (227 KB).
 constexpr int kMaxSmem = 232448;
-// Static shared memory of the pass kernel (descriptor, reductions) plus headroom.
-constexpr int kPassStaticSmem = 2048;
+// Static shared memory of the pass kernel (descriptor, reductions, per-warp
+// culling thresholds) plus headroom.
+constexpr int kPassStaticSmem = 2048 + 32 * 8 * 8 * 4;
 // Histogram budget: what is left after the source chunk and static storage.
 constexpr int kHistBudget = kMaxSmem - kSrcChunk * 16 - kPassStaticSmem;
 
@@ -40,6 +41,7 @@ struct PassDesc {
   int slab_x;            // x-planes per histogram slab
   int n_slabs;
   int hist_u16;          // 1: two 16-bit counters per 32-bit word
+  int sparse;            // 1: cull (source, target group) pairs outside the window
   // vote work decomposition per rotation: items = n_tchunks x n_sgroups
   int n_tchunks;         // target chunks of 32 * P points
   int n_sgroups;         // source groups
@@ -78,7 +80,9 @@ struct PassLaunch {
 };
 
 // Hot path, kernel 1: vote -> mode (k*, V) per rotation (persistent, one CTA per SM).
-cudaError_t launch_vote(const PassLaunch& L, int points_per_thread, int grid_ctas, cudaStream_t s);
+// sparse: launch the instance that also carries the culled path (any problem
+// of the launch with d.sparse set); points_per_thread 8 only without it.
+cudaError_t launch_vote(const PassLaunch& L, int points_per_thread, bool sparse, int grid_ctas, cudaStream_t s);
 // Kernel 2: inlier count M at t* and, on the fused path, grid score + argmin.
 cudaError_t launch_count(const PassLaunch& L, int total_rot, cudaStream_t s);
 int pass_smem_bytes(int hist_bytes);

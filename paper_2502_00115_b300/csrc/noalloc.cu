@@ -169,7 +169,7 @@ extern "C" dses_status dses_vote_static(int device, void* cuda_stream, const flo
     L.tile_rot = tile;
     L.work_counter = reinterpret_cast<int*>(base + kOffCounter);
     L.hist_bytes = hist_bytes;
-    if (launch_vote(L, ppt, std::max(1, std::min(sms, tiles)), s) != cudaSuccess) {
+    if (launch_vote(L, ppt, false, std::max(1, std::min(sms, tiles)), s) != cudaSuccess) {
       cudaGetLastError();
       st = DSES_ERR_CUDA;
       break;

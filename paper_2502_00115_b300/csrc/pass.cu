@@ -204,6 +204,89 @@ __device__ __forceinline__ void vote_centred(const PassDesc& d, const float4* __
   }
 }
 
+// Sparse centred path, for translation boxes small against the target: the
+// P x 32 targets of an item are P groups of 32 Morton-consecutive points with
+// known bounding boxes. For each block of 32 sources the lanes test (source,
+// group) pairs against the source's translation window, widened by a margin
+// of kCullMargin lattice units (far above the FP32 rounding of w, so no pair
+// that could vote is dropped); only surviving (source, group) pairs are
+// voted, one group at a time over the set bits of its ballot.
+constexpr float kCullMargin = 1e-3f;
+
+template <int P, bool U16>
+__device__ __forceinline__ void vote_centred_sparse(const PassDesc& d, const float4* __restrict__ srcc, int nsrc,
+                                                    unsigned SX, uint32_t hist_base, int* item_ctr, int lane,
+                                                    float* __restrict__ thr) {
+  const int n_tchunks = d.n_tchunks, n_sgroups = d.n_sgroups;
+  const int n_items = n_tchunks * n_sgroups;
+  const int spg = (nsrc + n_sgroups - 1) / n_sgroups;
+  const unsigned Ey = (unsigned)d.E[1], Ez = (unsigned)d.E[2], Eyz = Ey * Ez;
+  const float inv = d.inv_delta;
+  const float hx = 0.5f * (float)SX, hy = 0.5f * (float)Ey, hz = 0.5f * (float)Ez;
+  const float mx = kMagic + (float)((SX - 1) / 2), my = kMagic + (float)((Ey - 1) / 2),
+              mz = kMagic + (float)((Ez - 1) / 2);
+  const uint32_t bias = kMagicBits * (Eyz + Ez + 1u);
+  const uint32_t abase32 = hist_base - 4u * bias;
+  const uint32_t abase16 = hist_base - 2u * bias;
+  for (int it = next_item(item_ctr, lane); it < n_items; it = next_item(item_ctr, lane)) {
+    const int tc = it % n_tchunks, sg = it / n_tchunks;
+    float ty[P][3];
+    load_targets(d.Yv, d.M, tc * P * 32, lane, P, ty);
+    // keep (source, group) iff s1_a <= c_a <= s2_a on every axis
+    if (lane < P) {
+      const int g = tc * P + lane;
+      float* t = thr + 8 * lane;
+      if (g < d.n_groups) {
+        const float4 lo = __ldg(d.gbox + 2 * g), hi = __ldg(d.gbox + 2 * g + 1);
+        t[0] = -hx - kCullMargin - hi.x * inv; t[1] = hx + kCullMargin - lo.x * inv;
+        t[2] = -hy - kCullMargin - hi.y * inv; t[3] = hy + kCullMargin - lo.y * inv;
+        t[4] = -hz - kCullMargin - hi.z * inv; t[5] = hz + kCullMargin - lo.z * inv;
+      } else {
+        t[0] = t[2] = t[4] = INFINITY;
+        t[1] = t[3] = t[5] = -INFINITY;
+      }
+    }
+    __syncwarp();
+    const int i0 = sg * spg, i1 = min(i0 + spg, nsrc);
+    for (int s0 = i0; s0 < i1; s0 += 32) {
+      const int mine = s0 + lane;
+      const bool valid = mine < i1;
+      const float4 cm = srcc[valid ? mine : i0];
+      uint32_t kmask[P];
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const float4 ta = *reinterpret_cast<const float4*>(thr + 8 * p);
+        const float2 tb = *reinterpret_cast<const float2*>(thr + 8 * p + 4);
+        const bool keep = valid && cm.x >= ta.x && cm.x <= ta.y && cm.y >= ta.z && cm.y <= ta.w && cm.z >= tb.x &&
+                          cm.z <= tb.y;
+        kmask[p] = __ballot_sync(0xffffffffu, keep);
+      }
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        uint32_t m = kmask[p];
+        while (m) {
+          const int j = __ffs(m) - 1;
+          m &= m - 1;
+          const float4 c = srcc[s0 + j];
+          const float wx = __fmaf_rn(ty[p][0], inv, c.x);
+          const float wy = __fmaf_rn(ty[p][1], inv, c.y);
+          const float wz = __fmaf_rn(ty[p][2], inv, c.z);
+          const uint32_t bx = __float_as_uint(__fadd_rn(wx, mx));
+          const uint32_t by = __float_as_uint(__fadd_rn(wy, my));
+          const uint32_t bz = __float_as_uint(__fadd_rn(wz, mz));
+          if (U16) {
+            const uint32_t b = bx * Eyz + (by * Ez + bz);
+            red_if_inside(abase16 + ((b >> 1) << 2), 1u + (b & 1u) * 0xffffu, wx, wy, wz, hx, hy, hz);
+          } else {
+            red_if_inside(abase32 + 4u * (bx * Eyz + (by * Ez + bz)), 1u, wx, wy, wz, hx, hy, hz);
+          }
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
 // Generic path (any extents): k_a = floor(w_a) by a round-down add, box test on
 // the integer indices.
 template <int P, bool U16>
@@ -238,12 +321,15 @@ __device__ __forceinline__ void vote_generic(const PassDesc& d, const float4* __
   }
 }
 
-template <int P>
+// SPARSE: this instance also carries the culled path (problems with
+// d.sparse); the dense instance leaves it out so it keeps its registers.
+template <int P, bool SPARSE>
 __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ PassDesc sd;
   __shared__ unsigned long long red64[32];
   __shared__ int s_item, s_prob, s_vote_item;
+  __shared__ __align__(16) float s_thr[SPARSE ? 32 : 1][8 * 8];
 
   uint32_t* hist = reinterpret_cast<uint32_t*>(smem);
   const uint32_t hist_base = (uint32_t)__cvta_generic_to_shared(hist);
@@ -320,7 +406,14 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
                                        fmaf(-uz, d.inv_delta, off2), 0.f);
           }
           __syncthreads();
-          if (centred) {
+          if (SPARSE && centred && d.sparse) {
+            if (d.hist_u16)
+              vote_centred_sparse<P, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane,
+                                           s_thr[SPARSE ? warp : 0]);
+            else
+              vote_centred_sparse<P, false>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane,
+                                            s_thr[SPARSE ? warp : 0]);
+          } else if (centred) {
             if (d.hist_u16)
               vote_centred<P, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane);
             else
@@ -439,17 +532,18 @@ __global__ void __launch_bounds__(256) count_kernel(PassLaunch L) {
   }
 }
 
-template <int P>
+template <int P, bool SPARSE>
 cudaError_t launch_vote_p(const PassLaunch& L, int grid_ctas, cudaStream_t s) {
   const int smem = pass_smem_bytes(L.hist_bytes);
   static int configured = 0;
   if (configured < smem) {
-    cudaError_t e = cudaFuncSetAttribute(vote_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(vote_kernel<P, SPARSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     configured = smem;
   }
   g_launches.fetch_add(1, std::memory_order_relaxed);
-  vote_kernel<P><<<grid_ctas, kPassThreads, smem, s>>>(L);
+  vote_kernel<P, SPARSE><<<grid_ctas, kPassThreads, smem, s>>>(L);
   return cudaGetLastError();
 }
 
@@ -457,12 +551,20 @@ cudaError_t launch_vote_p(const PassLaunch& L, int grid_ctas, cudaStream_t s) {
 
 int pass_smem_bytes(int hist_bytes) { return hist_bytes + kSrcChunk * (int)sizeof(float4); }
 
-cudaError_t launch_vote(const PassLaunch& L, int points_per_thread, int grid_ctas, cudaStream_t s) {
+cudaError_t launch_vote(const PassLaunch& L, int points_per_thread, bool sparse, int grid_ctas, cudaStream_t s) {
+  if (sparse) {
+    switch (points_per_thread) {
+      case 1: return launch_vote_p<1, true>(L, grid_ctas, s);
+      case 2: return launch_vote_p<2, true>(L, grid_ctas, s);
+      case 4: return launch_vote_p<4, true>(L, grid_ctas, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (points_per_thread) {
-    case 1: return launch_vote_p<1>(L, grid_ctas, s);
-    case 2: return launch_vote_p<2>(L, grid_ctas, s);
-    case 4: return launch_vote_p<4>(L, grid_ctas, s);
-    case 8: return launch_vote_p<8>(L, grid_ctas, s);
+    case 1: return launch_vote_p<1, false>(L, grid_ctas, s);
+    case 2: return launch_vote_p<2, false>(L, grid_ctas, s);
+    case 4: return launch_vote_p<4, false>(L, grid_ctas, s);
+    case 8: return launch_vote_p<8, false>(L, grid_ctas, s);
     default: return cudaErrorInvalidValue;
   }
 }

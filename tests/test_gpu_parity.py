@@ -162,9 +162,10 @@ def test_histogram_modes_and_launch_shapes_agree(ctx):
     base = ctx.debug(pb, n)
     variants = [dict(hist_mode=1), dict(hist_mode=2), dict(hist_mode=1, hist_budget_bytes=20000),
                 dict(hist_mode=2, hist_budget_bytes=9000), dict(points_per_thread=1), dict(points_per_thread=2),
-                dict(points_per_thread=8), dict(fuse_score=0), dict(tile_rotations=1)]
+                dict(points_per_thread=8), dict(fuse_score=0), dict(tile_rotations=1), dict(vote_sparse=2),
+                dict(vote_sparse=2, points_per_thread=2)]
     defaults = {k: ctx.get_option(k) for k in ("hist_mode", "hist_budget_bytes", "points_per_thread", "fuse_score",
-                                               "tile_rotations")}
+                                               "tile_rotations", "vote_sparse")}
     try:
         for v in variants:
             for key, val in v.items():
@@ -205,6 +206,35 @@ def test_modelnet_full_size_sampled_rotations(ctx):
     # the winner is a plausible pose (grid resolution ~3.75 degrees)
     ang = np.degrees(np.arccos(np.clip((np.trace(np.array(r.R[:]).reshape(3, 3).T @ p.R_true) - 1) / 2, -1, 1)))
     assert ang < 10.0, ang
+    ctx.destroy_target(t)
+
+
+def test_robot_like_full_size_sampled_rotations(ctx):
+    # 2,359,296 coarse rotations + Euler boxes around the best 32 (the culled
+    # vote path); sampled first-pass rotations against the oracle, second-pass
+    # consistency, and pose quality
+    p = synth.robot_like_problem(0)
+    t = ctx.create_target(p.Y, grid_cap=p.grid_cap)
+    gp = gpu_params(p, nn_mode="grid", huber_h=p.huber_h)
+    pb = ctx.problem(t, p.X, capi.hopf_grid(p.hopf_n), gp)
+    n1 = 72 * p.hopf_n**3
+    n = p.n_rotations
+    k, V, M, C, r = ctx.debug(pb, n)
+    assert r.status == 0
+    P = oracle_params(p, gp, p.grid_cap)
+    rng = np.random.default_rng(1)
+    idx = sorted(set(rng.choice(n1, size=8, replace=False).tolist()) | {int(np.argmax(V[:n1]))})
+    Rs = np.stack([oracle.hopf_rotation(p.hopf_n, i) for i in idx])
+    rep = check_rotations(p.X, p.Y, Rs, P, k, V, M, None, idx)
+    assert rep.ok(), rep.summary()
+    # each second-pass box is centred on one of the best first-pass candidates
+    B = (2 * p.refine_K + 1) ** 3
+    best_first = np.lexsort((np.arange(n1), C[:n1]))[: p.refine_top_k]
+    for c, rc in enumerate(best_first):
+        assert V[n1 + c * B + B // 2] == V[rc] and M[n1 + c * B + B // 2] == M[rc]
+    assert r.cost <= C[:n1].min() + 1e-7
+    ang = np.degrees(np.arccos(np.clip((np.trace(np.array(r.R[:]).reshape(3, 3).T @ p.R_true) - 1) / 2, -1, 1)))
+    assert ang < 3.0, ang
     ctx.destroy_target(t)
 
 
