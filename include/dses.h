@@ -205,7 +205,9 @@ dses_status dses_target_distance_grid(dses_ctx* ctx, const dses_target* target, 
  *   "serve_max_batch"      requests the serving worker runs together
  *   "serve_queue_cap"      submitted requests waiting for admission
  *   "serve_mem_budget"     device bytes the serving worker may hold for requests
- *   "serve_tile_rotations" rotations per request per serving iteration
+ *   "serve_tile_rotations" most rotations one request takes per serving iteration
+ *   "serve_iter_pairs"     pair votes per serving iteration (requests in arrival
+ *                          order fill it; default 3e10, ~20 ms of vote work)
  *   "vote_sparse"          0 auto, 1 dense vote, 2 cull (source, target group) pairs
  *                          outside the translation window (pays for small boxes)
  *   "record_timing"        1: time every rotation pass with CUDA events on the

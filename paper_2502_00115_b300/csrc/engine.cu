@@ -81,6 +81,26 @@ struct CellList {
   float4* sorted = nullptr; // m points in cell order
 };
 
+// Pinned host staging for host-to-device uploads of one pipeline run (the
+// copies read it asynchronously, and a captured graph replays from it).
+struct Stage {
+  char* host = nullptr;
+  size_t cap = 0, used = 0;
+  void reserve(size_t bytes) {
+    if (bytes <= cap) return;
+    if (host) cudaFreeHost(host);
+    host = nullptr;
+    cap = 0;
+    CK(cudaMallocHost((void**)&host, bytes));
+    cap = bytes;
+  }
+  void release() {
+    if (host) cudaFreeHost(host);
+    host = nullptr;
+    cap = used = 0;
+  }
+};
+
 struct Options {
   int64_t hist_mode = 0;
   int64_t hist_budget = kHistBudget;
@@ -92,7 +112,8 @@ struct Options {
   int64_t serve_max_batch = 16;
   int64_t serve_queue_cap = 100000;
   int64_t serve_mem_budget = 8LL << 30;
-  int64_t serve_tile_rotations = 8192;
+  int64_t serve_tile_rotations = 1LL << 30;
+  int64_t serve_iter_pairs = 30000000000LL;
   int64_t record_timing = 0;
   int64_t vote_sparse = 0;
 };
@@ -153,6 +174,20 @@ struct dses_ctx {
   int64_t count_ns = 0;    // ... and of its inlier-count / score launches
   int64_t pass_launches = 0;
   int64_t launch_snapshot = 0;
+  // host staging: blocking calls, the serving worker, and the one in use
+  Stage stage, serve_stage;
+  Stage* cur_stage = nullptr;
+  bool capturing = false;
+  // captured batch graphs by problem signature
+  struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    Stage stage;
+    dses_result* res = nullptr;  // pinned results written by the graph
+    std::vector<std::pair<size_t, size_t>> src_slots;  // (stage offset, bytes) per problem, host sources
+  };
+  std::map<std::string, GraphEntry> graphs;
+  std::map<std::string, int> graph_seen;
+  std::map<std::string, int> tuned_p;  // autotuner: problem-size bucket -> points per thread
 };
 
 namespace {
@@ -341,7 +376,30 @@ struct Job {
   dses_result* res = nullptr;
   size_t bytes = 0;
   int ksel_k = 0;
+  size_t src_stage_off = 0;  // where the host source sits in the pinned stage
 };
+
+// Copies bytes into the current pinned stage; returns the staged pointer.
+const void* stage_put(dses_ctx* c, const void* src, size_t bytes, size_t* offset = nullptr) {
+  Stage* st = c->cur_stage;
+  const size_t off = (st->used + 63) & ~(size_t)63;
+  if (!st->host || off + bytes > st->cap) throw Error{DSES_ERR_CUDA, "internal: host staging too small"};
+  std::memcpy(st->host + off, src, bytes);
+  st->used = off + bytes;
+  if (offset) *offset = off;
+  return st->host + off;
+}
+
+// Upper bound of the staging bytes one pipeline run over `jobs` uses.
+size_t stage_bytes(const std::vector<Job*>& jobs) {
+  size_t b = 4096;
+  for (auto* j : jobs) {
+    b += 64 * 16 + 6 * sizeof(PassDesc) + 2 * 16 + sizeof(FinalDesc) + 72;
+    if (!j->prob->src_is_device) b += 12 * (size_t)j->N;
+    if (j->prob->grid.kind == DSES_GRID_EXPLICIT) b += 36 * (size_t)j->n_first;
+  }
+  return b;
+}
 
 void resolve(dses_ctx* c, const dses_problem* pb, Job& j) {
   if (!pb) invalid("problem is NULL");
@@ -514,7 +572,8 @@ void stage_setup(dses_ctx* c, Job& j) {
   carve(j);
   j.cl = cell_list(c, j.T, j.eps);
   if (j.Xown) {
-    CK(cudaMemcpyAsync(j.Xown, j.prob->src, 12 * (size_t)j.N, cudaMemcpyHostToDevice, s));
+    const void* st = stage_put(c, j.prob->src, 12 * (size_t)j.N, &j.src_stage_off);
+    CK(cudaMemcpyAsync(j.Xown, st, 12 * (size_t)j.N, cudaMemcpyHostToDevice, s));
     j.X = j.Xown;
   } else {
     j.X = j.prob->src;
@@ -523,12 +582,13 @@ void stage_setup(dses_ctx* c, Job& j) {
   if (g.kind == DSES_GRID_HOPF) {
     j.rot = hopf_grid(c, g.hopf_n);
   } else if (g.kind == DSES_GRID_EULER_BOX) {
-    CK(cudaMemcpyAsync(j.R0, g.R0, sizeof(double) * 9, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(j.R0, stage_put(c, g.R0, sizeof(double) * 9), sizeof(double) * 9, cudaMemcpyHostToDevice, s));
     CK(launch_euler_box_single(j.R0, g.K, g.delta_r, j.rot_own, s));
     j.rot = j.rot_own;
   } else {
     if (!finite3(g.explicit_R, 3 * g.n_explicit)) invalid("explicit rotations have a non-finite entry");
-    CK(cudaMemcpyAsync(j.rot_own, g.explicit_R, 36 * (size_t)g.n_explicit, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(j.rot_own, stage_put(c, g.explicit_R, 36 * (size_t)g.n_explicit), 36 * (size_t)g.n_explicit,
+                       cudaMemcpyHostToDevice, s));
     j.rot = j.rot_own;
   }
   CK(cudaMemsetAsync(j.acc, 0, 16, s));
@@ -640,9 +700,12 @@ void launch_pass(dses_ctx* c, const std::vector<PassPart>& parts, int P) {
   DevMem m;
   m.alloc(db + 2 * pb + 256, s);
   char* base = (char*)m.p;
-  CK(cudaMemcpyAsync(base, descs.data(), sizeof(PassDesc) * descs.size(), cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(base + db, prefix.data(), sizeof(int) * prefix.size(), cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(base + db + pb, rprefix.data(), sizeof(int) * rprefix.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(base, stage_put(c, descs.data(), sizeof(PassDesc) * descs.size()),
+                     sizeof(PassDesc) * descs.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(base + db, stage_put(c, prefix.data(), sizeof(int) * prefix.size()), sizeof(int) * prefix.size(),
+                     cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(base + db + pb, stage_put(c, rprefix.data(), sizeof(int) * rprefix.size()),
+                     sizeof(int) * rprefix.size(), cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(base + db + 2 * pb, 0, 4, s));
   PassLaunch L;
   L.probs = (const PassDesc*)base;
@@ -654,7 +717,7 @@ void launch_pass(dses_ctx* c, const std::vector<PassPart>& parts, int P) {
   L.hist_bytes = hist;
   const int ctas = std::max(1, std::min(c->sms, prefix.back()));
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
-  if (c->opt.record_timing) {
+  if (c->opt.record_timing && !c->capturing) {
     for (auto& e : ev) CK(cudaEventCreate(&e));
     CK(cudaEventRecord(ev[0], s));
   }
@@ -759,27 +822,91 @@ void stage_finalize(dses_ctx* c, std::vector<Job*>& jobs) {
   }
   DevMem m;
   m.alloc(sizeof(FinalDesc) * fd.size(), s);
-  CK(cudaMemcpyAsync(m.p, fd.data(), sizeof(FinalDesc) * fd.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(m.p, stage_put(c, fd.data(), sizeof(FinalDesc) * fd.size()), sizeof(FinalDesc) * fd.size(),
+                     cudaMemcpyHostToDevice, s));
   CK(launch_finalize((const FinalDesc*)m.p, (int)fd.size(), s));
   m.release();
 }
 
+// Autotuner: points per thread of the vote for a problem-size bucket, chosen
+// once per bucket by timing each candidate on a slice of the problem's own
+// rotations (the trial only rewrites per-rotation values the pass rewrites
+// identically).
+int pick_p(dses_ctx* c, Job& j) {
+  if (c->opt.points_per_thread > 0) return (int)c->opt.points_per_thread;
+  std::vector<Job*> one{&j};
+  if (!c->opt.autotune) return choose_p(c, one);
+  auto lg = [](int64_t v) { int b = 0; while ((1LL << b) < v) ++b; return b; };
+  char key[96];
+  snprintf(key, sizeof(key), "m%d n%d b%d s%d u%d", lg(j.T->m), lg(j.N), lg((int64_t)j.E[0] * j.E[1] * j.E[2]),
+           (int)j.sparse, j.u16);
+  auto it = c->tuned_p.find(key);
+  if (it != c->tuned_p.end()) return it->second;
+  if (c->capturing) return choose_p(c, one);
+  const int64_t slice = std::min<int64_t>(j.n_first, (int64_t)c->sms * 16);
+  float best_ms = 1e30f;
+  int best_p = choose_p(c, one);
+  const int cands[4] = {1, 2, 4, 8};
+  for (int P : cands) {
+    if (j.sparse && P == 8) continue;
+    std::vector<PassDesc> d{make_desc(j, P, false)};
+    d[0].n_rot = (int)slice;
+    const int tile = 1;
+    std::vector<int> tp{0, (int)slice}, rp{0, (int)slice};
+    DevMem m;
+    m.alloc(4096, c->stream);
+    char* base = (char*)m.p;
+    CK(cudaMemcpyAsync(base, stage_put(c, d.data(), sizeof(PassDesc)), sizeof(PassDesc), cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaMemcpyAsync(base + 1024, stage_put(c, tp.data(), 8), 8, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(base + 2048, stage_put(c, rp.data(), 8), 8, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(base + 3072, 0, 4, c->stream));
+    PassLaunch L;
+    L.probs = (const PassDesc*)base;
+    L.tile_prefix = (const int*)(base + 1024);
+    L.rot_prefix = (const int*)(base + 2048);
+    L.n_probs = 1;
+    L.tile_rot = tile;
+    L.work_counter = (int*)(base + 3072);
+    L.hist_bytes = j.hist_bytes;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, c->stream));
+    CK(launch_vote(L, P, j.sparse, std::min<int>(c->sms, (int)slice), c->stream));
+    CK(cudaEventRecord(e1, c->stream));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    m.release();
+    if (ms < best_ms) {
+      best_ms = ms;
+      best_p = P;
+    }
+  }
+  c->tuned_p[key] = best_p;
+  return best_p;
+}
+
 // The whole pipeline for a set of jobs; results land in each job's device
-// result slot. No host synchronisation inside.
+// result slot. No host synchronisation inside (except autotuner trials).
 void run_pipeline(dses_ctx* c, std::vector<Job*>& jobs) {
   for (auto* j : jobs) stage_setup(c, *j);
-  const int P = choose_p(c, jobs);
-  std::vector<PassPart> parts;
-  for (auto* j : jobs) parts.push_back({j, false, 0, j->n_first});
-  launch_pass(c, parts, P);
+  // one persistent launch per points-per-thread shape (normally one)
+  std::map<int, std::vector<PassPart>> first, fine;
+  std::map<Job*, int> shape;
+  for (auto* j : jobs) shape[j] = pick_p(c, *j);
+  for (auto* j : jobs) first[shape[j]].push_back({j, false, 0, j->n_first});
+  for (auto& kv : first) launch_pass(c, kv.second, kv.first);
   for (auto* j : jobs) stage_candidates(c, *j, false);
-  std::vector<PassPart> fine;
   for (auto* j : jobs)
     if (j->rtop > 0) {
       stage_refine_grid(c, *j);
-      fine.push_back({j, true, 0, j->n_fine});
+      fine[shape[j]].push_back({j, true, 0, j->n_fine});
     }
-  launch_pass(c, fine, P);
+  for (auto& kv : fine) launch_pass(c, kv.second, kv.first);
   for (auto* j : jobs)
     if (j->rtop > 0) stage_candidates(c, *j, true);
   stage_finalize(c, jobs);
@@ -841,6 +968,20 @@ void worker_loop(dses_ctx* c) {
     bool launched = false;
     {
       std::lock_guard<std::recursive_mutex> g(c->mu);
+      {
+        std::vector<Job*> all;
+        for (auto& r : active) all.push_back(&r->job);
+        c->cur_stage = &c->serve_stage;
+        try {
+          c->serve_stage.reserve(2 * stage_bytes(all));
+        } catch (const Error& e) {
+          for (auto& r : active) {
+            fail_request(*r, e);
+            r->state = 2;
+          }
+        }
+        c->serve_stage.used = 0;
+      }
       // set up newly admitted requests
       for (auto& r : active) {
         if (r->state.load() != 0) continue;
@@ -852,16 +993,23 @@ void worker_loop(dses_ctx* c) {
           r->state = 2;
         }
       }
-      // one iteration: the next slice of every running request
+      // one iteration: requests in admission order take rotations until the
+      // iteration's pair-vote budget is spent (the oldest request finishes
+      // first; the next one starts in the same launch when budget is left)
       std::vector<PassPart> parts;
       std::vector<Job*> jobs;
       const int64_t slice = std::max<int64_t>(1, c->opt.serve_tile_rotations);
+      double budget = (double)c->opt.serve_iter_pairs;
       for (auto& r : active) {
         if (r->state.load() != 1) continue;
-        const int64_t a = r->next, b = std::min(r->job.n_first, a + slice);
+        if (budget <= 0) break;
+        const double per_rot = (double)r->job.N * (double)r->job.T->m;
+        const int64_t want = std::max<int64_t>(1, (int64_t)(budget / per_rot));
+        const int64_t a = r->next, b = std::min({r->job.n_first, a + slice, a + want});
         parts.push_back({&r->job, false, a, b});
         jobs.push_back(&r->job);
         r->next = b;
+        budget -= (double)(b - a) * per_rot;
       }
       try {
         if (!parts.empty()) launch_pass(c, parts, choose_p(c, jobs));
@@ -930,6 +1078,109 @@ void worker_loop(dses_ctx* c) {
     }
     active.swap(keep);
   }
+}
+
+// ---------------------------------------------------------------------------
+// CUDA graphs for repeated batches. A batch whose problems have the same
+// shapes, targets, grids and parameters as an earlier call is captured once
+// (every upload comes from the graph's own pinned stage, every scratch buffer
+// is a stream-ordered allocation inside the graph) and then replayed: the new
+// host source clouds are copied into the stage and the graph is launched.
+
+std::string graph_key(dses_ctx* c, const std::vector<Job*>& jobs) {
+  if (c->opt.record_timing) return std::string();
+  std::string k;
+  char buf[512];
+  snprintf(buf, sizeof(buf), "o%lld,%lld,%lld,%lld,%lld,%lld,%lld|", (long long)c->opt.hist_mode,
+           (long long)c->opt.hist_budget, (long long)c->opt.points_per_thread, (long long)c->opt.fuse_score,
+           (long long)c->opt.tile_rotations, (long long)c->opt.vote_sparse, (long long)c->opt.autotune);
+  k += buf;
+  for (auto* j : jobs) {
+    const dses_problem& pb = *j->prob;
+    if (pb.grid.kind == DSES_GRID_EXPLICIT) return std::string();  // grid contents not tracked
+    const dses_params& P = pb.params;
+    snprintf(buf, sizeof(buf), "%p,%d,%p,%lld,%d,%d,%d,%.17g|", (const void*)pb.target, pb.src_is_device,
+             pb.src_is_device ? (const void*)pb.src : nullptr, (long long)pb.n_src, pb.grid.kind, pb.grid.hopf_n,
+             pb.grid.K, pb.grid.delta_r);
+    k += buf;
+    for (int a = 0; a < 9; ++a) {
+      snprintf(buf, sizeof(buf), "%.17g,", pb.grid.R0[a]);
+      k += buf;
+    }
+    snprintf(buf, sizeof(buf), "|%d,%a,%a,%a,%a,%a,%a,%a,%a,%a,%a,%a,%d,%d,%d,%d,%d,%.17g;", P.metric, P.epsilon,
+             P.delta_t, P.tau, P.huber_h, P.p, P.t_center[0], P.t_center[1], P.t_center[2], P.t_half[0],
+             P.t_half[1], P.t_half[2], P.q_milli, P.top_k, P.nn_mode, P.refine_top_k, P.refine_K, P.refine_delta_r);
+    k += buf;
+  }
+  return k;
+}
+
+void free_graph(dses_ctx::GraphEntry& e) {
+  if (e.exec) cudaGraphExecDestroy(e.exec);
+  e.exec = nullptr;
+  e.stage.release();
+  if (e.res) cudaFreeHost(e.res);
+  e.res = nullptr;
+}
+
+dses_status replay_graph(dses_ctx* c, dses_ctx::GraphEntry& e, std::vector<Job*>& jobs, dses_result* out) {
+  for (size_t i = 0; i < jobs.size(); ++i)
+    if (!jobs[i]->prob->src_is_device)
+      std::memcpy(e.stage.host + e.src_slots[i].first, jobs[i]->prob->src, e.src_slots[i].second);
+  CK(cudaGraphLaunch(e.exec, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  dses_status st = DSES_OK;
+  for (size_t i = 0; i < jobs.size(); ++i) {
+    out[i] = e.res[i];
+    if (st == DSES_OK && out[i].status != DSES_OK) st = (dses_status)out[i].status;
+  }
+  return st;
+}
+
+dses_status capture_and_replay(dses_ctx* c, const std::string& key, std::vector<Job*>& jobs, dses_result* out) {
+  if (c->graphs.size() >= 8) {  // bounded cache: drop the oldest-keyed entry
+    free_graph(c->graphs.begin()->second);
+    c->graphs.erase(c->graphs.begin());
+  }
+  dses_ctx::GraphEntry e;
+  e.stage.reserve(stage_bytes(jobs));
+  CK(cudaMallocHost((void**)&e.res, sizeof(dses_result) * jobs.size()));
+  c->cur_stage = &e.stage;
+  e.stage.used = 0;
+  cudaStream_t s = c->stream;
+  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+  c->capturing = true;
+  cudaGraph_t g = nullptr;
+  try {
+    run_pipeline(c, jobs);
+    for (size_t i = 0; i < jobs.size(); ++i)
+      CK(cudaMemcpyAsync(e.res + i, jobs[i]->res, sizeof(dses_result), cudaMemcpyDeviceToHost, s));
+    for (auto* j : jobs) j->mem.release();
+  } catch (...) {
+    c->capturing = false;
+    cudaStreamEndCapture(s, &g);
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    free_graph(e);
+    throw;
+  }
+  c->capturing = false;
+  CK(cudaStreamEndCapture(s, &g));
+  const cudaError_t ie = cudaGraphInstantiate(&e.exec, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) {
+    cudaGetLastError();
+    free_graph(e);
+    throw Error{DSES_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie)};
+  }
+  e.src_slots.resize(jobs.size());
+  for (size_t i = 0; i < jobs.size(); ++i) e.src_slots[i] = {jobs[i]->src_stage_off, 12 * (size_t)jobs[i]->N};
+  auto& slot = c->graphs[key];
+  slot = e;
+  e.exec = nullptr;
+  e.res = nullptr;
+  e.stage.host = nullptr;
+  return replay_graph(c, slot, jobs, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -1061,6 +1312,9 @@ dses_status dses_destroy(dses_ctx* c) {
   for (auto* T : c->targets) free_target(T);
   for (auto& h : c->hopf) cudaFree(h.second);
   if (c->pinned_res) cudaFreeHost(c->pinned_res);
+  for (auto& g : c->graphs) free_graph(g.second);
+  c->stage.release();
+  c->serve_stage.release();
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
   return DSES_OK;
@@ -1149,8 +1403,18 @@ dses_status dses_register_batch(dses_ctx* c, const dses_problem* problems, int32
       plan(c, *owned.back());
       jobs.push_back(owned.back().get());
     }
-    run_pipeline(c, jobs);
-    st = finish_results(c, jobs, out);
+    const std::string key = c->opt.use_graphs ? graph_key(c, jobs) : std::string();
+    if (!key.empty() && c->graphs.count(key)) {
+      st = replay_graph(c, c->graphs[key], jobs, out);
+    } else if (!key.empty() && ++c->graph_seen[key] >= 2) {
+      st = capture_and_replay(c, key, jobs, out);
+    } else {
+      c->cur_stage = &c->stage;
+      c->stage.reserve(stage_bytes(jobs));
+      c->stage.used = 0;
+      run_pipeline(c, jobs);
+      st = finish_results(c, jobs, out);
+    }
     if (st != DSES_OK) c->err = "a problem found no candidate (no pair voted inside its translation box)";
   });
   return gs != DSES_OK ? gs : st;
@@ -1171,6 +1435,9 @@ dses_status dses_debug_per_rotation(dses_ctx* c, const dses_problem* problem, in
     resolve(c, problem, job);
     plan(c, job);
     std::vector<Job*> jobs{&job};
+    c->cur_stage = &c->stage;
+    c->stage.reserve(stage_bytes(jobs));
+    c->stage.used = 0;
     run_pipeline(c, jobs);
     const size_t n = (size_t)job.n_total;
     std::vector<int4> kv(n);
@@ -1325,6 +1592,7 @@ static int64_t* option_slot(dses_ctx* c, const char* key) {
   if (k == "serve_queue_cap") return &o.serve_queue_cap;
   if (k == "serve_mem_budget") return &o.serve_mem_budget;
   if (k == "serve_tile_rotations") return &o.serve_tile_rotations;
+  if (k == "serve_iter_pairs") return &o.serve_iter_pairs;
   if (k == "record_timing") return &o.record_timing;
   if (k == "vote_sparse") return &o.vote_sparse;
   if (k == "last_pass_ns") return &c->pass_ns;

@@ -495,25 +495,39 @@ __global__ void __launch_bounds__(256) count_kernel(PassLaunch L) {
     const bool grid_cost = d.fuse_score && d.metric != 0;
     int cnt = 0;
     float csum = 0.f;
-    for (int i = lane; i < d.N; i += 32) {
-      const float x = __ldg(d.X + 3 * (size_t)i), y = __ldg(d.X + 3 * (size_t)i + 1),
-                  z = __ldg(d.X + 3 * (size_t)i + 2);
-      const float qx = fmaf(R[0], x, fmaf(R[1], y, R[2] * z)) + tx;
-      const float qy = fmaf(R[3], x, fmaf(R[4], y, R[5] * z)) + ty;
-      const float qz = fmaf(R[6], x, fmaf(R[7], y, R[8] * z)) + tz;
-      // The capped distance field is 1-Lipschitz, so its trilinear interpolant
-      // between voxel centres is within grid_err of min(d, cap); only queries
-      // within that band of epsilon need the exact cell-list search.
-      const float dg = grid_lookup(d, qx, qy, qz);
-      bool inl;
-      if (dg >= d.eps + d.grid_err)
-        inl = false;
-      else if (dg < d.eps - d.grid_err && d.gcap > d.eps)
-        inl = true;
-      else
-        inl = has_inlier(d, qx, qy, qz);
-      cnt += inl ? 1 : 0;
-      if (grid_cost) csum += rho(d.metric, dg, d.eps, d.tau, d.huber_h, d.p_exp);
+    // two source points per lane per step: their grid lookups are in flight together
+    for (int i0 = lane; i0 < d.N; i0 += 64) {
+      float qx[2], qy[2], qz[2], dg[2];
+      bool live[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int i = i0 + 32 * u;
+        live[u] = i < d.N;
+        const int ii = live[u] ? i : i0;
+        const float x = __ldg(d.X + 3 * (size_t)ii), y = __ldg(d.X + 3 * (size_t)ii + 1),
+                    z = __ldg(d.X + 3 * (size_t)ii + 2);
+        qx[u] = fmaf(R[0], x, fmaf(R[1], y, R[2] * z)) + tx;
+        qy[u] = fmaf(R[3], x, fmaf(R[4], y, R[5] * z)) + ty;
+        qz[u] = fmaf(R[6], x, fmaf(R[7], y, R[8] * z)) + tz;
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) dg[u] = grid_lookup(d, qx[u], qy[u], qz[u]);
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        if (!live[u]) continue;
+        // The capped distance field is 1-Lipschitz, so its trilinear
+        // interpolant between voxel centres is within grid_err of min(d, cap);
+        // only queries within that band of epsilon need the exact cell search.
+        bool inl;
+        if (dg[u] >= d.eps + d.grid_err)
+          inl = false;
+        else if (dg[u] < d.eps - d.grid_err && d.gcap > d.eps)
+          inl = true;
+        else
+          inl = has_inlier(d, qx[u], qy[u], qz[u]);
+        cnt += inl ? 1 : 0;
+        if (grid_cost) csum += rho(d.metric, dg[u], d.eps, d.tau, d.huber_h, d.p_exp);
+      }
     }
 #pragma unroll
     for (int k = 16; k > 0; k >>= 1) {

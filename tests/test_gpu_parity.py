@@ -257,6 +257,46 @@ def test_batch_equals_solo(ctx):
         ctx.destroy_target(t)
 
 
+def test_graph_replayed_batches_equal_solo(ctx):
+    # call 1 runs the pipeline, call 2 captures it as a CUDA graph and replays,
+    # call 3 replays with new source clouds of the same shapes
+    probs = [synth.tiny_problem(s, hopf_n=2) for s in range(3)]
+    probs.append(synth.modelnet_like_problem(4, m=400, keep=0.6, hopf_n=2))
+    targets = [ctx.create_target(p.Y, grid_cap=2 * p.tau) for p in probs]
+    mk = lambda X: [ctx.problem(t, x, capi.hopf_grid(p.hopf_n), gpu_params(p, nn_mode="grid"))
+                    for t, p, x in zip(targets, probs, X)]
+    X1 = [p.X for p in probs]
+    rng = np.random.default_rng(5)
+    X2 = [(p.X + rng.normal(scale=0.01, size=p.X.shape)).astype(np.float32) for p in probs]
+    for X in (X1, X1, X2, X2):
+        pbs = mk(X)
+        batch = [capi.result_dict(r) for r in ctx.register_batch(pbs)]
+        solo = [capi.result_dict(ctx.register(pb)) for pb in pbs]
+        for a, b in zip(solo, batch):
+            assert a["rot_index"] == b["rot_index"] and a["inliers"] == b["inliers"] and a["votes"] == b["votes"]
+            assert np.array_equal(a["t"], b["t"]) and a["cost"] == b["cost"]
+    for t in targets:
+        ctx.destroy_target(t)
+
+
+def test_autotuned_shapes_give_identical_results(ctx):
+    p = synth.modelnet_like_problem(6, m=700, keep=0.7, hopf_n=3)
+    t = ctx.create_target(p.Y, grid_cap=2 * p.tau)
+    pb = ctx.problem(t, p.X, capi.hopf_grid(3), gpu_params(p, nn_mode="grid"))
+    base = ctx.debug(pb, 72 * 27)
+    ctx.set_option("autotune", 1)
+    try:
+        tuned = ctx.debug(pb, 72 * 27)
+        tuned2 = ctx.debug(pb, 72 * 27)
+    finally:
+        ctx.set_option("autotune", 0)
+    for other in (tuned, tuned2):
+        for a, b in zip(base[:3], other[:3]):
+            assert np.array_equal(a, b)
+        assert other[4].rot_index == base[4].rot_index
+    ctx.destroy_target(t)
+
+
 def test_theorem_case_exact_recovery_on_gpu(ctx):
     rng = np.random.default_rng(8)
     delta = 0.05
@@ -432,7 +472,7 @@ def test_serving_results_equal_solo(ctx):
         assert len(out) == len(tickets)
         assert capi.dses_poll(ctx.h, tickets[0])[0] == capi.DSES_ERR_UNKNOWN_TICKET
     finally:
-        ctx.set_option("serve_tile_rotations", 8192)
+        ctx.set_option("serve_tile_rotations", 1 << 30)
     for tk, a in zip(tickets, solo):
         b = out[tk]
         assert a["rot_index"] == b["rot_index"] and a["inliers"] == b["inliers"] and a["votes"] == b["votes"]
