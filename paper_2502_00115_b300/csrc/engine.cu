@@ -649,10 +649,9 @@ PassDesc make_desc(const Job& j, int P, bool second) {
   d.G = j.T->G;
   d.gcap = j.T->gcap;
   {
-    // sqrt(3) times the largest voxel edge, plus a margin far above the FP32
-    // error of the stored distances and of the interpolation
-    const double hmax = std::max({(double)j.T->gh[0], (double)j.T->gh[1], (double)j.T->gh[2]});
-    d.grid_err = (float)(std::sqrt(3.0) * hmax * 1.0001 + 1e-5 + 1e-5 * j.T->gcap);
+    // margin of the grid distance bounds: far above the FP32 error of the
+    // stored distances and of the corner distances
+    d.grid_err = (float)(1e-5 + 1e-5 * j.T->gcap);
   }
   d.out_base = 0;
   d.kv = j.kv;

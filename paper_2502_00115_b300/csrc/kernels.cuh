@@ -58,7 +58,7 @@ struct PassDesc {
   const float* D;        // G^3 truncated distance grid
   int G;
   float glo[3], ginv_h[3], gcap;
-  float grid_err;        // bound on |interpolated - exact capped distance| (sqrt(3) max h + margin)
+  float grid_err;        // FP32 margin of the distance bounds from the grid
   // outputs, indexed by (global rotation index - out_base)
   uint32_t out_base;
   int4* kv;              // (kx, ky, kz, V)

@@ -83,6 +83,54 @@ __device__ __forceinline__ float grid_lookup(const PassDesc& d, float qx, float 
   return c0 + fx * (c1 - c0);
 }
 
+// Trilinear value of the distance grid at q (as grid_lookup) together with
+// bounds on the exact nearest-target distance d(q): the stored values are
+// min(d, cap) at voxel centres and d is 1-Lipschitz, so every corner c_k used
+// gives D_k - |q - c_k| <= d(q), and, if D_k < cap, d(q) <= D_k + |q - c_k|.
+__device__ __forceinline__ float grid_lookup_bounds(const PassDesc& d, float qx, float qy, float qz, float* lb,
+                                                    float* ub) {
+  const float G = (float)d.G;
+  const float ux = (qx - d.glo[0]) * d.ginv_h[0];
+  const float uy = (qy - d.glo[1]) * d.ginv_h[1];
+  const float uz = (qz - d.glo[2]) * d.ginv_h[2];
+  if (!(ux >= 0.f && ux <= G && uy >= 0.f && uy <= G && uz >= 0.f && uz <= G)) {
+    // outside the grid box every target lies at least cap + h away
+    *lb = d.gcap;
+    *ub = INFINITY;
+    return d.gcap;
+  }
+  const float gx = fminf(fmaxf(ux - 0.5f, 0.f), G - 1.f);
+  const float gy = fminf(fmaxf(uy - 0.5f, 0.f), G - 1.f);
+  const float gz = fminf(fmaxf(uz - 0.5f, 0.f), G - 1.f);
+  const int ix = min((int)gx, d.G - 2), iy = min((int)gy, d.G - 2), iz = min((int)gz, d.G - 2);
+  const float fx = gx - (float)ix, fy = gy - (float)iy, fz = gz - (float)iz;
+  const float* b = d.D + ((size_t)ix * d.G + iy) * d.G + iz;
+  const size_t sy = d.G, sx = (size_t)d.G * d.G;
+  float v[8];
+  v[0] = __ldg(b); v[1] = __ldg(b + 1); v[2] = __ldg(b + sy); v[3] = __ldg(b + sy + 1);
+  v[4] = __ldg(b + sx); v[5] = __ldg(b + sx + 1); v[6] = __ldg(b + sx + sy); v[7] = __ldg(b + sx + sy + 1);
+  // q - corner per axis, in world units (corner i at lo + (i + 1/2) h)
+  const float h0 = 1.f / d.ginv_h[0], h1 = 1.f / d.ginv_h[1], h2 = 1.f / d.ginv_h[2];
+  const float dx0 = (ux - 0.5f - (float)ix) * h0, dy0 = (uy - 0.5f - (float)iy) * h1, dz0 = (uz - 0.5f - (float)iz) * h2;
+  float l = 0.f, u = INFINITY;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const float ex = (k & 4) ? dx0 - h0 : dx0, ey = (k & 2) ? dy0 - h1 : dy0, ez = (k & 1) ? dz0 - h2 : dz0;
+    const float r = sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
+    l = fmaxf(l, v[k] - r);
+    if (v[k] < d.gcap) u = fminf(u, v[k] + r);
+  }
+  *lb = l;
+  *ub = u;
+  const float c00 = v[0] + fz * (v[1] - v[0]);
+  const float c01 = v[2] + fz * (v[3] - v[2]);
+  const float c10 = v[4] + fz * (v[5] - v[4]);
+  const float c11 = v[6] + fz * (v[7] - v[6]);
+  const float c0 = c00 + fy * (c01 - c00);
+  const float c1 = c10 + fy * (c11 - c10);
+  return c0 + fx * (c1 - c0);
+}
+
 // Is some target point strictly within epsilon of q? (Eq. 3, one source point.)
 // Cells are at least epsilon wide, so the 3x3x3 cell neighbourhood suffices.
 __device__ __forceinline__ bool has_inlier(const PassDesc& d, float qx, float qy, float qz) {
@@ -495,39 +543,26 @@ __global__ void __launch_bounds__(256) count_kernel(PassLaunch L) {
     const bool grid_cost = d.fuse_score && d.metric != 0;
     int cnt = 0;
     float csum = 0.f;
-    // two source points per lane per step: their grid lookups are in flight together
-    for (int i0 = lane; i0 < d.N; i0 += 64) {
-      float qx[2], qy[2], qz[2], dg[2];
-      bool live[2];
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int i = i0 + 32 * u;
-        live[u] = i < d.N;
-        const int ii = live[u] ? i : i0;
-        const float x = __ldg(d.X + 3 * (size_t)ii), y = __ldg(d.X + 3 * (size_t)ii + 1),
-                    z = __ldg(d.X + 3 * (size_t)ii + 2);
-        qx[u] = fmaf(R[0], x, fmaf(R[1], y, R[2] * z)) + tx;
-        qy[u] = fmaf(R[3], x, fmaf(R[4], y, R[5] * z)) + ty;
-        qz[u] = fmaf(R[6], x, fmaf(R[7], y, R[8] * z)) + tz;
-      }
-#pragma unroll
-      for (int u = 0; u < 2; ++u) dg[u] = grid_lookup(d, qx[u], qy[u], qz[u]);
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        if (!live[u]) continue;
-        // The capped distance field is 1-Lipschitz, so its trilinear
-        // interpolant between voxel centres is within grid_err of min(d, cap);
-        // only queries within that band of epsilon need the exact cell search.
-        bool inl;
-        if (dg[u] >= d.eps + d.grid_err)
-          inl = false;
-        else if (dg[u] < d.eps - d.grid_err && d.gcap > d.eps)
-          inl = true;
-        else
-          inl = has_inlier(d, qx[u], qy[u], qz[u]);
-        cnt += inl ? 1 : 0;
-        if (grid_cost) csum += rho(d.metric, dg[u], d.eps, d.tau, d.huber_h, d.p_exp);
-      }
+    for (int i = lane; i < d.N; i += 32) {
+      const float x = __ldg(d.X + 3 * (size_t)i), y = __ldg(d.X + 3 * (size_t)i + 1),
+                  z = __ldg(d.X + 3 * (size_t)i + 2);
+      const float qx = fmaf(R[0], x, fmaf(R[1], y, R[2] * z)) + tx;
+      const float qy = fmaf(R[3], x, fmaf(R[4], y, R[5] * z)) + ty;
+      const float qz = fmaf(R[6], x, fmaf(R[7], y, R[8] * z)) + tz;
+      // Bounds on the exact nearest-target distance from the grid's corners
+      // decide most queries; those within kBoundMargin of epsilon take the
+      // exact cell-list search.
+      float lb, ub;
+      const float dg = grid_lookup_bounds(d, qx, qy, qz, &lb, &ub);
+      bool inl;
+      if (lb >= d.eps + d.grid_err)
+        inl = false;
+      else if (ub < d.eps - d.grid_err)
+        inl = true;
+      else
+        inl = has_inlier(d, qx, qy, qz);
+      cnt += inl ? 1 : 0;
+      if (grid_cost) csum += rho(d.metric, dg, d.eps, d.tau, d.huber_h, d.p_exp);
     }
 #pragma unroll
     for (int k = 16; k > 0; k >>= 1) {
