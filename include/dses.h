@@ -216,6 +216,8 @@ dses_status dses_target_distance_grid(dses_ctx* ctx, const dses_target* target, 
  *                          last blocking call, in nanoseconds
  *   "last_count_ns"        (read-only) the same for its inlier-count / score kernels
  *   "last_pass_launches"   (read-only) how many rotation passes that call made
+ *   "last_votes_total"     (read-only) histogram increments (pairs voting inside
+ *                          the translation box) of the last blocking call
  *   "kernel_launches"      (read-only) kernels this library has launched in the
  *                          process so far (all contexts)
  * INVALID_ARG for an unknown key or a value out of range. */

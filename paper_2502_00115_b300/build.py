@@ -23,6 +23,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libdses.so")
+PEAKS_SRC = os.path.join(HERE, "peaks", "peaks.cu")
+PEAKS_LIB = os.path.join(HERE, "peaks", "libdses_peaks.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
@@ -69,6 +71,14 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
         os.replace(tmp, LIB)
+    # resource microbenchmarks (a separate library; not part of the registration path)
+    if force or not os.path.exists(PEAKS_LIB) or os.path.getmtime(PEAKS_LIB) < os.path.getmtime(PEAKS_SRC):
+        tmp = PEAKS_LIB + f".tmp{os.getpid()}"
+        r = subprocess.run([nvcc(), *ARCH, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", PEAKS_SRC, "-o",
+                            tmp], capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed on {PEAKS_SRC}:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, PEAKS_LIB)
     if verbose:
         print(LIB)
     return LIB

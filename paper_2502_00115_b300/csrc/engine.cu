@@ -174,6 +174,7 @@ struct dses_ctx {
   int64_t count_ns = 0;    // ... and of its inlier-count / score launches
   int64_t pass_launches = 0;
   int64_t launch_snapshot = 0;
+  int64_t votes_total = 0;  // in-box pair votes of the last blocking call
   // host staging: blocking calls, the serving worker, and the one in use
   Stage stage, serve_stage;
   Stage* cur_stage = nullptr;
@@ -365,7 +366,7 @@ struct Job {
   uint32_t* cand = nullptr;
   uint32_t* n_cand = nullptr;  // [0] first pass, [1] second pass
   uint32_t* acc = nullptr;     // [0] M* first, [1] max V first, [2] M* second, [3] max V second
-  unsigned long long* best = nullptr;
+  unsigned long long* best = nullptr;  // [0] argmin key, [1] total in-box pair votes
   unsigned long long* keys = nullptr;
   unsigned long long* ks_scratch = nullptr;
   unsigned long long* ksel = nullptr;
@@ -528,7 +529,7 @@ void carve(Job& j) {
   const int kmax = std::max({j.topk, j.rtop, 1});
   j.ksel_k = kmax;
   const size_t o_kv = take(16 * n), o_M = take(4 * n), o_cost = take(4 * n), o_cand = take(4 * n),
-               o_nc = take(8), o_acc = take(16), o_best = take(8), o_keys = take(8 * n),
+               o_nc = take(8), o_acc = take(16), o_best = take(16), o_keys = take(8 * n),
                o_ks = take(8 * k_smallest_scratch((int)j.n_total, kmax)), o_ksel = take(8 * (size_t)kmax),
                o_fine = take(36 * (size_t)j.n_fine + 4), o_res = take(sizeof(dses_result));
   const bool own_rot = j.prob->grid.kind != DSES_GRID_HOPF;
@@ -594,6 +595,7 @@ void stage_setup(dses_ctx* c, Job& j) {
   CK(cudaMemsetAsync(j.acc, 0, 16, s));
   CK(cudaMemsetAsync(j.n_cand, 0, 8, s));
   CK(launch_fill_u64(j.best, ~0ull, 1, s));
+  CK(cudaMemsetAsync(j.best + 1, 0, 8, s));
   CK(launch_fill_f32(j.cost, NAN, (size_t)j.n_total, s));
 }
 
@@ -658,6 +660,7 @@ PassDesc make_desc(const Job& j, int P, bool second) {
   d.Mout = j.M;
   d.cost = j.cost;
   d.best = j.best;
+  d.votes_total = j.best + 1;
   return d;
 }
 
@@ -1231,7 +1234,12 @@ dses_status finish_results(dses_ctx* c, std::vector<Job*>& jobs, dses_result* ou
   dses_result* pinned = c->pinned_res;
   for (size_t i = 0; i < jobs.size(); ++i)
     CK(cudaMemcpyAsync(pinned + i, jobs[i]->res, sizeof(dses_result), cudaMemcpyDeviceToHost, c->stream));
+  std::vector<unsigned long long> votes(jobs.size(), 0);
+  for (size_t i = 0; i < jobs.size(); ++i)
+    CK(cudaMemcpyAsync(&votes[i], jobs[i]->best + 1, 8, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  c->votes_total = 0;
+  for (auto v : votes) c->votes_total += (int64_t)v;
   collect_timing(c);
   dses_status st = DSES_OK;
   for (size_t i = 0; i < jobs.size(); ++i) {
@@ -1597,6 +1605,7 @@ static int64_t* option_slot(dses_ctx* c, const char* key) {
   if (k == "last_pass_ns") return &c->pass_ns;
   if (k == "last_pass_launches") return &c->pass_launches;
   if (k == "last_count_ns") return &c->count_ns;
+  if (k == "last_votes_total") return &c->votes_total;
   if (k == "kernel_launches") {
     c->launch_snapshot = kernel_launch_count();
     return &c->launch_snapshot;
@@ -1617,7 +1626,8 @@ dses_status dses_set_option(dses_ctx* c, const char* key, int64_t value) {
     else if (k == "points_per_thread") ok = value == 0 || value == 1 || value == 2 || value == 4 || value == 8;
     else if (k == "fuse_score" || k == "autotune" || k == "use_graphs" || k == "record_timing")
       ok = value == 0 || value == 1;
-    else if (k == "last_pass_ns" || k == "last_pass_launches" || k == "kernel_launches" || k == "last_count_ns")
+    else if (k == "last_pass_ns" || k == "last_pass_launches" || k == "kernel_launches" || k == "last_count_ns" ||
+             k == "last_votes_total")
       ok = false;  // read-only
     else if (k == "tile_rotations") ok = value >= 0 && value <= 4096;
     else ok = value >= 1;

@@ -67,6 +67,7 @@ struct PassDesc {
   // per-problem accumulators
   uint32_t* acc;         // [0] = M*, [1] = max V
   unsigned long long* best;  // argmin key (cost bits << 32 | rotation index)
+  unsigned long long* votes_total;  // sum of all histogram counts (in-box pair votes)
 };
 
 struct PassLaunch {

@@ -158,6 +158,12 @@ __device__ __forceinline__ bool has_inlier(const PassDesc& d, float qx, float qy
   return false;
 }
 
+__device__ __forceinline__ unsigned warp_sum_u32(unsigned v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -423,6 +429,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
       for (int k = 0; k < 9; ++k) R[k] = __ldg(d.rot + 9 * (size_t)r + k);
       const unsigned Ey = (unsigned)d.E[1], Ez = (unsigned)d.E[2];
       unsigned long long best = 0ull;  // (count << 32) | ~global_bin, max wins
+      unsigned long long vtotal = 0ull;  // this warp's share of the rotation's votes
 
       for (int s = 0; s < d.n_slabs; ++s) {
         const int x0 = s * d.slab_x;
@@ -476,13 +483,14 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
         __syncthreads();
         // mode of this slab: scan and clear; each thread walks increasing bins
         const unsigned nbins = SX * Ey * Ez;
-        unsigned bc = 0, bb = 0;
+        unsigned bc = 0, bb = 0, vsum = 0;
         if (d.hist_u16) {
           const unsigned words = (nbins + 1) >> 1;
           for (unsigned w = tid; w < words; w += kPassThreads) {
             const uint32_t v = hist[w];
             hist[w] = 0u;
             const unsigned a = v & 0xffffu, b = v >> 16;
+            vsum += a + b;
             if (a > bc) { bc = a; bb = 2 * w; }
             if (b > bc) { bc = b; bb = 2 * w + 1; }
           }
@@ -490,9 +498,11 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
           for (unsigned w = tid; w < nbins; w += kPassThreads) {
             const uint32_t v = hist[w];
             hist[w] = 0u;
+            vsum += v;
             if (v > bc) { bc = v; bb = w; }
           }
         }
+        vtotal += warp_sum_u32(vsum);
         const unsigned gbin = (unsigned)x0 * Ey * Ez + bb;
         unsigned long long key = ((unsigned long long)bc << 32) | (unsigned long long)(0xffffffffu - gbin);
         key = warp_max_u64(key);
@@ -507,6 +517,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
         // strict: an earlier slab holds smaller bins and keeps ties
         if (s == 0 || (sk >> 32) > (best >> 32)) best = sk;
       }
+      if (lane == 0 && d.votes_total && vtotal) atomicAdd(d.votes_total, vtotal);
       if (tid == 0) {
         const unsigned V = (unsigned)(best >> 32);
         const unsigned gbin = 0xffffffffu - (unsigned)(best & 0xffffffffull);
