@@ -599,6 +599,9 @@ void stage_setup(dses_ctx* c, Job& j) {
   CK(launch_fill_f32(j.cost, NAN, (size_t)j.n_total, s));
 }
 
+// Vote items per source chunk the sparse path aims for (a few per warp).
+constexpr int c_sparse_items = 128;
+
 PassDesc make_desc(const Job& j, int P, bool second) {
   PassDesc d;
   std::memset(&d, 0, sizeof(d));
@@ -631,7 +634,11 @@ PassDesc make_desc(const Job& j, int P, bool second) {
   d.hist_u16 = j.u16;
   d.sparse = j.sparse ? 1 : 0;
   d.n_tchunks = (j.T->m + 32 * P - 1) / (32 * P);
-  d.n_sgroups = 32 / gcd(d.n_tchunks, 32);
+  // dense: items a multiple of the 32 warps (equal work per item); sparse:
+  // items are uneven anyway and the CTA's item counter balances them, so keep
+  // each item's target loads and thresholds amortised over many sources
+  d.n_sgroups = j.sparse ? std::max(1, (int)(c_sparse_items / std::max(1, d.n_tchunks)))
+                         : 32 / gcd(d.n_tchunks, 32);
   d.eps2 = j.eps * j.eps;
   d.cell_start = j.cl->start;
   for (int a = 0; a < 3; ++a) {
