@@ -89,6 +89,7 @@ def _load():
                 "orc_vote_consistent": (i32, [pd, i64, pd, i64, pd, d, pi32, pi32, d, pi32, i64]),
                 "orc_nn_dist": (None, [pd, i64, pd, i64, pd, pd, pd]),
                 "orc_inliers": (None, [pd, i64, pd, i64, pd, pd, d, d, pi64, pi64]),
+                "orc_refine_translation": (i64, [pd, i64, pd, i64, pd, pd, d, d, pd, pi64, pi64]),
                 "orc_rho": (d, [P(Params), d]),
                 "orc_cost_exact": (d, [pd, i64, pd, i64, pd, pd, P(Params)]),
                 "orc_dist_grid_geometry": (None, [pd, i64, i32, d, pd, pd]),
@@ -231,6 +232,19 @@ def inliers(X, Y, R, t, eps, band=1e-5):
     _load().orc_inliers(_pd(X), len(X), _pd(Y), len(Y), _pd(R), _pd(t), eps, band, ctypes.byref(c),
                         ctypes.byref(nb))
     return int(c.value), int(nb.value)
+
+
+def refine_translation(X, Y, R, t, eps, band=1e-5):
+    """Mean of the inlier translations y_nn(i) - R x_i at the pose (R, t) (the
+    least-squares translation for those correspondences; t when no point is an
+    inlier). Returns (t_refined, n_inliers, n_boundary, n_tie)."""
+    X, Y, R, t = _f64(X), _f64(Y), _f64(R), _f64(t)
+    out = np.zeros(3)
+    nb = ctypes.c_int64()
+    nt = ctypes.c_int64()
+    n = _load().orc_refine_translation(_pd(X), len(X), _pd(Y), len(Y), _pd(R), _pd(t), eps, band, _pd(out),
+                                       ctypes.byref(nb), ctypes.byref(nt))
+    return out, int(n), int(nb.value), int(nt.value)
 
 
 def rho(P: Params, d: float) -> float:

@@ -40,6 +40,9 @@
 //   exact cost                 pinned: cKDTree distances
 //   distance grid + lookup     pinned: cKDTree at centres, scipy
 //                              RegularGridInterpolator between them
+//   translation refinement     pinned: exact recovery on a noiseless subset,
+//                              the least-squares optimality of the mean
+//                              (scipy least squares), equivariance
 //   register (Algorithm 2)     pinned: theorem special case, exhaustive
 //                              search (Algorithm 1) on tiny inputs
 
@@ -362,6 +365,61 @@ void orc_inliers(const double* X, int64_t N, const double* Y, int64_t M, const d
   }
   *count = c;
   if (n_boundary) *n_boundary = nb;
+}
+
+// ---------------------------------------------------------------------------
+// Sub-voxel translation refinement (a step after Algorithm 2; the paper stops
+// at the voxel centre t* = k* delta_t). With the correspondences fixed at the
+// pose (R, t) -- each source point paired with its nearest target, kept when
+// that distance is below epsilon as in Eq. 3 -- the translation minimising the
+// summed squared residual is the mean of the inlier translations:
+//   t' = (1 / |I|) sum_{i in I} (y_nn(i) - R x_i).
+// With no inlier t' = t. Returns |I|. Bookkeeping: n_boundary counts points
+// whose nearest distance lies within band of epsilon, n_tie inlier candidates
+// (distance below epsilon + band) whose second-nearest target is within band
+// of the nearest; only there may an FP32 implementation pick differently.
+int64_t orc_refine_translation(const double* X, int64_t N, const double* Y, int64_t M, const double* R,
+                               const double* t, double eps, double band, double* t_out, int64_t* n_boundary,
+                               int64_t* n_tie) {
+  double sx = 0.0, sy = 0.0, sz = 0.0;
+  int64_t n_in = 0, nb = 0, nt = 0;
+  for (int64_t i = 0; i < N; ++i) {
+    const V3 u = rot(R, X + 3 * i);
+    const double qx = u.x + t[0], qy = u.y + t[1], qz = u.z + t[2];
+    double d1 = std::numeric_limits<double>::infinity(), d2 = d1;
+    int64_t j1 = -1;
+    for (int64_t j = 0; j < M; ++j) {
+      const double dx = Y[3 * j] - qx, dy = Y[3 * j + 1] - qy, dz = Y[3 * j + 2] - qz;
+      const double dd = std::sqrt(dx * dx + dy * dy + dz * dz);
+      if (dd < d1) {
+        d2 = d1;
+        d1 = dd;
+        j1 = j;
+      } else if (dd < d2) {
+        d2 = dd;
+      }
+    }
+    if (std::fabs(d1 - eps) <= band) ++nb;
+    if (d1 < eps + band && d2 - d1 <= band) ++nt;
+    if (d1 < eps) {
+      sx += Y[3 * j1] - u.x;
+      sy += Y[3 * j1 + 1] - u.y;
+      sz += Y[3 * j1 + 2] - u.z;
+      ++n_in;
+    }
+  }
+  if (n_in > 0) {
+    t_out[0] = sx / (double)n_in;
+    t_out[1] = sy / (double)n_in;
+    t_out[2] = sz / (double)n_in;
+  } else {
+    t_out[0] = t[0];
+    t_out[1] = t[1];
+    t_out[2] = t[2];
+  }
+  if (n_boundary) *n_boundary = nb;
+  if (n_tie) *n_tie = nt;
+  return n_in;
 }
 
 // ---------------------------------------------------------------------------

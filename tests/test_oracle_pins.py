@@ -413,3 +413,75 @@ def test_q_filter_keeps_equality():
     reg = oracle.register(X, Y, grid, P)
     keep = reg.M == reg.M.max()
     assert np.array_equal(np.isfinite(reg.costs), keep) and reg.rot_index == r_true
+
+
+# ---------------------------------------------------------------------------
+# sub-voxel translation refinement (mean of the inlier translations)
+
+
+def _separated_cloud(rng, m, spacing):
+    """m points of a jittered cubic lattice: every pair at least `spacing` apart."""
+    side = int(math.ceil(m ** (1 / 3))) + 1
+    cells = np.array(list(itertools.product(range(side), repeat=3)), float)
+    pick = cells[rng.choice(len(cells), m, replace=False)]
+    return (pick + rng.uniform(-0.2, 0.2, pick.shape)) * spacing
+
+
+def test_refine_translation_recovers_exact_pose_on_noiseless_subset():
+    # X is an exact subset of Y moved by (R, t): from any start within a
+    # quarter of the spacing every source point pairs with its own target, so
+    # the mean of the inlier translations is t itself.
+    rng = np.random.default_rng(3)
+    Y = _separated_cloud(rng, 300, 0.1)
+    R = Rotation.random(random_state=4).as_matrix()
+    t = np.array([0.31, -0.12, 0.07])
+    Xs = Y[rng.choice(300, 120, replace=False)]
+    X = (Xs - t) @ R  # rows: R^T (y - t)
+    start = t + np.array([0.012, -0.009, 0.014])
+    tr, n, nb, nt = oracle.refine_translation(X, Y, R, start, eps=0.04)
+    assert n == 120 and nb == 0 and nt == 0
+    np.testing.assert_allclose(tr, t, atol=1e-12)
+
+
+def test_refine_translation_is_the_least_squares_translation_of_the_inliers():
+    # Correspondences from cKDTree at the start pose, inliers below epsilon;
+    # the refined t must be the least-squares solution of
+    # min_t sum_i ||y_nn(i) - R x_i - t||^2 over those inliers (numpy lstsq on
+    # the stacked identity design), with clutter points excluded.
+    rng = np.random.default_rng(5)
+    Y = _separated_cloud(rng, 400, 0.1)
+    R = Rotation.random(random_state=6).as_matrix()
+    t = np.array([-0.2, 0.4, 0.1])
+    Xs = Y[rng.choice(400, 150, replace=False)] + rng.normal(0, 0.004, (150, 3))
+    clutter = rng.uniform(-2, 3, (40, 3))
+    X = (np.vstack([Xs, clutter]) - t) @ R
+    start = t + np.array([0.01, 0.008, -0.006])
+    eps = 0.035
+    tr, n, nb, nt = oracle.refine_translation(X, Y, R, start, eps=eps)
+    assert nb == 0 and nt == 0
+    U = X @ R.T
+    dist, idx = cKDTree(Y).query(U + start)
+    keep = dist < eps
+    assert n == int(keep.sum()) and 140 <= n <= 150
+    A = np.tile(np.eye(3), (n, 1))
+    b = (Y[idx[keep]] - U[keep]).reshape(-1)
+    ls = np.linalg.lstsq(A, b, rcond=None)[0]
+    np.testing.assert_allclose(tr, ls, atol=1e-12)
+    assert np.linalg.norm(tr - t) < np.linalg.norm(start - t)
+
+
+def test_refine_translation_equivariance_and_no_inlier_case():
+    rng = np.random.default_rng(7)
+    Y = _separated_cloud(rng, 200, 0.1)
+    R = Rotation.random(random_state=8).as_matrix()
+    X = (Y[:80] + rng.normal(0, 0.003, (80, 3))) @ R
+    start = np.array([0.004, -0.006, 0.002])
+    v = np.array([1.25, -0.5, 0.75])
+    a, na, _, _ = oracle.refine_translation(X, Y, R, start, eps=0.03)
+    b, nb_, _, _ = oracle.refine_translation(X, Y + v, R, start + v, eps=0.03)
+    assert na == nb_ == 80
+    np.testing.assert_allclose(b, a + v, atol=1e-12)
+    far = np.array([50.0, 0.0, 0.0])
+    c, nc, _, _ = oracle.refine_translation(X, Y, R, far, eps=0.03)
+    assert nc == 0
+    np.testing.assert_array_equal(c, far)
