@@ -59,32 +59,9 @@ __device__ __forceinline__ float rho(int metric, float d, float eps, float tau, 
   }
 }
 
-// Trilinear interpolation between voxel centres of the truncated distance
-// grid, clamped at the outermost centres; outside the grid box: the cap.
-__device__ __forceinline__ float grid_lookup(const PassDesc& d, float qx, float qy, float qz) {
-  const float G = (float)d.G;
-  float gx = (qx - d.glo[0]) * d.ginv_h[0];
-  float gy = (qy - d.glo[1]) * d.ginv_h[1];
-  float gz = (qz - d.glo[2]) * d.ginv_h[2];
-  if (!(gx >= 0.f && gx <= G && gy >= 0.f && gy <= G && gz >= 0.f && gz <= G)) return d.gcap;
-  gx = fminf(fmaxf(gx - 0.5f, 0.f), G - 1.f);
-  gy = fminf(fmaxf(gy - 0.5f, 0.f), G - 1.f);
-  gz = fminf(fmaxf(gz - 0.5f, 0.f), G - 1.f);
-  const int ix = min((int)gx, d.G - 2), iy = min((int)gy, d.G - 2), iz = min((int)gz, d.G - 2);
-  const float fx = gx - (float)ix, fy = gy - (float)iy, fz = gz - (float)iz;
-  const float* b = d.D + ((size_t)ix * d.G + iy) * d.G + iz;
-  const size_t sy = d.G, sx = (size_t)d.G * d.G;
-  const float c00 = __ldg(b) + fz * (__ldg(b + 1) - __ldg(b));
-  const float c01 = __ldg(b + sy) + fz * (__ldg(b + sy + 1) - __ldg(b + sy));
-  const float c10 = __ldg(b + sx) + fz * (__ldg(b + sx + 1) - __ldg(b + sx));
-  const float c11 = __ldg(b + sx + sy) + fz * (__ldg(b + sx + sy + 1) - __ldg(b + sx + sy));
-  const float c0 = c00 + fy * (c01 - c00);
-  const float c1 = c10 + fy * (c11 - c10);
-  return c0 + fx * (c1 - c0);
-}
-
-// Trilinear value of the distance grid at q (as grid_lookup) together with
-// bounds on the exact nearest-target distance d(q): the stored values are
+// Trilinear value of the distance grid at q (interpolation between voxel
+// centres, clamped at the outermost centres; the cap outside the grid box),
+// together with bounds on the exact nearest-target distance d(q): the stored values are
 // min(d, cap) at voxel centres and d is 1-Lipschitz, so every corner c_k used
 // gives D_k - |q - c_k| <= d(q), and, if D_k < cap, d(q) <= D_k + |q - c_k|.
 __device__ __forceinline__ float grid_lookup_bounds(const PassDesc& d, float qx, float qy, float qz, float* lb,
@@ -254,6 +231,109 @@ __device__ __forceinline__ void vote_centred(const PassDesc& d, const float4* __
           red_if_inside(addr, 1u, wx, wy, wz, hx, hy, hz);
         }
       }
+    }
+  }
+}
+
+// Dense centred path on packed FP32 pairs (fma.rn.f32x2 / add.rn.f32x2): a
+// lane's targets are held two by two per axis and each source offset is staged
+// duplicated, so one packed op computes the lattice coordinate (or its
+// rounding) of one source against two targets. Same per-pair arithmetic and
+// box test as vote_centred.
+template <bool U16>
+__device__ __forceinline__ void vote_two_pairs(uint64_t yx, uint64_t yy, uint64_t yz, uint64_t inv2, uint64_t cx2,
+                                               uint64_t cy2, uint64_t cz2, uint64_t mx2, uint64_t my2, uint64_t mz2,
+                                               uint32_t Eyz, uint32_t Ez, uint32_t abase, float hx, float hy,
+                                               float hz) {
+  if (U16) {
+    asm volatile(
+        "{\n\t.reg .b64 wx, wy, wz, fx, fy, fz;\n\t"
+        ".reg .b32 bx0, bx1, by0, by1, bz0, bz1, t0, t1, a0, a1, i0, i1, u0, u1, v0, v1, s0, s1;\n\t"
+        ".reg .f32 x0, x1, y0, y1, z0, z1;\n\t.reg .pred p0, p1;\n\t"
+        "fma.rn.f32x2 wx, %0, %3, %4;\n\tfma.rn.f32x2 wy, %1, %3, %5;\n\tfma.rn.f32x2 wz, %2, %3, %6;\n\t"
+        "add.rn.f32x2 fx, wx, %7;\n\tadd.rn.f32x2 fy, wy, %8;\n\tadd.rn.f32x2 fz, wz, %9;\n\t"
+        "mov.b64 {bx0, bx1}, fx;\n\tmov.b64 {by0, by1}, fy;\n\tmov.b64 {bz0, bz1}, fz;\n\t"
+        "mad.lo.u32 t0, by0, %11, bz0;\n\tmad.lo.u32 t0, bx0, %10, t0;\n\t"
+        "mad.lo.u32 t1, by1, %11, bz1;\n\tmad.lo.u32 t1, bx1, %10, t1;\n\t"
+        "shr.u32 a0, t0, 1;\n\tshr.u32 a1, t1, 1;\n\t"
+        "mad.lo.u32 a0, a0, 4, %12;\n\tmad.lo.u32 a1, a1, 4, %12;\n\t"
+        "and.b32 i0, t0, 1;\n\tand.b32 i1, t1, 1;\n\t"
+        "mad.lo.u32 i0, i0, 65535, 1;\n\tmad.lo.u32 i1, i1, 65535, 1;\n\t"
+        "mov.b64 {u0, u1}, wx;\n\tmov.b64 {v0, v1}, wy;\n\tmov.b64 {s0, s1}, wz;\n\t"
+        "mov.b32 x0, u0;\n\tmov.b32 x1, u1;\n\tmov.b32 y0, v0;\n\tmov.b32 y1, v1;\n\t"
+        "mov.b32 z0, s0;\n\tmov.b32 z1, s1;\n\t"
+        "abs.f32 x0, x0;\n\tabs.f32 x1, x1;\n\tabs.f32 y0, y0;\n\tabs.f32 y1, y1;\n\t"
+        "abs.f32 z0, z0;\n\tabs.f32 z1, z1;\n\t"
+        "setp.lt.f32 p0, x0, %13;\n\tsetp.lt.and.f32 p0, y0, %14, p0;\n\tsetp.lt.and.f32 p0, z0, %15, p0;\n\t"
+        "setp.lt.f32 p1, x1, %13;\n\tsetp.lt.and.f32 p1, y1, %14, p1;\n\tsetp.lt.and.f32 p1, z1, %15, p1;\n\t"
+        "@p0 red.shared.add.u32 [a0], i0;\n\t@p1 red.shared.add.u32 [a1], i1;\n\t}" ::"l"(yx),
+        "l"(yy), "l"(yz), "l"(inv2), "l"(cx2), "l"(cy2), "l"(cz2), "l"(mx2), "l"(my2), "l"(mz2), "r"(Eyz), "r"(Ez),
+        "r"(abase), "f"(hx), "f"(hy), "f"(hz));
+  } else {
+    asm volatile(
+        "{\n\t.reg .b64 wx, wy, wz, fx, fy, fz;\n\t"
+        ".reg .b32 bx0, bx1, by0, by1, bz0, bz1, t0, t1, a0, a1, u0, u1, v0, v1, s0, s1;\n\t"
+        ".reg .f32 x0, x1, y0, y1, z0, z1;\n\t.reg .pred p0, p1;\n\t"
+        "fma.rn.f32x2 wx, %0, %3, %4;\n\tfma.rn.f32x2 wy, %1, %3, %5;\n\tfma.rn.f32x2 wz, %2, %3, %6;\n\t"
+        "add.rn.f32x2 fx, wx, %7;\n\tadd.rn.f32x2 fy, wy, %8;\n\tadd.rn.f32x2 fz, wz, %9;\n\t"
+        "mov.b64 {bx0, bx1}, fx;\n\tmov.b64 {by0, by1}, fy;\n\tmov.b64 {bz0, bz1}, fz;\n\t"
+        "mad.lo.u32 t0, bz0, 4, %12;\n\tmad.lo.u32 t0, by0, %11, t0;\n\tmad.lo.u32 a0, bx0, %10, t0;\n\t"
+        "mad.lo.u32 t1, bz1, 4, %12;\n\tmad.lo.u32 t1, by1, %11, t1;\n\tmad.lo.u32 a1, bx1, %10, t1;\n\t"
+        "mov.b64 {u0, u1}, wx;\n\tmov.b64 {v0, v1}, wy;\n\tmov.b64 {s0, s1}, wz;\n\t"
+        "mov.b32 x0, u0;\n\tmov.b32 x1, u1;\n\tmov.b32 y0, v0;\n\tmov.b32 y1, v1;\n\t"
+        "mov.b32 z0, s0;\n\tmov.b32 z1, s1;\n\t"
+        "abs.f32 x0, x0;\n\tabs.f32 x1, x1;\n\tabs.f32 y0, y0;\n\tabs.f32 y1, y1;\n\t"
+        "abs.f32 z0, z0;\n\tabs.f32 z1, z1;\n\t"
+        "setp.lt.f32 p0, x0, %13;\n\tsetp.lt.and.f32 p0, y0, %14, p0;\n\tsetp.lt.and.f32 p0, z0, %15, p0;\n\t"
+        "setp.lt.f32 p1, x1, %13;\n\tsetp.lt.and.f32 p1, y1, %14, p1;\n\tsetp.lt.and.f32 p1, z1, %15, p1;\n\t"
+        "@p0 red.shared.add.u32 [a0], 1;\n\t@p1 red.shared.add.u32 [a1], 1;\n\t}" ::"l"(yx),
+        "l"(yy), "l"(yz), "l"(inv2), "l"(cx2), "l"(cy2), "l"(cz2), "l"(mx2), "l"(my2), "l"(mz2), "r"(Eyz * 4u),
+        "r"(Ez * 4u), "r"(abase), "f"(hx), "f"(hy), "f"(hz));
+  }
+}
+
+__device__ __forceinline__ uint64_t pack2(float lo, float hi) {
+  return ((uint64_t)__float_as_uint(hi) << 32) | (uint64_t)__float_as_uint(lo);
+}
+
+// Staged layout of source i: float4 [2i] holds (c_x, c_x, c_y, c_y), float4
+// [2i + 1] holds (c_z, c_z, 0, 0).
+template <int P, bool U16>
+__device__ __forceinline__ void vote_centred_x2(const PassDesc& d, const float4* __restrict__ srcd, int nsrc,
+                                                unsigned SX, uint32_t hist_base, int* item_ctr, int lane) {
+  static_assert(P % 2 == 0, "targets are packed two by two");
+  const int n_tchunks = d.n_tchunks, n_sgroups = d.n_sgroups;
+  const int n_items = n_tchunks * n_sgroups;
+  const int spg = (nsrc + n_sgroups - 1) / n_sgroups;
+  const unsigned Ey = (unsigned)d.E[1], Ez = (unsigned)d.E[2], Eyz = Ey * Ez;
+  const float inv = d.inv_delta;
+  const float hx = 0.5f * (float)SX, hy = 0.5f * (float)Ey, hz = 0.5f * (float)Ez;
+  const float mx = kMagic + (float)((SX - 1) / 2), my = kMagic + (float)((Ey - 1) / 2),
+              mz = kMagic + (float)((Ez - 1) / 2);
+  const uint64_t inv2 = pack2(inv, inv), mx2 = pack2(mx, mx), my2 = pack2(my, my), mz2 = pack2(mz, mz);
+  const uint32_t bias = kMagicBits * (Eyz + Ez + 1u);
+  const uint32_t abase = U16 ? hist_base - 2u * bias : hist_base - 4u * bias;
+  for (int it = next_item(item_ctr, lane); it < n_items; it = next_item(item_ctr, lane)) {
+    const int tc = it % n_tchunks, sg = it / n_tchunks;
+    float ty[P][3];
+    load_targets(d.Yv, d.M, tc * P * 32, lane, P, ty);
+    uint64_t yx[P / 2], yy[P / 2], yz[P / 2];
+#pragma unroll
+    for (int q = 0; q < P / 2; ++q) {
+      yx[q] = pack2(ty[2 * q][0], ty[2 * q + 1][0]);
+      yy[q] = pack2(ty[2 * q][1], ty[2 * q + 1][1]);
+      yz[q] = pack2(ty[2 * q][2], ty[2 * q + 1][2]);
+    }
+    const int i0 = sg * spg, i1 = min(i0 + spg, nsrc);
+    constexpr int kUnroll = P >= 8 ? 1 : 4;  // P = 8 spills when unrolled
+#pragma unroll kUnroll
+    for (int i = i0; i < i1; ++i) {
+      const float4 ca = srcd[2 * i];
+      const float2 cb = *reinterpret_cast<const float2*>(srcd + 2 * i + 1);
+      const uint64_t cx2 = pack2(ca.x, ca.y), cy2 = pack2(ca.z, ca.w), cz2 = pack2(cb.x, cb.y);
+#pragma unroll
+      for (int q = 0; q < P / 2; ++q)
+        vote_two_pairs<U16>(yx[q], yy[q], yz[q], inv2, cx2, cy2, cz2, mx2, my2, mz2, Eyz, Ez, abase, hx, hy, hz);
     }
   }
 }
@@ -447,8 +527,11 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
           off1 = 0.5f - (float)d.lo[1];
           off2 = 0.5f - (float)d.lo[2];
         }
-        for (int c0 = 0; c0 < d.N; c0 += kSrcChunk) {
-          const int c1 = min(c0 + kSrcChunk, d.N);
+        // the packed path stages 32 bytes per source: half as many per chunk
+        const bool packed = P >= 2 && centred && !(SPARSE && d.sparse);
+        const int chunk = packed ? kSrcChunk / 2 : kSrcChunk;
+        for (int c0 = 0; c0 < d.N; c0 += chunk) {
+          const int c1 = min(c0 + chunk, d.N);
           __syncthreads();  // previous chunk's readers are done
           if (tid == 0) s_vote_item = 0;
           for (int i = c0 + tid; i < c1; i += kPassThreads) {
@@ -457,8 +540,14 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
             const float ux = fmaf(R[0], x, fmaf(R[1], y, R[2] * z));
             const float uy = fmaf(R[3], x, fmaf(R[4], y, R[5] * z));
             const float uz = fmaf(R[6], x, fmaf(R[7], y, R[8] * z));
-            srcc[i - c0] = make_float4(fmaf(-ux, d.inv_delta, off0), fmaf(-uy, d.inv_delta, off1),
-                                       fmaf(-uz, d.inv_delta, off2), 0.f);
+            const float cx = fmaf(-ux, d.inv_delta, off0), cy = fmaf(-uy, d.inv_delta, off1),
+                        cz = fmaf(-uz, d.inv_delta, off2);
+            if (packed) {
+              srcc[2 * (i - c0)] = make_float4(cx, cx, cy, cy);
+              srcc[2 * (i - c0) + 1] = make_float4(cz, cz, 0.f, 0.f);
+            } else {
+              srcc[i - c0] = make_float4(cx, cy, cz, 0.f);
+            }
           }
           __syncthreads();
           if (SPARSE && centred && d.sparse) {
@@ -469,10 +558,17 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
               vote_centred_sparse<P, false>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane,
                                             s_thr[SPARSE ? warp : 0]);
           } else if (centred) {
-            if (d.hist_u16)
+            constexpr int PP = P >= 2 ? P : 2;  // the P = 1 instance never takes the packed path
+            if (packed) {
+              if (d.hist_u16)
+                vote_centred_x2<PP, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane);
+              else
+                vote_centred_x2<PP, false>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane);
+            } else if (d.hist_u16) {
               vote_centred<P, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane);
-            else
+            } else {
               vote_centred<P, false>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane);
+            }
           } else {
             if (d.hist_u16)
               vote_generic<P, true>(d, srcc, c1 - c0, SX, hist, &s_vote_item, lane);
