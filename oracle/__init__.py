@@ -91,6 +91,7 @@ def _load():
                 "orc_inliers": (None, [pd, i64, pd, i64, pd, pd, d, d, pi64, pi64]),
                 "orc_refine_translation": (i64, [pd, i64, pd, i64, pd, pd, d, d, pd, pi64, pi64]),
                 "orc_rho": (d, [P(Params), d]),
+                "orc_exhaustive": (i64, [pd, i64, pd, i64, pd, i64, P(Params), pd, pi64, d, pi64]),
                 "orc_cost_exact": (d, [pd, i64, pd, i64, pd, pd, P(Params)]),
                 "orc_dist_grid_geometry": (None, [pd, i64, i32, d, pd, pd]),
                 "orc_dist_grid": (None, [pd, i64, i32, d, pd]),
@@ -245,6 +246,21 @@ def refine_translation(X, Y, R, t, eps, band=1e-5):
     n = _load().orc_refine_translation(_pd(X), len(X), _pd(Y), len(Y), _pd(R), _pd(t), eps, band, _pd(out),
                                        ctypes.byref(nb), ctypes.byref(nt))
     return out, int(n), int(nb.value), int(nt.value)
+
+
+def exhaustive(X, Y, rotations, P: Params, rel_tie=1e-4):
+    """Algorithm 1 over `rotations` and the lattice translations of P's box:
+    returns (cost (n_rot, n_t), inlier count (n_rot, n_t), flat argmin, near_tie)."""
+    X, Y = _f64(X), _f64(Y)
+    Rl = _f64(np.asarray(rotations).reshape(-1, 9))
+    lo, hi = lattice_box(P.t_center[:], P.t_half[:], P.delta_t)
+    nt = int(np.prod(np.asarray(hi) - np.asarray(lo) + 1))
+    cost = np.zeros((len(Rl), nt))
+    cnt = np.zeros((len(Rl), nt), dtype=np.int64)
+    tie = ctypes.c_int64()
+    best = _load().orc_exhaustive(_pd(X), len(X), _pd(Y), len(Y), _pd(Rl), len(Rl), ctypes.byref(P), _pd(cost),
+                                  cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), rel_tie, ctypes.byref(tie))
+    return cost, cnt, int(best), int(tie.value)
 
 
 def rho(P: Params, d: float) -> float:

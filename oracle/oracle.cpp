@@ -43,6 +43,9 @@
 //   translation refinement     pinned: exact recovery on a noiseless subset,
 //                              the least-squares optimality of the mean
 //                              (scipy least squares), equivariance
+//   exhaustive (Algorithm 1)   pinned: independent numpy brute force on tiny
+//                              inputs, the theorem special case (zero error at
+//                              the planted pose)
 //   register (Algorithm 2)     pinned: theorem special case, exhaustive
 //                              search (Algorithm 1) on tiny inputs
 
@@ -686,6 +689,64 @@ int orc_register_threads(const double* X, int64_t N, const double* Y, int64_t M,
                          int64_t nR, const orc_params* P, int threads, orc_result* res) {
   return run_register(X, N, Y, M, Rlist, nR, P, threads, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                       res);
+}
+
+// Algorithm 1 (pure exhaustive search): every rotation of Rlist against every
+// lattice translation k delta_t of the translation box, with the error
+//   e(R, t) = sum over source points of rho(min_j ||y_j - R x_i - t||)
+// (exact nearest neighbours; rho is non-decreasing, so the minimum of the
+// per-pair errors is rho of the nearest distance). Entry r * n_t + t_idx of
+// cost / count, t_idx = ((kx - lo_x) E_y + (ky - lo_y)) E_z + (kz - lo_z);
+// count is the inlier count of Eq. 3 at that pose. Returns the index of the
+// smallest cost (the first on ties), or -1 with no entry. near_tie receives
+// how many entries lie within rel_tie (relative) of the smallest cost.
+int64_t orc_exhaustive(const double* X, int64_t N, const double* Y, int64_t M, const double* Rlist, int64_t nR,
+                       const orc_params* P, double* cost, int64_t* count, double rel_tie, int64_t* near_tie) {
+  int lo[3], hi[3];
+  orc_lattice_box(P->t_center, P->t_half, P->delta_t, lo, hi);
+  const int64_t E[3] = {hi[0] - lo[0] + 1, hi[1] - lo[1] + 1, hi[2] - lo[2] + 1};
+  if (E[0] < 1 || E[1] < 1 || E[2] < 1) return -1;
+  const int64_t nt = E[0] * E[1] * E[2];
+  std::vector<double> u(3 * (size_t)N);
+  int64_t best = -1;
+  for (int64_t r = 0; r < nR; ++r) {
+    for (int64_t i = 0; i < N; ++i) {
+      const V3 v = rot(Rlist + 9 * r, X + 3 * i);
+      u[3 * i] = v.x;
+      u[3 * i + 1] = v.y;
+      u[3 * i + 2] = v.z;
+    }
+    for (int64_t a = 0; a < E[0]; ++a)
+      for (int64_t b = 0; b < E[1]; ++b)
+        for (int64_t c = 0; c < E[2]; ++c) {
+          const double t[3] = {(double)(lo[0] + a) * P->delta_t, (double)(lo[1] + b) * P->delta_t,
+                               (double)(lo[2] + c) * P->delta_t};
+          double e = 0.0;
+          int64_t n_in = 0;
+          for (int64_t i = 0; i < N; ++i) {
+            double m2 = std::numeric_limits<double>::infinity();
+            for (int64_t j = 0; j < M; ++j) {
+              const double dx = Y[3 * j] - u[3 * i] - t[0], dy = Y[3 * j + 1] - u[3 * i + 1] - t[1],
+                           dz = Y[3 * j + 2] - u[3 * i + 2] - t[2];
+              m2 = std::min(m2, dx * dx + dy * dy + dz * dz);
+            }
+            const double d = std::sqrt(m2);
+            e += orc_rho(P, d);
+            if (d < P->epsilon) ++n_in;
+          }
+          const int64_t idx = r * nt + (a * E[1] + b) * E[2] + c;
+          cost[idx] = e;
+          count[idx] = n_in;
+          if (best < 0 || e < cost[best]) best = idx;
+        }
+  }
+  if (near_tie) {
+    int64_t n = 0;
+    const double lim = cost[best] + rel_tie * std::max(1.0, std::fabs(cost[best]));
+    for (int64_t k = 0; k < nR * nt; ++k) n += cost[k] <= lim ? 1 : 0;
+    *near_tie = n;
+  }
+  return best;
 }
 
 // A target's distance field, built once and reused by orc_register_field_threads

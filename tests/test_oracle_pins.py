@@ -485,3 +485,74 @@ def test_refine_translation_equivariance_and_no_inlier_case():
     c, nc, _, _ = oracle.refine_translation(X, Y, R, far, eps=0.03)
     assert nc == 0
     np.testing.assert_array_equal(c, far)
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 1 (pure exhaustive search)
+
+
+def _tiny_pose_problem(seed, n_src=9, n_tgt=20, delta=0.1, K=1):
+    rng = np.random.default_rng(seed)
+    Y = synth.dyadic_cloud(rng, n_tgt, extent=0.4, min_sep_inf=delta)
+    rots = oracle.euler_box(np.eye(3), K, math.radians(20.0))
+    return rng, Y, rots
+
+
+@pytest.mark.parametrize("metric", ["inlier", "trunc_l1", "trunc_l2", "huber", "lp"])
+def test_exhaustive_matches_numpy_brute_force(metric):
+    # every (rotation, lattice translation) entry against cKDTree distances and
+    # the closed-form rho, in the stated index order
+    rng, Y, rots = _tiny_pose_problem(2)
+    X = rng.uniform(-0.3, 0.3, (9, 3))
+    P = oracle.make_params(metric=metric, epsilon=0.1, tau=0.15, huber_h=0.05, p=0.5, t_half=(0.2, 0.2, 0.2))
+    cost, cnt, best, _ = oracle.exhaustive(X, Y, rots, P)
+    lo, hi = oracle.lattice_box((0, 0, 0), (0.2, 0.2, 0.2), 0.1)
+    ks = list(itertools.product(*[range(a, b + 1) for a, b in zip(lo, hi)]))
+    assert cost.shape == (len(rots), len(ks))
+    tree = cKDTree(Y)
+    for r, R in enumerate(rots):
+        for ti, k in enumerate(ks):
+            d, _ = tree.query(X @ R.T + np.array(k) * 0.1)
+            e = np.minimum(d, 0.15)
+            ref = {"inlier": float(np.sum(d >= 0.1)), "trunc_l1": e.sum(), "trunc_l2": (e * e).sum(),
+                   "huber": np.where(e <= 0.05, 0.5 * e * e, 0.05 * (e - 0.025)).sum(),
+                   "lp": np.sqrt(d).sum()}[metric]
+            assert abs(cost[r, ti] - ref) <= 1e-9 * max(1.0, abs(ref))
+            assert cnt[r, ti] == int(np.sum(d < 0.1))
+    assert best == int(np.argmin(cost.reshape(-1)))
+
+
+def test_exhaustive_finds_the_planted_pose_with_zero_error():
+    # Theorem setting: the source is a subset of the target moved by a grid
+    # rotation and a lattice translation; only that entry has zero error
+    rng, Y, rots = _tiny_pose_problem(4)
+    r_true, k_true = 17, np.array([1, -1, 0])
+    R = rots[r_true]
+    X = (Y[:8] - k_true * 0.1) @ R  # rows R^T (y - t)
+    P = oracle.make_params(metric="trunc_l1", epsilon=0.1, tau=0.15, t_half=(0.2, 0.2, 0.2))
+    cost, cnt, best, _ = oracle.exhaustive(X, Y, rots, P)
+    lo, hi = oracle.lattice_box((0, 0, 0), (0.2, 0.2, 0.2), 0.1)
+    E = hi - lo + 1
+    ti = ((k_true[0] - lo[0]) * E[1] + (k_true[1] - lo[1])) * E[2] + (k_true[2] - lo[2])
+    assert best == r_true * cost.shape[1] + ti
+    assert cost.reshape(-1)[best] < 1e-12 and cnt.reshape(-1)[best] == 8
+    assert np.sort(cost.reshape(-1))[1] > 1e-3
+
+
+def test_dses_per_rotation_cost_is_the_exhaustive_entry_at_its_mode():
+    # Algorithm 2 evaluates each rotation at its vote mode t*: with exact nearest
+    # neighbours its per-rotation cost and inlier count are Algorithm 1's entry
+    # at (r, t*), and so its best cost is never below Algorithm 1's optimum
+    rng, Y, rots = _tiny_pose_problem(6)
+    X = (Y[:8] + rng.normal(0, 0.01, (8, 3)) - np.array([0.1, 0.0, -0.1])) @ rots[5]
+    P = oracle.make_params(metric="trunc_l2", epsilon=0.1, tau=0.15, t_half=(0.2, 0.2, 0.2), nn_mode="brute")
+    cost, cnt, best, _ = oracle.exhaustive(X, Y, rots, P)
+    reg = oracle.register(X, Y, rots, P)
+    lo, hi = oracle.lattice_box((0, 0, 0), (0.2, 0.2, 0.2), 0.1)
+    E = hi - lo + 1
+    for r in range(len(rots)):
+        k = reg.k[r]
+        ti = ((k[0] - lo[0]) * E[1] + (k[1] - lo[1])) * E[2] + (k[2] - lo[2])
+        assert abs(reg.costs[r] - cost[r, ti]) <= 1e-12
+        assert reg.M[r] == cnt[r, ti]
+    assert reg.cost >= cost.reshape(-1)[best] - 1e-12
