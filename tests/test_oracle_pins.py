@@ -556,3 +556,19 @@ def test_dses_per_rotation_cost_is_the_exhaustive_entry_at_its_mode():
         assert abs(reg.costs[r] - cost[r, ti]) <= 1e-12
         assert reg.M[r] == cnt[r, ti]
     assert reg.cost >= cost.reshape(-1)[best] - 1e-12
+
+
+def test_refine_translation_inlier_threshold_is_strict_and_tight():
+    # source points displaced from their own target by 0.9 eps count, those
+    # displaced by 1.1 eps do not (targets are 0.1 apart, so the nearest target
+    # is always the own one); the mean then uses the 0.9 eps points only
+    rng = np.random.default_rng(11)
+    Y = _separated_cloud(rng, 200, 0.1)
+    eps = 0.02
+    dirs = rng.normal(size=(60, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    scale = np.where(np.arange(60) < 35, 0.9 * eps, 1.1 * eps)[:, None]
+    X = Y[:60] - dirs * scale  # R = I, t = 0: y - x = dirs * scale
+    tr, n, nb, nt = oracle.refine_translation(X, Y, np.eye(3), np.zeros(3), eps)
+    assert n == 35 and nb == 0 and nt == 0
+    np.testing.assert_allclose(tr, (dirs[:35] * 0.9 * eps).mean(axis=0), atol=1e-15)
