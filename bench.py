@@ -52,10 +52,16 @@ def parse():
     ap.add_argument("--points-per-thread", type=int, default=0, help="vote launch shape (0: library default)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["modelnet_like", "batched", "serving", "robot_like"],
+    ap.add_argument("--workload", choices=["modelnet_like", "batched", "serving", "robot_like", "quality", "sweep"],
                     default="modelnet_like",
                     help="modelnet_like: the benchmark line; batched / serving: the other configurations")
     ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--quality-count", type=int, default=64, help="quality: number of problems")
+    ap.add_argument("--rotated-frame", action="store_true", help="quality: both clouds in a rotated frame")
+    ap.add_argument("--refine-iterations", type=int, default=3, help="quality: translation refinement steps")
+    ap.add_argument("--refine-top-k", type=int, default=16, help="quality: Euler-box second pass around the best k")
+    ap.add_argument("--refine-K", type=int, default=3, help="quality: Euler-box half-size of the second pass")
+    ap.add_argument("--refine-delta-deg", type=float, default=1.0, help="quality: Euler-box step (degrees)")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: Poisson arrival rate (requests/s)")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: arrival window (s)")
     return ap.parse_args()
@@ -477,6 +483,122 @@ def robot(args, ws, rank, local):
     }), flush=True)
 
 
+def pose_errors(R_est, t_est, R_true, t_true) -> dict:
+    """Pose-error measures of Section V-A. Isotropic (Yew & Lee 2020): the
+    angle of R_true^T R_est in degrees and ||t_est - t_true||. Mean absolute
+    (Wang & Solomon 2019): the mean over the three 'zyx' Euler angles of
+    |angle(R_est) - angle(R_true)| in degrees, and the mean over the axes of
+    |t_est - t_true|."""
+    from scipy.spatial.transform import Rotation
+
+    R_est, R_true = np.asarray(R_est, np.float64), np.asarray(R_true, np.float64)
+    c = (np.trace(R_true.T @ R_est) - 1.0) / 2.0
+    mie_r = float(np.degrees(np.arccos(np.clip(c, -1.0, 1.0))))
+    mie_t = float(np.linalg.norm(np.asarray(t_est, np.float64) - t_true))
+    e_est = Rotation.from_matrix(R_est).as_euler("zyx", degrees=True)
+    e_true = Rotation.from_matrix(R_true).as_euler("zyx", degrees=True)
+    mae_r = float(np.mean(np.abs(e_est - e_true)))
+    mae_t = float(np.mean(np.abs(np.asarray(t_est, np.float64) - t_true)))
+    return {"mie_r": mie_r, "mie_t": mie_t, "mae_r": mae_r, "mae_t": mae_t}
+
+
+def summarise_errors(errs: list[dict]) -> dict:
+    """Means of the four measures and the recall (MAE(R) < 1 deg and MAE(t) < 0.1)."""
+    out = {k: float(np.mean([e[k] for e in errs])) for k in ("mie_r", "mie_t", "mae_r", "mae_t")}
+    out["recall"] = float(np.mean([(e["mae_r"] < 1.0) and (e["mae_t"] < 0.1) for e in errs]))
+    return out
+
+
+def quality(args, ws, rank, local):
+    """Pose quality of Section V-A on synthetic ModelNet-shaped problems: Euler
+    angles in [-45, 45] deg, translations in [-0.5, 0.5]^3, one registration
+    per problem (the Hopf grid, then Euler boxes around the best candidates,
+    the local search of Algorithm 2's loops), errors of the voxel-centre
+    translation t* and of the sub-voxel refined one."""
+    import torch
+
+    from paper_2502_00115_b300 import build, capi, synth
+
+    torch.cuda.set_device(local)
+    build.build()
+    ctx = capi.Context(local)
+    raw, ref, times = [], [], []
+    for k in range(args.quality_count):
+        p = synth.modelnet_like_problem(args.seed + k, hopf_n=args.hopf_n, max_euler_deg=45.0,
+                                        rotated_frame=args.rotated_frame)
+        t = ctx.create_target(p.Y, grid_cap=2 * p.tau)
+        pr = capi.make_params(metric=p.metric, epsilon=p.epsilon, delta_t=p.delta_t, tau=p.tau, t_half=p.t_half,
+                              refine_top_k=args.refine_top_k, refine_K=args.refine_K,
+                              refine_delta_r=math.radians(args.refine_delta_deg))
+        pb = ctx.problem(t, p.X, capi.hopf_grid(p.hopf_n), pr)
+        t0 = time.perf_counter()
+        r = capi.result_dict(ctx.register(pb))
+        t1 = time.perf_counter()
+        tr, _ = ctx.refine_translation(t, p.X, r["R"], r["t"], p.epsilon, args.refine_iterations)
+        times.append((t1 - t0, time.perf_counter() - t1))
+        raw.append(pose_errors(r["R"], r["t"], p.R_true, p.t_true))
+        ref.append(pose_errors(r["R"], tr, p.R_true, p.t_true))
+        ctx.destroy_target(t)
+    ctx.close()
+    a, b = summarise_errors(raw), summarise_errors(ref)
+    print(json.dumps({
+        "workload": "quality_modelnet_like", "metric": "recall (MAE(R) < 1 deg and MAE(t) < 0.1)",
+        "value": b["recall"], "unit": "fraction", "higher_is_better": True, "problems": args.quality_count,
+        "rotated_frame": bool(args.rotated_frame), "rotation_grid": f"hopf N_side={args.hopf_n}",
+        "voxel_centre_t": a, "refined_t": b, "refine_iterations": args.refine_iterations,
+        "second_pass": {"top_k": args.refine_top_k, "K": args.refine_K, "delta_deg": args.refine_delta_deg},
+        "register_s_mean": statistics.mean(x[0] for x in times),
+        "refine_ms_mean": 1e3 * statistics.mean(x[1] for x in times), "data": "synthetic",
+    }), flush=True)
+
+
+def sweep(args, ws, rank, local):
+    """Registration time against the search range (the compute-time study of
+    Section V): rotation range swept at a +-0.2 translation box, translation
+    range swept at +-45 deg, on Euler-box grids (step 2.5 deg) centred on the
+    identity, ModelNet-shaped clouds, the translation box centred on a 0.1
+    rounding of the true translation (a local search around a prior)."""
+    import torch
+
+    from paper_2502_00115_b300 import build, capi, synth
+
+    torch.cuda.set_device(local)
+    build.build()
+    ctx = capi.Context(local)
+    ctx.set_option("record_timing", 1)
+    step = math.radians(2.5)
+    points = [("rotation", deg, 0.2) for deg in (5.0, 10.0, 20.0, 30.0, 45.0)]
+    points += [("translation", 45.0, s) for s in (0.05, 0.1, 0.2, 0.4, 0.8)]
+    rows = []
+    for kind, deg, half in points:
+        p = synth.modelnet_like_problem(args.seed, max_euler_deg=deg)
+        K = int(round(deg / 2.5))
+        t = ctx.create_target(p.Y, grid_cap=2 * p.tau)
+        centre = tuple(float(v) for v in np.round(p.t_true, 1))
+        pr = capi.make_params(metric=p.metric, epsilon=p.epsilon, delta_t=p.delta_t, tau=p.tau, t_center=centre,
+                              t_half=(half, half, half))
+        pb = ctx.problem(t, p.X, capi.euler_box_grid(np.eye(3), K, step), pr)
+        for _ in range(max(1, args.warmup)):
+            ctx.register(pb)
+        ts = []
+        for _ in range(max(1, args.steps)):
+            t0 = time.perf_counter()
+            r = capi.result_dict(ctx.register(pb))
+            ts.append(time.perf_counter() - t0)
+        ctx.destroy_target(t)
+        e = pose_errors(r["R"], r["t"], p.R_true, p.t_true)
+        rows.append({"sweep": kind, "rotation_range_deg": deg, "translation_half": half,
+                     "rotations": (2 * K + 1) ** 3, "ms_per_registration": 1e3 * statistics.median(ts),
+                     "vote_ms": ctx.get_option("last_pass_ns") / 1e6,
+                     "count_ms": ctx.get_option("last_count_ns") / 1e6,
+                     "culled_vote": bool(ctx.get_option("last_vote_sparse")),
+                     "rotation_error_deg": e["mie_r"], "translation_error": e["mie_t"]})
+    ctx.close()
+    print(json.dumps({"workload": "search_range_sweep", "metric": "ms per registration", "unit": "ms",
+                      "higher_is_better": False, "data": "synthetic", "euler_step_deg": 2.5,
+                      "source_points": len(p.X), "target_points": len(p.Y), "points": rows}), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args.gpus)
@@ -489,6 +611,10 @@ def main():
         serving(args, ws, rank, local)
     elif args.workload == "robot_like":
         robot(args, ws, rank, local)
+    elif args.workload == "quality":
+        quality(args, ws, rank, local)
+    elif args.workload == "sweep":
+        sweep(args, ws, rank, local)
     else:
         ours(args, ws, rank, local)
 

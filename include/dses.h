@@ -193,6 +193,38 @@ dses_status dses_rotation_grid_build(dses_ctx* ctx, const dses_rotation_grid* gr
 dses_status dses_target_distance_grid(dses_ctx* ctx, const dses_target* target, float* D, float lo[3],
                                       float h[3], int32_t* res, float* cap);
 
+/* Sub-voxel translation refinement (a step after Algorithm 2, which returns
+ * the voxel centre t* = k* delta_t, up to (sqrt 3 / 2) delta_t from the
+ * optimum). At the pose (R, t) every source point is paired with its nearest
+ * target point and the pair is kept when that distance is below epsilon (the
+ * inlier test of Eq. 3); the translation minimising the summed squared
+ * residual of the kept pairs is their mean of y_nn(i) - R x_i, which replaces
+ * t. `iterations` (1..64) such steps run, each re-pairing at the new t. src:
+ * n_src x 3 FP32 (host, or a device pointer of the context's device with
+ * src_is_device = 1). R (row-major 3x3, y ~ R x + t), t and t_out (3 floats)
+ * are host memory; t_out may alias t. *n_inliers (may be NULL) receives the
+ * number of pairs kept in the last step; with none kept t is left as it was.
+ * Blocking. Errors: INVALID_ARG (NULL or non-finite input, epsilon <= 0,
+ * iterations out of range, a target of another context), OOM, CUDA. */
+dses_status dses_refine_translation(dses_ctx* ctx, const dses_target* target, const float* src, int64_t n_src,
+                                    int32_t src_is_device, const float R[9], const float t[3], float epsilon,
+                                    int32_t iterations, float t_out[3], uint32_t* n_inliers);
+
+/* Algorithm 1 (pure exhaustive search), the validator of Algorithm 2 on small
+ * problems: for every rotation of problem->grid and every lattice translation
+ * k delta_t of the params' translation box, the error
+ *   e(R, t) = sum_i rho(min_j ||y_j - R x_i - t||)
+ * with exact nearest neighbours (nn_mode, q_milli, top_k and the refinement
+ * fields are ignored). out receives the pose of the smallest error (the first
+ * in index order on ties): R, t = k delta_t, rot_index, cost = e, inliers =
+ * M of Eq. 3 at that pose, votes = 0. cost_out (host, may be NULL) receives
+ * every e at [r * n_t + t], t = ((kx - lo_x) E_y + (ky - lo_y)) E_z +
+ * (kz - lo_z) over the box's lattice extents E, and needs cost_capacity >=
+ * n_rot * n_t. Work is n_rot * n_t * N * M distances: target m <= 12288 and
+ * n_rot * n_t <= 2^28 (else INVALID_ARG). Blocking. Errors: as dses_register. */
+dses_status dses_exhaustive_search(dses_ctx* ctx, const dses_problem* problem, float* cost_out,
+                                   int64_t cost_capacity, dses_result* out);
+
 /* Tuning and engine options (key = value). Keys:
  *   "hist_mode"            0 auto, 1 force 32-bit counters, 2 force packed 16-bit
  *   "hist_budget_bytes"    shared-memory bytes for the vote histogram (slabs below it)
@@ -218,6 +250,10 @@ dses_status dses_target_distance_grid(dses_ctx* ctx, const dses_target* target, 
  *   "last_pass_launches"   (read-only) how many rotation passes that call made
  *   "last_votes_total"     (read-only) histogram increments (pairs voting inside
  *                          the translation box) of the last blocking call
+ *   "last_vote_sparse"     (read-only) how many problems of the last blocking call
+ *                          ran the culled (windowed) vote
+ *   "graphs_cached"        (read-only) captured CUDA graphs held by the context
+ *                          (dses_destroy_target drops those that read the target)
  *   "kernel_launches"      (read-only) kernels this library has launched in the
  *                          process so far (all contexts)
  * INVALID_ARG for an unknown key or a value out of range. */

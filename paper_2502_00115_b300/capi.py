@@ -108,6 +108,8 @@ SIGNATURES = {
     "dses_set_option": (_i32, [_vp, ctypes.c_char_p, _i64]),
     "dses_get_option": (_i32, [_vp, ctypes.c_char_p, _P(_i64)]),
     "dses_vote_static": (_i32, [_i32, _vp, _vp, _i64, _vp, _i64, _vp, _i64, _P(dses_params), _vp]),
+    "dses_exhaustive_search": (_i32, [_vp, _P(dses_problem), _vp, _i64, _P(dses_result)]),
+    "dses_refine_translation": (_i32, [_vp, _vp, _vp, _i64, _i32, _vp, _vp, _f32, _i32, _vp, _P(ctypes.c_uint32)]),
     "dses_last_error": (ctypes.c_char_p, [_vp]),
     "dses_status_string": (ctypes.c_char_p, [_i32]),
 }
@@ -240,6 +242,33 @@ def dses_vote_static(device: int, stream: int, src_ptr: int, n_src: int, tgt_ptr
     return load().dses_vote_static(device, ctypes.c_void_p(stream or 0), ctypes.c_void_p(src_ptr), n_src,
                                    ctypes.c_void_p(tgt_ptr), n_tgt, ctypes.c_void_p(rot_ptr), n_rot,
                                    ctypes.byref(params), ctypes.c_void_p(kv_ptr))
+
+
+def dses_refine_translation(ctx, target, src, n_src: int, src_is_device: int, R, t, epsilon: float,
+                            iterations: int = 1):
+    """src: a float32 (n, 3) array, or a device pointer with src_is_device = 1.
+    Returns (status, t_refined float32[3], n_inliers)."""
+    Rh = np.ascontiguousarray(np.asarray(R, dtype=np.float32).reshape(9))
+    th = np.ascontiguousarray(np.asarray(t, dtype=np.float32).reshape(3))
+    out = np.zeros(3, dtype=np.float32)
+    n = ctypes.c_uint32()
+    if src_is_device:
+        sp = ctypes.c_void_p(src)
+    else:
+        src = np.ascontiguousarray(np.asarray(src, dtype=np.float32))
+        sp = ctypes.c_void_p(src.ctypes.data)
+    st = load().dses_refine_translation(ctx, target, sp, n_src, src_is_device, Rh.ctypes.data, th.ctypes.data,
+                                        epsilon, iterations, out.ctypes.data, ctypes.byref(n))
+    return st, out, n.value
+
+
+def dses_exhaustive_search(ctx, problem: dses_problem, n_entries: int = 0):
+    """Returns (status, result, cost array of n_entries floats or None)."""
+    r = dses_result()
+    cost = np.zeros(n_entries, dtype=np.float32) if n_entries else None
+    st = load().dses_exhaustive_search(ctx, ctypes.byref(problem), cost.ctypes.data if cost is not None else None,
+                                       n_entries, ctypes.byref(r))
+    return st, r, cost
 
 
 def dses_last_error(ctx) -> str:
@@ -394,6 +423,17 @@ class Context:
         st, D, lo, h, cap = dses_target_distance_grid(self.h, target)
         self.check(st)
         return D, lo, h, cap
+
+    def exhaustive(self, pb: dses_problem, n_entries: int = 0):
+        st, r, cost = dses_exhaustive_search(self.h, pb, n_entries)
+        self.check(st)
+        return r, cost
+
+    def refine_translation(self, target, X, R, t, epsilon: float, iterations: int = 1):
+        X = np.ascontiguousarray(np.asarray(X, dtype=np.float32))
+        st, tr, n = dses_refine_translation(self.h, target, X, len(X), 0, R, t, epsilon, iterations)
+        self.check(st)
+        return tr, n
 
 
 def result_dict(r: dses_result) -> dict:

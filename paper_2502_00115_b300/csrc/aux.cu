@@ -294,16 +294,6 @@ __global__ void cand_from_keys_kernel(const unsigned long long* keys, int k, uin
 // ---------------------------------------------------------------------------
 // candidate scoring
 
-__device__ __forceinline__ float rho_f(int metric, float d, float eps, float tau, float h, float p) {
-  switch (metric) {
-    case 0: return d < eps ? 0.f : 1.f;
-    case 1: return fminf(d, tau);
-    case 2: { const float e = fminf(d, tau); return e * e; }
-    case 3: { const float e = fminf(d, tau); return e <= h ? 0.5f * e * e : h * (e - 0.5f * h); }
-    default: return powf(d, p);
-  }
-}
-
 __device__ __forceinline__ float grid_lookup_s(const ScoreDesc& d, float qx, float qy, float qz) {
   const float G = (float)d.G;
   float gx = (qx - d.glo[0]) * d.ginv_h[0];
@@ -343,7 +333,7 @@ __global__ void score_grid_kernel(ScoreDesc d, const uint32_t* cand, const uint3
       const float qx = fmaf(R[0], x, fmaf(R[1], y, R[2] * z)) + tx;
       const float qy = fmaf(R[3], x, fmaf(R[4], y, R[5] * z)) + ty;
       const float qz = fmaf(R[6], x, fmaf(R[7], y, R[8] * z)) + tz;
-      s += rho_f(d.metric, grid_lookup_s(d, qx, qy, qz), d.eps, d.tau, d.huber_h, d.p_exp);
+      s += robust_rho(d.metric, grid_lookup_s(d, qx, qy, qz), d.eps, d.tau, d.huber_h, d.p_exp);
     }
 #pragma unroll
     for (int k = 16; k > 0; k >>= 1) s += __shfl_xor_sync(0xffffffffu, s, k);
@@ -400,7 +390,7 @@ __global__ void __launch_bounds__(kBruteThreads) score_brute_kernel(ScoreDesc d,
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int i = g0 + u * kBruteThreads + threadIdx.x;
-        if (i < d.N) s += rho_f(d.metric, sqrtf(best[u]), d.eps, d.tau, d.huber_h, d.p_exp);
+        if (i < d.N) s += robust_rho(d.metric, sqrtf(best[u]), d.eps, d.tau, d.huber_h, d.p_exp);
       }
     }
 #pragma unroll

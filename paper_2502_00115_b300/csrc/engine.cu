@@ -122,6 +122,7 @@ struct Options {
 
 struct dses_target {
   dses_ctx* ctx = nullptr;
+  uint64_t uid = 0;         // never reused within a context (graph-cache key)
   int m = 0;
   std::vector<float> host;  // m x 3
   float bbmin[3], bbmax[3];
@@ -153,6 +154,7 @@ struct dses_ctx {
   std::string err;
   std::map<int, float*> hopf;  // cached Hopf grids by N_side
   std::vector<dses_target*> targets;
+  uint64_t next_target_uid = 1;
   Options opt;
   // serving
   std::mutex smu;
@@ -175,6 +177,8 @@ struct dses_ctx {
   int64_t pass_launches = 0;
   int64_t launch_snapshot = 0;
   int64_t votes_total = 0;  // in-box pair votes of the last blocking call
+  int64_t vote_sparse_jobs = 0;  // problems of the last blocking call on the culled vote
+  int64_t graph_count = 0;       // snapshot for the "graphs_cached" option
   // host staging: blocking calls, the serving worker, and the one in use
   Stage stage, serve_stage;
   Stage* cur_stage = nullptr;
@@ -1108,7 +1112,9 @@ std::string graph_key(dses_ctx* c, const std::vector<Job*>& jobs) {
     const dses_problem& pb = *j->prob;
     if (pb.grid.kind == DSES_GRID_EXPLICIT) return std::string();  // grid contents not tracked
     const dses_params& P = pb.params;
-    snprintf(buf, sizeof(buf), "%p,%d,%p,%lld,%d,%d,%d,%.17g|", (const void*)pb.target, pb.src_is_device,
+    // the target by its uid, not its address: a destroyed target's address can
+    // come back for a new one while graphs captured on the old one remain
+    snprintf(buf, sizeof(buf), "T%llu,%d,%p,%lld,%d,%d,%d,%.17g|", (unsigned long long)j->T->uid, pb.src_is_device,
              pb.src_is_device ? (const void*)pb.src : nullptr, (long long)pb.n_src, pb.grid.kind, pb.grid.hopf_n,
              pb.grid.K, pb.grid.delta_r);
     k += buf;
@@ -1247,6 +1253,8 @@ dses_status finish_results(dses_ctx* c, std::vector<Job*>& jobs, dses_result* ou
   CK(cudaStreamSynchronize(c->stream));
   c->votes_total = 0;
   for (auto v : votes) c->votes_total += (int64_t)v;
+  c->vote_sparse_jobs = 0;
+  for (auto* j : jobs) c->vote_sparse_jobs += j->sparse ? 1 : 0;
   collect_timing(c);
   dses_status st = DSES_OK;
   for (size_t i = 0; i < jobs.size(); ++i) {
@@ -1347,6 +1355,7 @@ dses_status dses_create_target(dses_ctx* c, const float* xyz, int64_t m, int32_t
     set_device(c);
     std::unique_ptr<dses_target> T(new dses_target());
     T->ctx = c;
+    T->uid = c->next_target_uid++;
     T->m = (int)m;
     T->host.resize(3 * (size_t)m);
     if (ptr_is_device) {
@@ -1397,6 +1406,18 @@ dses_status dses_destroy_target(dses_ctx* c, dses_target* T) {
     if (T->inflight.load() > 0) invalid("target is still used by submitted requests");
     set_device(c);
     CK(cudaStreamSynchronize(c->stream));
+    // drop the captured graphs (and capture counters) that read this target
+    const std::string tok = "T" + std::to_string((unsigned long long)T->uid) + ",";
+    for (auto g = c->graphs.begin(); g != c->graphs.end();) {
+      if (g->first.find(tok) != std::string::npos) {
+        free_graph(g->second);
+        g = c->graphs.erase(g);
+      } else {
+        ++g;
+      }
+    }
+    for (auto g = c->graph_seen.begin(); g != c->graph_seen.end();)
+      g = g->first.find(tok) != std::string::npos ? c->graph_seen.erase(g) : std::next(g);
     c->targets.erase(it);
     free_target(T);
   });
@@ -1591,6 +1612,161 @@ dses_status dses_target_distance_grid(dses_ctx* c, const dses_target* T, float* 
   });
 }
 
+dses_status dses_refine_translation(dses_ctx* c, const dses_target* Tc, const float* src, int64_t n_src,
+                                    int32_t src_is_device, const float R[9], const float t[3], float epsilon,
+                                    int32_t iterations, float t_out[3], uint32_t* n_inliers) {
+  if (!c || !Tc) return DSES_ERR_INVALID_ARG;
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  return guard(c, [&] {
+    dses_target* T = const_cast<dses_target*>(Tc);
+    if (T->ctx != c) invalid("target belongs to another context");
+    if (!src || n_src < 1 || n_src > (1 << 24)) invalid("n_src must be in [1, 2^24]");
+    if (!R || !t || !t_out) invalid("R, t and t_out are required");
+    if (!finite3(R, 3) || !finite3(t, 1)) invalid("R and t must be finite");
+    if (!(epsilon > 0) || !std::isfinite(epsilon)) invalid("epsilon must be positive and finite");
+    if (iterations < 1 || iterations > 64) invalid("iterations must be in [1, 64]");
+    if (!src_is_device && !finite3(src, n_src)) invalid("source cloud has a non-finite coordinate");
+    set_device(c);
+    CellList* cl = cell_list(c, T, epsilon);
+    DevMem scratch, xs;
+    scratch.alloc(64, c->stream);  // t (3 doubles), acc (4 doubles), count
+    double* td = (double*)scratch.p;
+    double* acc = td + 3;
+    uint32_t* nd = (uint32_t*)(td + 7);
+    double th[8] = {t[0], t[1], t[2], 0.0, 0.0, 0.0, 0.0, 0.0};
+    CK(cudaMemcpyAsync(td, th, sizeof(th), cudaMemcpyHostToDevice, c->stream));
+    const float* X = src;
+    if (!src_is_device) {
+      xs.alloc(12 * (size_t)n_src, c->stream);
+      CK(cudaMemcpyAsync(xs.p, src, 12 * (size_t)n_src, cudaMemcpyHostToDevice, c->stream));
+      X = (const float*)xs.p;
+    }
+    RefineDesc d;
+    d.X = X;
+    d.N = (int)n_src;
+    d.Y = cl->sorted;
+    d.cell_start = cl->start;
+    for (int a = 0; a < 3; ++a) {
+      d.cell_lo[a] = cl->lo[a];
+      d.cell_dim[a] = cl->dim[a];
+    }
+    d.cell_inv = cl->inv;
+    d.eps2 = epsilon * epsilon;
+    for (int k = 0; k < 9; ++k) d.R[k] = R[k];
+    d.t = td;
+    d.acc = acc;
+    for (int it = 0; it < iterations; ++it) CK(launch_refine_step(d, nd, c->stream));
+    double tr[3];
+    uint32_t n = 0;
+    CK(cudaMemcpyAsync(tr, td, sizeof(tr), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&n, nd, sizeof(n), cudaMemcpyDeviceToHost, c->stream));
+    xs.release();
+    scratch.release();
+    CK(cudaStreamSynchronize(c->stream));
+    for (int a = 0; a < 3; ++a) t_out[a] = (float)tr[a];
+    if (n_inliers) *n_inliers = n;
+  });
+}
+
+dses_status dses_exhaustive_search(dses_ctx* c, const dses_problem* problem, float* cost_out, int64_t cost_capacity,
+                                   dses_result* out) {
+  if (!c || !problem || !out) return DSES_ERR_INVALID_ARG;
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  return guard(c, [&] {
+    // exact nearest neighbours; the candidate filter and the second pass do not apply
+    dses_problem q = *problem;
+    q.params.nn_mode = DSES_NN_BRUTE;
+    q.params.q_milli = 0;
+    q.params.top_k = 0;
+    q.params.refine_top_k = 0;
+    Job j;
+    resolve(c, &q, j);
+    if (j.T->m > kExhaustiveMaxTargets) invalid("exhaustive search stages the target in shared memory: m <= 12288");
+    const int64_t nt = (int64_t)j.E[0] * j.E[1] * j.E[2];
+    const int64_t total = j.n_first * nt;
+    if (total > (1LL << 28)) invalid("exhaustive search is limited to 2^28 (rotation, translation) pairs");
+    if (cost_out && cost_capacity < total) invalid("cost_capacity is smaller than rotations x translations");
+    set_device(c);
+    cudaStream_t s = c->stream;
+    const dses_rotation_grid& gr = q.grid;
+    DevMem rmem, xmem, omem;
+    const float* rot = nullptr;
+    if (gr.kind == DSES_GRID_HOPF) {
+      rot = hopf_grid(c, gr.hopf_n);
+    } else if (gr.kind == DSES_GRID_EULER_BOX) {
+      rmem.alloc(align256(36 * (size_t)j.n_first) + 256, s);
+      double* R0 = (double*)((char*)rmem.p + align256(36 * (size_t)j.n_first));
+      CK(cudaMemcpyAsync(R0, gr.R0, 72, cudaMemcpyHostToDevice, s));
+      CK(launch_euler_box_single(R0, gr.K, gr.delta_r, (float*)rmem.p, s));
+      rot = (const float*)rmem.p;
+    } else {
+      if (!finite3(gr.explicit_R, 3 * gr.n_explicit)) invalid("explicit rotations have a non-finite entry");
+      rmem.alloc(36 * (size_t)j.n_first, s);
+      CK(cudaMemcpyAsync(rmem.p, gr.explicit_R, 36 * (size_t)j.n_first, cudaMemcpyHostToDevice, s));
+      rot = (const float*)rmem.p;
+    }
+    const float* X = q.src;
+    if (!q.src_is_device) {
+      xmem.alloc(12 * (size_t)j.N, s);
+      CK(cudaMemcpyAsync(xmem.p, q.src, 12 * (size_t)j.N, cudaMemcpyHostToDevice, s));
+      X = (const float*)xmem.p;
+    }
+    omem.alloc(align256(4 * (size_t)total) * 2 + 256, s);
+    float* cost = (float*)omem.p;
+    uint32_t* count = (uint32_t*)((char*)omem.p + align256(4 * (size_t)total));
+    unsigned long long* best = (unsigned long long*)((char*)count + align256(4 * (size_t)total));
+    CK(launch_fill_u64(best, ~0ull, 1, s));
+    ExhaustiveDesc d;
+    d.X = X;
+    d.N = j.N;
+    d.Y = j.T->Y;
+    d.M = j.T->m;
+    d.rot = rot;
+    d.n_rot = (int)j.n_first;
+    for (int a = 0; a < 3; ++a) {
+      d.lo[a] = j.lo[a];
+      d.E[a] = j.E[a];
+    }
+    d.n_t = (int)nt;
+    d.delta = j.delta;
+    d.metric = j.metric;
+    d.eps = j.eps;
+    d.tau = j.tau;
+    d.huber_h = j.hh;
+    d.p_exp = j.pexp;
+    d.cost = cost;
+    d.count = count;
+    d.best = best;
+    CK(launch_exhaustive(d, s));
+    unsigned long long key = 0;
+    CK(cudaMemcpyAsync(&key, best, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const int64_t idx = (int64_t)(key & 0xffffffffull);
+    const int64_t r = idx / nt, ti = idx % nt;
+    float Rh[9], ch = 0.f;
+    uint32_t nh = 0;
+    CK(cudaMemcpyAsync(Rh, rot + 9 * r, 36, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&ch, cost + idx, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&nh, count + idx, 4, cudaMemcpyDeviceToHost, s));
+    if (cost_out) CK(cudaMemcpyAsync(cost_out, cost, 4 * (size_t)total, cudaMemcpyDeviceToHost, s));
+    rmem.release();
+    xmem.release();
+    omem.release();
+    CK(cudaStreamSynchronize(s));
+    dses_result res;
+    std::memset(&res, 0, sizeof(res));
+    for (int k = 0; k < 9; ++k) res.R[k] = Rh[k];
+    const int64_t k3[3] = {ti / ((int64_t)j.E[1] * j.E[2]), (ti / j.E[2]) % j.E[1], ti % j.E[2]};
+    for (int a = 0; a < 3; ++a) res.t[a] = (float)(j.lo[a] + k3[a]) * j.delta;
+    res.rot_index = r;
+    res.inliers = nh;
+    res.votes = 0;
+    res.cost = ch;
+    res.status = DSES_OK;
+    *out = res;
+  });
+}
+
 static int64_t* option_slot(dses_ctx* c, const char* key) {
   if (!key) return nullptr;
   const std::string k(key);
@@ -1613,6 +1789,11 @@ static int64_t* option_slot(dses_ctx* c, const char* key) {
   if (k == "last_pass_launches") return &c->pass_launches;
   if (k == "last_count_ns") return &c->count_ns;
   if (k == "last_votes_total") return &c->votes_total;
+  if (k == "last_vote_sparse") return &c->vote_sparse_jobs;
+  if (k == "graphs_cached") {
+    c->graph_count = (int64_t)c->graphs.size();
+    return &c->graph_count;
+  }
   if (k == "kernel_launches") {
     c->launch_snapshot = kernel_launch_count();
     return &c->launch_snapshot;
@@ -1634,7 +1815,7 @@ dses_status dses_set_option(dses_ctx* c, const char* key, int64_t value) {
     else if (k == "fuse_score" || k == "autotune" || k == "use_graphs" || k == "record_timing")
       ok = value == 0 || value == 1;
     else if (k == "last_pass_ns" || k == "last_pass_launches" || k == "kernel_launches" || k == "last_count_ns" ||
-             k == "last_votes_total")
+             k == "last_votes_total" || k == "last_vote_sparse" || k == "graphs_cached")
       ok = false;  // read-only
     else if (k == "tile_rotations") ok = value >= 0 && value <= 4096;
     else ok = value >= 1;

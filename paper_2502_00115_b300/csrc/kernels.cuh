@@ -8,6 +8,19 @@
 
 namespace dses {
 
+// Robust per-point error rho(d) of a nearest-target distance d (the norm of
+// Eq. 1): 0 inlier indicator [d >= eps] (Eq. 3), 1 truncated L1 min(d, tau),
+// 2 truncated L2 min(d, tau)^2, 3 Huber with knee h on min(d, tau), 4 d^p.
+__device__ __forceinline__ float robust_rho(int metric, float d, float eps, float tau, float h, float p) {
+  switch (metric) {
+    case 0: return d < eps ? 0.f : 1.f;
+    case 1: return fminf(d, tau);
+    case 2: { const float e = fminf(d, tau); return e * e; }
+    case 3: { const float e = fminf(d, tau); return e <= h ? 0.5f * e * e : h * (e - 0.5f * h); }
+    default: return powf(d, p);
+  }
+}
+
 // Threads of the rotation-pass CTA (one CTA per SM, 32 warps).
 constexpr int kPassThreads = 1024;
 // Source points staged per chunk in shared memory (float4 each).
@@ -169,6 +182,50 @@ struct FinalDesc {
   void* result;           // device dses_result
 };
 cudaError_t launch_finalize(const FinalDesc* d_dev, int count, cudaStream_t s);
+
+// One step of the sub-voxel translation refinement at (R, t): the mean of
+// y_nn(i) - R x_i over source points whose nearest target (cell-list search)
+// is closer than epsilon. t (3 doubles, device) is read and replaced by that
+// mean (kept when no pair qualifies); acc (4 doubles, device) must be zero and
+// is left zero; *n_out (device) receives the number of pairs.
+struct RefineDesc {
+  const float* X;         // source, N x 3
+  int N;
+  const float4* Y;        // target in cell order
+  const int* cell_start;  // cells + 1
+  float cell_lo[3];
+  float cell_inv;
+  int cell_dim[3];
+  float eps2;
+  float R[9];
+  double* t;
+  double* acc;
+};
+cudaError_t launch_refine_step(const RefineDesc& d, uint32_t* n_out, cudaStream_t s);
+
+// Algorithm 1 over a rotation list and the lattice box: cost[r n_t + t] and
+// count[r n_t + t] (inliers of Eq. 3) for every pair, atomicMin of
+// (cost bits << 32 | r n_t + t) into *best (initialised to ~0 by the caller).
+// t = ((kx - lo_x) E_y + (ky - lo_y)) E_z + (kz - lo_z). The target (M float4)
+// is staged in shared memory: M <= kExhaustiveMaxTargets.
+constexpr int kExhaustiveMaxTargets = 12288;
+struct ExhaustiveDesc {
+  const float* X;     // source, N x 3
+  int N;
+  const float4* Y;    // target, M points
+  int M;
+  const float* rot;   // n_rot x 9
+  int n_rot;
+  int lo[3], E[3];
+  int n_t;            // E_x E_y E_z
+  float delta;
+  int metric;
+  float eps, tau, huber_h, p_exp;
+  float* cost;
+  uint32_t* count;
+  unsigned long long* best;
+};
+cudaError_t launch_exhaustive(const ExhaustiveDesc& d, cudaStream_t s);
 
 // Kernels launched by this library since it was loaded (all launch sites count).
 long long kernel_launch_count();

@@ -40,25 +40,6 @@ __device__ __forceinline__ unsigned floor_bits(float v) {
   return (unsigned)(__float_as_int(__fadd_rd(v, kMagic)) - (int)kMagicBits);
 }
 
-__device__ __forceinline__ float rho(int metric, float d, float eps, float tau, float h, float p) {
-  switch (metric) {
-    case 0:
-      return d < eps ? 0.f : 1.f;
-    case 1:
-      return fminf(d, tau);
-    case 2: {
-      const float e = fminf(d, tau);
-      return e * e;
-    }
-    case 3: {
-      const float e = fminf(d, tau);
-      return e <= h ? 0.5f * e * e : h * (e - 0.5f * h);
-    }
-    default:
-      return powf(d, p);
-  }
-}
-
 // Trilinear value of the distance grid at q (interpolation between voxel
 // centres, clamped at the outermost centres; the cap outside the grid box),
 // together with bounds on the exact nearest-target distance d(q): the stored values are
@@ -244,7 +225,7 @@ template <bool U16>
 __device__ __forceinline__ void vote_two_pairs(uint64_t yx, uint64_t yy, uint64_t yz, uint64_t inv2, uint64_t cx2,
                                                uint64_t cy2, uint64_t cz2, uint64_t mx2, uint64_t my2, uint64_t mz2,
                                                uint32_t Eyz, uint32_t Ez, uint32_t abase, float hx, float hy,
-                                               float hz) {
+                                               float hz, float hx1) {
   if (U16) {
     asm volatile(
         "{\n\t.reg .b64 wx, wy, wz, fx, fy, fz;\n\t"
@@ -265,10 +246,10 @@ __device__ __forceinline__ void vote_two_pairs(uint64_t yx, uint64_t yy, uint64_
         "abs.f32 x0, x0;\n\tabs.f32 x1, x1;\n\tabs.f32 y0, y0;\n\tabs.f32 y1, y1;\n\t"
         "abs.f32 z0, z0;\n\tabs.f32 z1, z1;\n\t"
         "setp.lt.f32 p0, x0, %13;\n\tsetp.lt.and.f32 p0, y0, %14, p0;\n\tsetp.lt.and.f32 p0, z0, %15, p0;\n\t"
-        "setp.lt.f32 p1, x1, %13;\n\tsetp.lt.and.f32 p1, y1, %14, p1;\n\tsetp.lt.and.f32 p1, z1, %15, p1;\n\t"
+        "setp.lt.f32 p1, x1, %16;\n\tsetp.lt.and.f32 p1, y1, %14, p1;\n\tsetp.lt.and.f32 p1, z1, %15, p1;\n\t"
         "@p0 red.shared.add.u32 [a0], i0;\n\t@p1 red.shared.add.u32 [a1], i1;\n\t}" ::"l"(yx),
         "l"(yy), "l"(yz), "l"(inv2), "l"(cx2), "l"(cy2), "l"(cz2), "l"(mx2), "l"(my2), "l"(mz2), "r"(Eyz), "r"(Ez),
-        "r"(abase), "f"(hx), "f"(hy), "f"(hz));
+        "r"(abase), "f"(hx), "f"(hy), "f"(hz), "f"(hx1));
   } else {
     asm volatile(
         "{\n\t.reg .b64 wx, wy, wz, fx, fy, fz;\n\t"
@@ -285,10 +266,10 @@ __device__ __forceinline__ void vote_two_pairs(uint64_t yx, uint64_t yy, uint64_
         "abs.f32 x0, x0;\n\tabs.f32 x1, x1;\n\tabs.f32 y0, y0;\n\tabs.f32 y1, y1;\n\t"
         "abs.f32 z0, z0;\n\tabs.f32 z1, z1;\n\t"
         "setp.lt.f32 p0, x0, %13;\n\tsetp.lt.and.f32 p0, y0, %14, p0;\n\tsetp.lt.and.f32 p0, z0, %15, p0;\n\t"
-        "setp.lt.f32 p1, x1, %13;\n\tsetp.lt.and.f32 p1, y1, %14, p1;\n\tsetp.lt.and.f32 p1, z1, %15, p1;\n\t"
+        "setp.lt.f32 p1, x1, %16;\n\tsetp.lt.and.f32 p1, y1, %14, p1;\n\tsetp.lt.and.f32 p1, z1, %15, p1;\n\t"
         "@p0 red.shared.add.u32 [a0], 1;\n\t@p1 red.shared.add.u32 [a1], 1;\n\t}" ::"l"(yx),
         "l"(yy), "l"(yz), "l"(inv2), "l"(cx2), "l"(cy2), "l"(cz2), "l"(mx2), "l"(my2), "l"(mz2), "r"(Eyz * 4u),
-        "r"(Ez * 4u), "r"(abase), "f"(hx), "f"(hy), "f"(hz));
+        "r"(Ez * 4u), "r"(abase), "f"(hx), "f"(hy), "f"(hz), "f"(hx1));
   }
 }
 
@@ -333,7 +314,7 @@ __device__ __forceinline__ void vote_centred_x2(const PassDesc& d, const float4*
       const uint64_t cx2 = pack2(ca.x, ca.y), cy2 = pack2(ca.z, ca.w), cz2 = pack2(cb.x, cb.y);
 #pragma unroll
       for (int q = 0; q < P / 2; ++q)
-        vote_two_pairs<U16>(yx[q], yy[q], yz[q], inv2, cx2, cy2, cz2, mx2, my2, mz2, Eyz, Ez, abase, hx, hy, hz);
+        vote_two_pairs<U16>(yx[q], yy[q], yz[q], inv2, cx2, cy2, cz2, mx2, my2, mz2, Eyz, Ez, abase, hx, hy, hz, hx);
     }
   }
 }
@@ -669,7 +650,7 @@ __global__ void __launch_bounds__(256) count_kernel(PassLaunch L) {
       else
         inl = has_inlier(d, qx, qy, qz);
       cnt += inl ? 1 : 0;
-      if (grid_cost) csum += rho(d.metric, dg, d.eps, d.tau, d.huber_h, d.p_exp);
+      if (grid_cost) csum += robust_rho(d.metric, dg, d.eps, d.tau, d.huber_h, d.p_exp);
     }
 #pragma unroll
     for (int k = 16; k > 0; k >>= 1) {

@@ -41,6 +41,16 @@ def uniform_rotation(rng: np.random.Generator) -> np.ndarray:
     )
 
 
+def euler_rotation(rng: np.random.Generator, max_deg: float) -> np.ndarray:
+    """Rz(a) Ry(b) Rx(c) with the three angles uniform in [-max_deg, max_deg]
+    (the ModelNet40 protocol of Section V-A draws Euler angles in [-45, 45] deg)."""
+    a, b, c = np.radians(rng.uniform(-max_deg, max_deg, 3))
+    Rz = np.array([[math.cos(a), -math.sin(a), 0], [math.sin(a), math.cos(a), 0], [0, 0, 1]])
+    Ry = np.array([[math.cos(b), 0, math.sin(b)], [0, 1, 0], [-math.sin(b), 0, math.cos(b)]])
+    Rx = np.array([[1, 0, 0], [0, math.cos(c), -math.sin(c)], [0, math.sin(c), math.cos(c)]])
+    return Rz @ Ry @ Rx
+
+
 def unit_vector(rng: np.random.Generator) -> np.ndarray:
     v = rng.normal(size=3)
     return v / np.linalg.norm(v)
@@ -206,13 +216,14 @@ class Problem:
         return base + self.refine_top_k * (2 * self.refine_K + 1) ** 3
 
 
-def _place_source(rng, shape_pts, t_range):
-    """Apply a uniform rotation and a uniform translation to the observed points.
+def _place_source(rng, shape_pts, t_range, max_euler_deg=None):
+    """Apply a rotation (uniform, or Euler angles uniform in +-max_euler_deg)
+    and a uniform translation to the observed points.
 
     Returns the moved points and the pose (R, t) with y = R x + t mapping the
     moved points back onto the model frame.
     """
-    A = uniform_rotation(rng)
+    A = uniform_rotation(rng) if max_euler_deg is None else euler_rotation(rng, max_euler_deg)
     b = rng.uniform(-t_range, t_range, size=3)
     moved = shape_pts @ A.T + b
     return moved, A.T, -A.T @ b
@@ -234,11 +245,15 @@ def tiny_problem(seed: int = 0, noise: float = 0.005, hopf_n: int = 4) -> Proble
 
 
 def modelnet_like_problem(seed: int = 0, m: int = 1024, keep: float = 0.7, hopf_n: int = 16,
-                          name: str = "modelnet_like") -> Problem:
+                          name: str = "modelnet_like", max_euler_deg: float | None = None,
+                          rotated_frame: bool = False) -> Problem:
     """Section V-A protocol on a synthetic shape: independent 1,024-point samples of
     the same surface for source and target, noise N(0, 0.01) clipped at 0.05 on
-    both clouds, a 70% half-space crop of the source, a uniform random rotation
-    and a translation in [-0.5, 0.5]^3."""
+    both clouds, a 70% half-space crop of the source, a random rotation (uniform,
+    or Euler angles uniform in +-max_euler_deg as the paper draws them) and a
+    translation in [-0.5, 0.5]^3. rotated_frame: both clouds are then turned by
+    one more uniform rotation Q (the changed reference frame of Section V-A);
+    the relative pose becomes (Q R Q^T, Q t)."""
     rng = np.random.default_rng(seed)
     prims = random_primitives(rng, 3)
     both = sample_union_surface(rng, prims, 2 * m)
@@ -246,7 +261,11 @@ def modelnet_like_problem(seed: int = 0, m: int = 1024, keep: float = 0.7, hopf_
     Y = both[:m] + clipped_noise(rng, (m, 3), 0.01, 0.05)
     Xs = both[m:] + clipped_noise(rng, (m, 3), 0.01, 0.05)
     Xs = half_space_crop(rng, Xs, keep)
-    X, Rt, tt = _place_source(rng, Xs, 0.5)
+    X, Rt, tt = _place_source(rng, Xs, 0.5, max_euler_deg)
+    if rotated_frame:
+        Q = uniform_rotation(rng)
+        X, Y = X @ Q.T, Y @ Q.T
+        Rt, tt = Q @ Rt @ Q.T, Q @ tt
     return Problem(
         name=name, X=X.astype(np.float32), Y=Y.astype(np.float32), R_true=Rt, t_true=tt,
         epsilon=0.04, delta_t=0.04, t_center=(0.0, 0.0, 0.0), t_half=(0.9, 0.9, 0.9),

@@ -279,6 +279,33 @@ def test_graph_replayed_batches_equal_solo(ctx):
         ctx.destroy_target(t)
 
 
+def test_destroyed_targets_drop_their_graphs(ctx):
+    # captured graphs are keyed by a target id that is never reused: a target
+    # created after another was destroyed (its host address may come back)
+    # must not replay a graph captured on the old one, and destroying a target
+    # frees the graphs that read it
+    plain = capi.Context(0)
+    plain.set_option("use_graphs", 0)
+    base = ctx.get_option("graphs_cached")
+    try:
+        for s in range(4):
+            p = synth.tiny_problem(10 + s, hopf_n=2)
+            t = ctx.create_target(p.Y, grid_cap=2 * p.tau)
+            gp = gpu_params(p, nn_mode="grid")
+            rs = [capi.result_dict(ctx.register(ctx.problem(t, p.X, capi.hopf_grid(2), gp))) for _ in range(3)]
+            assert ctx.get_option("graphs_cached") == base + 1
+            tp = plain.create_target(p.Y, grid_cap=2 * p.tau)
+            ref = capi.result_dict(plain.register(plain.problem(tp, p.X, capi.hopf_grid(2), gp)))
+            plain.destroy_target(tp)
+            for r in rs:
+                assert r["rot_index"] == ref["rot_index"] and r["cost"] == ref["cost"]
+                assert np.array_equal(r["t"], ref["t"]) and r["inliers"] == ref["inliers"]
+            ctx.destroy_target(t)
+            assert ctx.get_option("graphs_cached") == base
+    finally:
+        plain.close()
+
+
 def test_autotuned_shapes_give_identical_results(ctx):
     p = synth.modelnet_like_problem(6, m=700, keep=0.7, hopf_n=3)
     t = ctx.create_target(p.Y, grid_cap=2 * p.tau)
