@@ -39,6 +39,10 @@ ALU_PEAK_OPS = 148 * 128 * 2032e6
 # (rotation, source point) 15 FP32 operations (the rotation R x_i)
 OPS_PER_PAIR = 4
 OPS_PER_ROT_SRC = 15
+# DRAM bytes (read + write) of one vote_kernel launch, from an ncu capture of
+# the same kernel on this problem at N_side 4: a launch reads its inputs (KB)
+# once, so the figure does not grow with the rotations and is used unscaled.
+VOTE_DRAM_BYTES = 240640
 
 
 def parse():
@@ -323,7 +327,8 @@ def ours(args, ws, rank, local):
         "latency_ms": {"p50": 1000 * float(np.percentile(e2e_s, 50)), "p99": 1000 * float(np.percentile(e2e_s, 99))},
         "roofline": {"bound": "alu", "kernel": "vote_kernel", "achieved": achieved / 1e12,
                      "peak": ALU_PEAK_OPS / 1e12, "unit": "Tops/s", "frac": achieved / ALU_PEAK_OPS,
-                     "traffic": None, "kernel_ms": pass_s * 1000,
+                     "traffic": VOTE_DRAM_BYTES, "traffic_unit": "bytes per launch (ncu, N_side 4 capture)",
+                     "kernel_ms": pass_s * 1000,
                      "count_kernel_ms": statistics.mean(count_ns) / 1e6,
                      "peak_source": "recipe unit counts: 148 SMs x 128 lanes x 2032 MHz",
                      "ops_per_launch": ops},
@@ -332,6 +337,10 @@ def ours(args, ws, rank, local):
             "peak": pk.get("smem_atomic_random_per_s"), "unit": "increments/s",
             "frac": (votes / pass_s / pk["smem_atomic_random_per_s"]) if "smem_atomic_random_per_s" in pk else None,
             "increments_per_launch": int(votes),
+            # the kernel issues one atomic per pair (pairs outside the box add to a sink word)
+            "issued_per_s": n_rot * len(p.X) * M / pass_s,
+            "issued_frac": (n_rot * len(p.X) * M / pass_s / pk["smem_atomic_random_per_s"])
+            if "smem_atomic_random_per_s" in pk else None,
             "peak_source": "measured in this run: red.shared.add on random bins of a 46,575-word histogram"},
         "peaks_measured": pk,
         "e2e": {"value": job_throughput(ws, args.steps, units, 1000 * e2e_tot), "unit": UNIT,

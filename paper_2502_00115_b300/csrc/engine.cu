@@ -359,7 +359,7 @@ struct Job {
   int64_t n_first = 0, n_fine = 0, n_total = 0;
   int hopf_n = 0;
   // plan
-  int u16 = 0, slab_x = 0, n_slabs = 1, hist_bytes = 0;
+  int u16 = 0, lanes = 0, slab_x = 0, n_slabs = 1, hist_bytes = 0;
   bool fused = false;
   bool sparse = false;
   // device scratch
@@ -500,6 +500,22 @@ void plan(dses_ctx* c, Job& j) {
   const int64_t bins = sx * Ey * Ez;
   const int64_t hb = u16 ? ((bins + 1) / 2) * 4 : bins * 4;
   j.hist_bytes = (int)((hb + 15) & ~15LL);
+  j.lanes = 0;
+  // Small boxes: one 32-bit copy of every bin per lane (word bin * 32 + lane,
+  // so a warp's increments never share a bank). Auto when the copies fit and a
+  // rotation's pair votes outnumber the words its scan reads 16 to 1.
+  const int64_t all = Ex * Ey * Ez;
+  const bool lanes_fit = all * 128 + 8 <= budget;
+  const bool lanes = c->opt.hist_mode == 3 ||
+                     (c->opt.hist_mode == 0 && lanes_fit && (int64_t)j.N * M >= 16 * 32 * all);
+  if (lanes) {
+    if (!lanes_fit) invalid("lane-private counters need 128 bytes per lattice bin within the histogram budget");
+    j.u16 = 0;
+    j.lanes = 1;
+    j.slab_x = (int)Ex;
+    j.n_slabs = 1;
+    j.hist_bytes = (int)(all * 128);
+  }
   j.fused = c->opt.fuse_score && j.q == 0 && j.topk == 0 && (j.metric == DSES_METRIC_INLIER || j.nn == DSES_NN_GRID);
   // Culling pays when the translation window (plus a target group's extent)
   // covers a small part of the target: estimated fraction of (source, group)
@@ -636,6 +652,7 @@ PassDesc make_desc(const Job& j, int P, bool second) {
   d.slab_x = j.slab_x;
   d.n_slabs = j.n_slabs;
   d.hist_u16 = j.u16;
+  d.hist_lanes = j.lanes;
   d.sparse = j.sparse ? 1 : 0;
   d.n_tchunks = (j.T->m + 32 * P - 1) / (32 * P);
   // dense: items a multiple of the 32 warps (equal work per item); sparse:
@@ -736,7 +753,8 @@ void launch_pass(dses_ctx* c, const std::vector<PassPart>& parts, int P) {
   }
   bool any_sparse = false;
   for (auto& pp : parts) any_sparse |= pp.job->sparse;
-  CK(launch_vote(L, any_sparse && P == 8 ? 4 : P, any_sparse, ctas, s));
+  if (any_sparse && P == 8) throw Error{DSES_ERR_CUDA, "internal: culled vote planned with 8 points per thread"};
+  CK(launch_vote(L, P, any_sparse, ctas, s));
   if (ev[0]) CK(cudaEventRecord(ev[1], s));
   CK(launch_count(L, (int)total_rot, s));
   if (ev[0]) {
@@ -846,13 +864,18 @@ void stage_finalize(dses_ctx* c, std::vector<Job*>& jobs) {
 // rotations (the trial only rewrites per-rotation values the pass rewrites
 // identically).
 int pick_p(dses_ctx* c, Job& j) {
-  if (c->opt.points_per_thread > 0) return (int)c->opt.points_per_thread;
+  // the culled vote has no 8-points-per-thread instance: the shape is settled
+  // here, before any descriptor is built for it
+  if (c->opt.points_per_thread > 0) {
+    const int P = (int)c->opt.points_per_thread;
+    return j.sparse && P == 8 ? 4 : P;
+  }
   std::vector<Job*> one{&j};
   if (!c->opt.autotune) return choose_p(c, one);
   auto lg = [](int64_t v) { int b = 0; while ((1LL << b) < v) ++b; return b; };
   char key[96];
-  snprintf(key, sizeof(key), "m%d n%d b%d s%d u%d", lg(j.T->m), lg(j.N), lg((int64_t)j.E[0] * j.E[1] * j.E[2]),
-           (int)j.sparse, j.u16);
+  snprintf(key, sizeof(key), "m%d n%d b%d s%d u%d l%d", lg(j.T->m), lg(j.N), lg((int64_t)j.E[0] * j.E[1] * j.E[2]),
+           (int)j.sparse, j.u16, j.lanes);
   auto it = c->tuned_p.find(key);
   if (it != c->tuned_p.end()) return it->second;
   if (c->capturing) return choose_p(c, one);
@@ -1809,7 +1832,8 @@ dses_status dses_set_option(dses_ctx* c, const char* key, int64_t value) {
     if (!slot) invalid(std::string("unknown option ") + (key ? key : "(null)"));
     const std::string k(key);
     bool ok = true;
-    if (k == "hist_mode" || k == "vote_sparse") ok = value >= 0 && value <= 2;
+    if (k == "hist_mode") ok = value >= 0 && value <= 3;
+    else if (k == "vote_sparse") ok = value >= 0 && value <= 2;
     else if (k == "hist_budget_bytes") ok = value >= 1024 && value <= kHistBudget;
     else if (k == "points_per_thread") ok = value == 0 || value == 1 || value == 2 || value == 4 || value == 8;
     else if (k == "fuse_score" || k == "autotune" || k == "use_graphs" || k == "record_timing")

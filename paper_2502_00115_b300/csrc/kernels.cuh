@@ -54,6 +54,7 @@ struct PassDesc {
   int slab_x;            // x-planes per histogram slab
   int n_slabs;
   int hist_u16;          // 1: two 16-bit counters per 32-bit word
+  int hist_lanes;        // 1: 32-bit counters, one copy per lane: word bin * 32 + lane
   int sparse;            // 1: cull (source, target group) pairs outside the window
   // vote work decomposition per rotation: items = n_tchunks x n_sgroups
   int n_tchunks;         // target chunks of 32 * P points

@@ -184,7 +184,10 @@ __device__ __forceinline__ void vote_centred(const PassDesc& d, const float4* __
               mz = kMagic + (float)((Ez - 1) / 2);
   // address = base + unit * (kx Eyz + ky Ez + kz), the kMagicBits offsets folded in
   const uint32_t bias = kMagicBits * (Eyz + Ez + 1u);
-  const uint32_t abase32 = hist_base - 4u * bias;
+  // 32-bit counters: word stride `unit` bytes (4, or 128 with a copy per lane)
+  const uint32_t unit = d.hist_lanes ? 128u : 4u;
+  const uint32_t EyzU = Eyz * unit, EzU = Ez * unit;
+  const uint32_t abase32 = hist_base + (d.hist_lanes ? 4u * (uint32_t)lane : 0u) - unit * bias;
   const uint32_t abase16 = hist_base - 2u * bias;
   for (int it = next_item(item_ctr, lane); it < n_items; it = next_item(item_ctr, lane)) {
     const int tc = it % n_tchunks, sg = it / n_tchunks;
@@ -208,7 +211,7 @@ __device__ __forceinline__ void vote_centred(const PassDesc& d, const float4* __
           const uint32_t inc = 1u + (b & 1u) * 0xffffu;
           red_if_inside(addr, inc, wx, wy, wz, hx, hy, hz);
         } else {
-          const uint32_t addr = abase32 + 4u * (bx * Eyz + (by * Ez + bz));
+          const uint32_t addr = abase32 + bx * EyzU + (by * EzU + bz * unit);
           red_if_inside(addr, 1u, wx, wy, wz, hx, hy, hz);
         }
       }
@@ -220,12 +223,15 @@ __device__ __forceinline__ void vote_centred(const PassDesc& d, const float4* __
 // lane's targets are held two by two per axis and each source offset is staged
 // duplicated, so one packed op computes the lattice coordinate (or its
 // rounding) of one source against two targets. Same per-pair arithmetic and
-// box test as vote_centred.
+// box test as vote_centred; the histogram increment is unconditional, with the
+// address selected by the box test (a pair outside the box adds to a per-lane
+// sink word that is never read), which keeps the loop free of branches around
+// the atomic.
 template <bool U16>
 __device__ __forceinline__ void vote_two_pairs(uint64_t yx, uint64_t yy, uint64_t yz, uint64_t inv2, uint64_t cx2,
                                                uint64_t cy2, uint64_t cz2, uint64_t mx2, uint64_t my2, uint64_t mz2,
                                                uint32_t Eyz, uint32_t Ez, uint32_t abase, float hx, float hy,
-                                               float hz, float hx1) {
+                                               float hz, float hx1, uint32_t adummy, uint32_t unit) {
   if (U16) {
     asm volatile(
         "{\n\t.reg .b64 wx, wy, wz, fx, fy, fz;\n\t"
@@ -247,9 +253,10 @@ __device__ __forceinline__ void vote_two_pairs(uint64_t yx, uint64_t yy, uint64_
         "abs.f32 z0, z0;\n\tabs.f32 z1, z1;\n\t"
         "setp.lt.f32 p0, x0, %13;\n\tsetp.lt.and.f32 p0, y0, %14, p0;\n\tsetp.lt.and.f32 p0, z0, %15, p0;\n\t"
         "setp.lt.f32 p1, x1, %16;\n\tsetp.lt.and.f32 p1, y1, %14, p1;\n\tsetp.lt.and.f32 p1, z1, %15, p1;\n\t"
-        "@p0 red.shared.add.u32 [a0], i0;\n\t@p1 red.shared.add.u32 [a1], i1;\n\t}" ::"l"(yx),
+        "selp.b32 a0, a0, %17, p0;\n\tselp.b32 a1, a1, %17, p1;\n\t"
+        "red.shared.add.u32 [a0], i0;\n\tred.shared.add.u32 [a1], i1;\n\t}" ::"l"(yx),
         "l"(yy), "l"(yz), "l"(inv2), "l"(cx2), "l"(cy2), "l"(cz2), "l"(mx2), "l"(my2), "l"(mz2), "r"(Eyz), "r"(Ez),
-        "r"(abase), "f"(hx), "f"(hy), "f"(hz), "f"(hx1));
+        "r"(abase), "f"(hx), "f"(hy), "f"(hz), "f"(hx1), "r"(adummy), "r"(unit));
   } else {
     asm volatile(
         "{\n\t.reg .b64 wx, wy, wz, fx, fy, fz;\n\t"
@@ -258,8 +265,8 @@ __device__ __forceinline__ void vote_two_pairs(uint64_t yx, uint64_t yy, uint64_
         "fma.rn.f32x2 wx, %0, %3, %4;\n\tfma.rn.f32x2 wy, %1, %3, %5;\n\tfma.rn.f32x2 wz, %2, %3, %6;\n\t"
         "add.rn.f32x2 fx, wx, %7;\n\tadd.rn.f32x2 fy, wy, %8;\n\tadd.rn.f32x2 fz, wz, %9;\n\t"
         "mov.b64 {bx0, bx1}, fx;\n\tmov.b64 {by0, by1}, fy;\n\tmov.b64 {bz0, bz1}, fz;\n\t"
-        "mad.lo.u32 t0, bz0, 4, %12;\n\tmad.lo.u32 t0, by0, %11, t0;\n\tmad.lo.u32 a0, bx0, %10, t0;\n\t"
-        "mad.lo.u32 t1, bz1, 4, %12;\n\tmad.lo.u32 t1, by1, %11, t1;\n\tmad.lo.u32 a1, bx1, %10, t1;\n\t"
+        "mad.lo.u32 t0, bz0, %18, %12;\n\tmad.lo.u32 t0, by0, %11, t0;\n\tmad.lo.u32 a0, bx0, %10, t0;\n\t"
+        "mad.lo.u32 t1, bz1, %18, %12;\n\tmad.lo.u32 t1, by1, %11, t1;\n\tmad.lo.u32 a1, bx1, %10, t1;\n\t"
         "mov.b64 {u0, u1}, wx;\n\tmov.b64 {v0, v1}, wy;\n\tmov.b64 {s0, s1}, wz;\n\t"
         "mov.b32 x0, u0;\n\tmov.b32 x1, u1;\n\tmov.b32 y0, v0;\n\tmov.b32 y1, v1;\n\t"
         "mov.b32 z0, s0;\n\tmov.b32 z1, s1;\n\t"
@@ -267,9 +274,10 @@ __device__ __forceinline__ void vote_two_pairs(uint64_t yx, uint64_t yy, uint64_
         "abs.f32 z0, z0;\n\tabs.f32 z1, z1;\n\t"
         "setp.lt.f32 p0, x0, %13;\n\tsetp.lt.and.f32 p0, y0, %14, p0;\n\tsetp.lt.and.f32 p0, z0, %15, p0;\n\t"
         "setp.lt.f32 p1, x1, %16;\n\tsetp.lt.and.f32 p1, y1, %14, p1;\n\tsetp.lt.and.f32 p1, z1, %15, p1;\n\t"
-        "@p0 red.shared.add.u32 [a0], 1;\n\t@p1 red.shared.add.u32 [a1], 1;\n\t}" ::"l"(yx),
-        "l"(yy), "l"(yz), "l"(inv2), "l"(cx2), "l"(cy2), "l"(cz2), "l"(mx2), "l"(my2), "l"(mz2), "r"(Eyz * 4u),
-        "r"(Ez * 4u), "r"(abase), "f"(hx), "f"(hy), "f"(hz), "f"(hx1));
+        "selp.b32 a0, a0, %17, p0;\n\tselp.b32 a1, a1, %17, p1;\n\t"
+        "red.shared.add.u32 [a0], 1;\n\tred.shared.add.u32 [a1], 1;\n\t}" ::"l"(yx),
+        "l"(yy), "l"(yz), "l"(inv2), "l"(cx2), "l"(cy2), "l"(cz2), "l"(mx2), "l"(my2), "l"(mz2), "r"(Eyz * unit),
+        "r"(Ez * unit), "r"(abase), "f"(hx), "f"(hy), "f"(hz), "f"(hx1), "r"(adummy), "r"(unit));
   }
 }
 
@@ -281,7 +289,8 @@ __device__ __forceinline__ uint64_t pack2(float lo, float hi) {
 // [2i + 1] holds (c_z, c_z, 0, 0).
 template <int P, bool U16>
 __device__ __forceinline__ void vote_centred_x2(const PassDesc& d, const float4* __restrict__ srcd, int nsrc,
-                                                unsigned SX, uint32_t hist_base, int* item_ctr, int lane) {
+                                                unsigned SX, uint32_t hist_base, int* item_ctr, int lane,
+                                                uint32_t sink) {
   static_assert(P % 2 == 0, "targets are packed two by two");
   const int n_tchunks = d.n_tchunks, n_sgroups = d.n_sgroups;
   const int n_items = n_tchunks * n_sgroups;
@@ -293,7 +302,13 @@ __device__ __forceinline__ void vote_centred_x2(const PassDesc& d, const float4*
               mz = kMagic + (float)((Ez - 1) / 2);
   const uint64_t inv2 = pack2(inv, inv), mx2 = pack2(mx, mx), my2 = pack2(my, my), mz2 = pack2(mz, mz);
   const uint32_t bias = kMagicBits * (Eyz + Ez + 1u);
-  const uint32_t abase = U16 ? hist_base - 2u * bias : hist_base - 4u * bias;
+  // 32-bit counters: word stride `unit` bytes (4, or 128 with a copy per lane)
+  const uint32_t unit = d.hist_lanes ? 128u : 4u;
+  const uint32_t abase = U16 ? hist_base - 2u * bias
+                             : hist_base + (d.hist_lanes ? 4u * (uint32_t)lane : 0u) - unit * bias;
+  // a pair outside the box adds to this lane's sink word outside the
+  // histogram instead (no branch, and the increment needs no select)
+  const uint32_t adummy = sink + 4u * (uint32_t)lane;
   for (int it = next_item(item_ctr, lane); it < n_items; it = next_item(item_ctr, lane)) {
     const int tc = it % n_tchunks, sg = it / n_tchunks;
     float ty[P][3];
@@ -314,7 +329,8 @@ __device__ __forceinline__ void vote_centred_x2(const PassDesc& d, const float4*
       const uint64_t cx2 = pack2(ca.x, ca.y), cy2 = pack2(ca.z, ca.w), cz2 = pack2(cb.x, cb.y);
 #pragma unroll
       for (int q = 0; q < P / 2; ++q)
-        vote_two_pairs<U16>(yx[q], yy[q], yz[q], inv2, cx2, cy2, cz2, mx2, my2, mz2, Eyz, Ez, abase, hx, hy, hz, hx);
+        vote_two_pairs<U16>(yx[q], yy[q], yz[q], inv2, cx2, cy2, cz2, mx2, my2, mz2, Eyz, Ez, abase, hx, hy, hz, hx,
+                            adummy, unit);
     }
   }
 }
@@ -341,7 +357,9 @@ __device__ __forceinline__ void vote_centred_sparse(const PassDesc& d, const flo
   const float mx = kMagic + (float)((SX - 1) / 2), my = kMagic + (float)((Ey - 1) / 2),
               mz = kMagic + (float)((Ez - 1) / 2);
   const uint32_t bias = kMagicBits * (Eyz + Ez + 1u);
-  const uint32_t abase32 = hist_base - 4u * bias;
+  const uint32_t unit = d.hist_lanes ? 128u : 4u;
+  const uint32_t EyzU = Eyz * unit, EzU = Ez * unit;
+  const uint32_t abase32 = hist_base + (d.hist_lanes ? 4u * (uint32_t)lane : 0u) - unit * bias;
   const uint32_t abase16 = hist_base - 2u * bias;
   for (int it = next_item(item_ctr, lane); it < n_items; it = next_item(item_ctr, lane)) {
     const int tc = it % n_tchunks, sg = it / n_tchunks;
@@ -393,7 +411,7 @@ __device__ __forceinline__ void vote_centred_sparse(const PassDesc& d, const flo
             const uint32_t b = bx * Eyz + (by * Ez + bz);
             red_if_inside(abase16 + ((b >> 1) << 2), 1u + (b & 1u) * 0xffffu, wx, wy, wz, hx, hy, hz);
           } else {
-            red_if_inside(abase32 + 4u * (bx * Eyz + (by * Ez + bz)), 1u, wx, wy, wz, hx, hy, hz);
+            red_if_inside(abase32 + bx * EyzU + (by * EzU + bz * unit), 1u, wx, wy, wz, hx, hy, hz);
           }
         }
       }
@@ -412,6 +430,7 @@ __device__ __forceinline__ void vote_generic(const PassDesc& d, const float4* __
   const int spg = (nsrc + n_sgroups - 1) / n_sgroups;
   const unsigned Ey = (unsigned)d.E[1], Ez = (unsigned)d.E[2];
   const float inv = d.inv_delta;
+  const unsigned bstride = d.hist_lanes ? 32u : 1u, boff = d.hist_lanes ? (unsigned)lane : 0u;
   for (int it = next_item(item_ctr, lane); it < n_items; it = next_item(item_ctr, lane)) {
     const int tc = it % n_tchunks, sg = it / n_tchunks;
     float ty[P][3];
@@ -429,7 +448,7 @@ __device__ __forceinline__ void vote_generic(const PassDesc& d, const float4* __
           if (U16)
             atomicAdd(&hist[bin >> 1], 1u << ((bin & 1u) << 4));
           else
-            atomicAdd(&hist[bin], 1u);
+            atomicAdd(&hist[bin * bstride + boff], 1u);
         }
       }
     }
@@ -444,6 +463,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
   __shared__ PassDesc sd;
   __shared__ unsigned long long red64[32];
   __shared__ int s_item, s_prob, s_vote_item;
+  __shared__ uint32_t s_sink[32];  // increments of out-of-box pairs (never read)
   __shared__ __align__(16) float s_thr[SPARSE ? 32 : 1][8 * 8];
 
   uint32_t* hist = reinterpret_cast<uint32_t*>(smem);
@@ -542,9 +562,11 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
             constexpr int PP = P >= 2 ? P : 2;  // the P = 1 instance never takes the packed path
             if (packed) {
               if (d.hist_u16)
-                vote_centred_x2<PP, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane);
+                vote_centred_x2<PP, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane,
+                                              (uint32_t)__cvta_generic_to_shared(s_sink));
               else
-                vote_centred_x2<PP, false>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane);
+                vote_centred_x2<PP, false>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane,
+                                               (uint32_t)__cvta_generic_to_shared(s_sink));
             } else if (d.hist_u16) {
               vote_centred<P, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane);
             } else {
@@ -561,7 +583,19 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
         // mode of this slab: scan and clear; each thread walks increasing bins
         const unsigned nbins = SX * Ey * Ez;
         unsigned bc = 0, bb = 0, vsum = 0;
-        if (d.hist_u16) {
+        if (d.hist_lanes) {
+          // a warp per bin: its 32 lane copies, summed across the warp (lane 0
+          // keeps the warp's first maximum, increasing bins)
+          for (unsigned b = warp; b < nbins; b += kPassThreads / 32) {
+            const uint32_t v = hist[b * 32u + lane];
+            hist[b * 32u + lane] = 0u;
+            const unsigned c = warp_sum_u32(v);
+            if (lane == 0) {
+              vsum += c;
+              if (c > bc) { bc = c; bb = b; }
+            }
+          }
+        } else if (d.hist_u16) {
           const unsigned words = (nbins + 1) >> 1;
           for (unsigned w = tid; w < words; w += kPassThreads) {
             const uint32_t v = hist[w];

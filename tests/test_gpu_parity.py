@@ -182,6 +182,59 @@ def test_histogram_modes_and_launch_shapes_agree(ctx):
     ctx.destroy_target(t)
 
 
+def test_small_box_lane_private_counters(ctx):
+    # a translation box of a few thousand bins (a local search around a prior):
+    # lane-private counters (auto here: the pair votes outnumber the scanned
+    # words) against the oracle on every rotation, and bit-identical to shared
+    # 32-bit counters under every vote path: packed (odd extents), scalar
+    # (1 point per lane), generic (an even extent) and culled
+    p = synth.modelnet_like_problem(7, hopf_n=2)
+    centre = tuple(float(v) for v in np.round(np.asarray(p.t_true) / 0.04) * 0.04)
+    t = ctx.create_target(p.Y, grid_cap=2 * p.tau)
+    # 11^3 bins; then the y range shifted by half a cell: 11 x 10 x 11 (an even extent)
+    for first, c in ((True, centre), (False, (centre[0], centre[1] + 0.02, centre[2]))):
+        gp = gpu_params(p, nn_mode="grid", t_center=c, t_half=(0.2, 0.2, 0.2))
+        pb = ctx.problem(t, p.X, capi.hopf_grid(2), gp)
+        n = 72 * 8
+        base = ctx.debug(pb, n)
+        if first:
+            P = oracle_params(p, gp, 2 * p.tau)
+            grid = oracle.hopf_grid(2)
+            g = oracle.dist_grid(p.Y, 128, P.grid_cap)
+            rep = check_rotations(p.X, p.Y, grid, P, base[0], base[1], base[2], base[3], range(0, n, 12),
+                                  dist_grid=g)
+            assert rep.ok(), rep.summary()
+        defaults = {k: ctx.get_option(k) for k in ("hist_mode", "points_per_thread", "vote_sparse")}
+        try:
+            for v in (dict(hist_mode=1), dict(hist_mode=3, points_per_thread=1), dict(hist_mode=3, points_per_thread=8),
+                      dict(hist_mode=3, vote_sparse=2), dict(hist_mode=1, vote_sparse=2)):
+                for key, val in v.items():
+                    ctx.set_option(key, val)
+                k, V, M, C, r = ctx.debug(pb, n)
+                assert np.array_equal(k, base[0]) and np.array_equal(V, base[1]) and np.array_equal(M, base[2]), v
+                np.testing.assert_allclose(C, base[3], rtol=2e-6, err_msg=str(v))
+                for key, val in defaults.items():
+                    ctx.set_option(key, val)
+        finally:
+            for key, val in defaults.items():
+                ctx.set_option(key, val)
+    ctx.destroy_target(t)
+
+
+def test_lane_private_counters_refused_when_they_do_not_fit(ctx):
+    p = synth.tiny_problem(2, hopf_n=1)
+    t = ctx.create_target(p.Y, grid_cap=2 * p.tau)
+    pb = ctx.problem(t, p.X, capi.hopf_grid(1), gpu_params(p, nn_mode="grid"))  # 91^3 bins
+    ctx.set_option("hist_mode", 3)
+    try:
+        st, _ = capi.dses_register(ctx.h, pb)
+        assert st == capi.DSES_ERR_INVALID_ARG
+    finally:
+        ctx.set_option("hist_mode", 0)
+    ctx.register(pb)  # the context stays usable
+    ctx.destroy_target(t)
+
+
 # ---------------------------------------------------------------------------
 # the full-size ModelNet-shaped problem (benchmark configuration), sampled
 
