@@ -360,6 +360,7 @@ struct Job {
   int hopf_n = 0;
   // plan
   int u16 = 0, lanes = 0, slab_x = 0, n_slabs = 1, hist_bytes = 0;
+  int Ep[3] = {0, 0, 0};  // vote layout extents: E padded to odd values
   bool fused = false;
   bool sparse = false;
   // device scratch
@@ -476,8 +477,26 @@ void resolve(dses_ctx* c, const dses_problem* pb, Job& j) {
   if (j.n_total >= (1LL << 31)) invalid("too many rotations");
 }
 
+// Histogram slabs over the x planes: (slab width, slab count, padded x extent)
+// such that every slab is an odd number of planes (the centred vote needs odd
+// extents); at most one padding plane is added.
+static void odd_slabs(int64_t Ex, int64_t max_planes, int64_t* sx, int64_t* n, int64_t* Exp) {
+  if (Ex + (Ex % 2 == 0 ? 1 : 0) <= max_planes) {
+    *sx = *Exp = Ex | 1;
+    *n = 1;
+    return;
+  }
+  int64_t w = max_planes % 2 == 0 ? max_planes - 1 : max_planes;
+  *sx = w;
+  *n = (Ex + w - 1) / w;
+  const int64_t last = Ex - (*n - 1) * w;
+  *Exp = Ex + (last % 2 == 0 ? 1 : 0);
+}
+
 void plan(dses_ctx* c, Job& j) {
-  const int64_t Ey = j.E[1], Ez = j.E[2], Ex = j.E[0];
+  // vote layout: the lattice box padded to odd extents (the centred vote
+  // paths need them); the scan of a padded layout skips the padding bins
+  const int64_t Ey = j.E[1] | 1, Ez = j.E[2] | 1, Ex = j.E[0];
   const int64_t budget = c->opt.hist_budget;
   const int64_t M = j.T->m;
   bool u16_ok = (int64_t)j.N * M <= 65535;
@@ -489,14 +508,18 @@ void plan(dses_ctx* c, Job& j) {
     if (!u16_ok) invalid("16-bit vote counters could overflow for this problem");
     u16 = true;
   } else {
-    u16 = (Ex * Ey * Ez * 4 > budget) && u16_ok;
+    u16 = ((Ex | 1) * Ey * Ez * 4 > budget) && u16_ok;
   }
   const int64_t per_plane = Ey * Ez * (u16 ? 2 : 4);
   if (per_plane + 8 > budget) invalid("translation box too large: one lattice plane exceeds the histogram budget");
-  int64_t sx = std::min<int64_t>(Ex, (budget - 8) / per_plane);
+  int64_t sx, ns, Exp;
+  odd_slabs(Ex, (budget - 8) / per_plane, &sx, &ns, &Exp);
   j.u16 = u16;
   j.slab_x = (int)sx;
-  j.n_slabs = (int)((Ex + sx - 1) / sx);
+  j.n_slabs = (int)ns;
+  j.Ep[0] = (int)Exp;
+  j.Ep[1] = (int)Ey;
+  j.Ep[2] = (int)Ez;
   const int64_t bins = sx * Ey * Ez;
   const int64_t hb = u16 ? ((bins + 1) / 2) * 4 : bins * 4;
   j.hist_bytes = (int)((hb + 15) & ~15LL);
@@ -504,7 +527,7 @@ void plan(dses_ctx* c, Job& j) {
   // Small boxes: one 32-bit copy of every bin per lane (word bin * 32 + lane,
   // so a warp's increments never share a bank). Auto when the copies fit and a
   // rotation's pair votes outnumber the words its scan reads 16 to 1.
-  const int64_t all = Ex * Ey * Ez;
+  const int64_t all = (Ex | 1) * Ey * Ez;
   const bool lanes_fit = all * 128 + 8 <= budget;
   const bool lanes = c->opt.hist_mode == 3 ||
                      (c->opt.hist_mode == 0 && lanes_fit && (int64_t)j.N * M >= 16 * 32 * all);
@@ -512,8 +535,9 @@ void plan(dses_ctx* c, Job& j) {
     if (!lanes_fit) invalid("lane-private counters need 128 bytes per lattice bin within the histogram budget");
     j.u16 = 0;
     j.lanes = 1;
-    j.slab_x = (int)Ex;
+    j.slab_x = (int)(Ex | 1);
     j.n_slabs = 1;
+    j.Ep[0] = (int)(Ex | 1);
     j.hist_bytes = (int)(all * 128);
   }
   j.fused = c->opt.fuse_score && j.q == 0 && j.topk == 0 && (j.metric == DSES_METRIC_INLIER || j.nn == DSES_NN_GRID);
@@ -647,7 +671,8 @@ PassDesc make_desc(const Job& j, int P, bool second) {
   d.delta = j.delta;
   for (int a = 0; a < 3; ++a) {
     d.lo[a] = j.lo[a];
-    d.E[a] = j.E[a];
+    d.E[a] = j.Ep[a];
+    d.Ev[a] = j.E[a];
   }
   d.slab_x = j.slab_x;
   d.n_slabs = j.n_slabs;
@@ -745,6 +770,9 @@ void launch_pass(dses_ctx* c, const std::vector<PassPart>& parts, int P) {
   L.tile_rot = tile;
   L.work_counter = (int*)(base + db + 2 * pb);
   L.hist_bytes = hist;
+  L.padded = 0;
+  for (auto& pp : parts)
+    for (int a = 0; a < 3; ++a) L.padded |= pp.job->Ep[a] != pp.job->E[a] ? 1 : 0;
   const int ctas = std::max(1, std::min(c->sms, prefix.back()));
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   if (c->opt.record_timing && !c->capturing) {
@@ -905,6 +933,8 @@ int pick_p(dses_ctx* c, Job& j) {
     L.tile_rot = tile;
     L.work_counter = (int*)(base + 3072);
     L.hist_bytes = j.hist_bytes;
+    L.padded = 0;
+    for (int a = 0; a < 3; ++a) L.padded |= j.Ep[a] != j.E[a] ? 1 : 0;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));

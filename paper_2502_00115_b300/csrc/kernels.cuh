@@ -50,7 +50,8 @@ struct PassDesc {
   // translation lattice (Lemma 1 discretised): k = floor((y - R x)/delta + 1/2)
   float inv_delta, delta;
   int lo[3];             // lattice box lower corner
-  int E[3];              // lattice box extent per axis
+  int E[3];              // histogram layout extent per axis (odd; >= Ev)
+  int Ev[3];             // lattice box extent per axis (bins beyond it are padding)
   int slab_x;            // x-planes per histogram slab
   int n_slabs;
   int hist_u16;          // 1: two 16-bit counters per 32-bit word
@@ -92,6 +93,8 @@ struct PassLaunch {
   int tile_rot;            // rotations per work item
   int* work_counter;       // device, zeroed before the launch
   int hist_bytes;          // histogram bytes of shared memory (max over problems)
+  int padded;              // 1: some problem's layout is padded (E != Ev): the
+                           // instance whose mode scan skips padding bins
 };
 
 // Hot path, kernel 1: vote -> mode (k*, V) per rotation (persistent, one CTA per SM).

@@ -144,6 +144,7 @@ extern "C" dses_status dses_vote_static(int device, void* cuda_stream, const flo
     for (int a = 0; a < 3; ++a) {
       d.lo[a] = lo[a];
       d.E[a] = E[a];
+      d.Ev[a] = E[a];
     }
     d.slab_x = sx;
     d.n_slabs = (E[0] + sx - 1) / sx;
@@ -169,6 +170,7 @@ extern "C" dses_status dses_vote_static(int device, void* cuda_stream, const flo
     L.tile_rot = tile;
     L.work_counter = reinterpret_cast<int*>(base + kOffCounter);
     L.hist_bytes = hist_bytes;
+    L.padded = 0;
     if (launch_vote(L, ppt, false, std::max(1, std::min(sms, tiles)), s) != cudaSuccess) {
       cudaGetLastError();
       st = DSES_ERR_CUDA;

@@ -457,7 +457,7 @@ __device__ __forceinline__ void vote_generic(const PassDesc& d, const float4* __
 
 // SPARSE: this instance also carries the culled path (problems with
 // d.sparse); the dense instance leaves it out so it keeps its registers.
-template <int P, bool SPARSE>
+template <int P, bool SPARSE, bool PADDED>
 __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ PassDesc sd;
@@ -583,7 +583,39 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
         // mode of this slab: scan and clear; each thread walks increasing bins
         const unsigned nbins = SX * Ey * Ez;
         unsigned bc = 0, bb = 0, vsum = 0;
-        if (d.hist_lanes) {
+        // (only PADDED instances carry the padded scan: the others keep the
+        // hot loop's code generation of a kernel without it)
+        const bool padded = PADDED && (d.Ev[0] != d.E[0] || d.Ev[1] != d.E[1] || d.Ev[2] != d.E[2]);
+        if (padded) {
+          // layout padded to odd extents: read the lattice box's bins only, a
+          // warp per (x, y) row of the slab (each thread's bins increase),
+          // then clear the whole slab
+          const unsigned Eyv = (unsigned)d.Ev[1], Ezv = (unsigned)d.Ev[2];
+          const unsigned rows = (unsigned)max(0, min((int)SX, d.Ev[0] - x0)) * Eyv;
+          for (unsigned row = warp; row < rows; row += kPassThreads / 32) {
+            const unsigned x = row / Eyv;
+            const unsigned base = (x * Ey + (row - x * Eyv)) * Ez;
+            if (d.hist_lanes) {
+              for (unsigned z = 0; z < Ezv; ++z) {
+                const unsigned c = warp_sum_u32(hist[(base + z) * 32u + lane]);
+                if (lane == 0) {
+                  vsum += c;
+                  if (c > bc) { bc = c; bb = base + z; }
+                }
+              }
+            } else {
+              for (unsigned z = lane; z < Ezv; z += 32) {
+                const unsigned b = base + z;
+                const unsigned c = d.hist_u16 ? (hist[b >> 1] >> ((b & 1u) << 4)) & 0xffffu : hist[b];
+                vsum += c;
+                if (c > bc) { bc = c; bb = b; }
+              }
+            }
+          }
+          __syncthreads();
+          const unsigned words = d.hist_lanes ? nbins * 32u : (d.hist_u16 ? (nbins + 1) >> 1 : nbins);
+          for (unsigned w = tid; w < words; w += kPassThreads) hist[w] = 0u;
+        } else if (d.hist_lanes) {
           // a warp per bin: its 32 lane copies, summed across the warp (lane 0
           // keeps the warp's first maximum, increasing bins)
           for (unsigned b = warp; b < nbins; b += kPassThreads / 32) {
@@ -703,19 +735,39 @@ __global__ void __launch_bounds__(256) count_kernel(PassLaunch L) {
   }
 }
 
-template <int P, bool SPARSE>
+template <int P, bool SPARSE, bool PADDED>
 cudaError_t launch_vote_p(const PassLaunch& L, int grid_ctas, cudaStream_t s) {
   const int smem = pass_smem_bytes(L.hist_bytes);
   static int configured = 0;
   if (configured < smem) {
     cudaError_t e =
-        cudaFuncSetAttribute(vote_kernel<P, SPARSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(vote_kernel<P, SPARSE, PADDED>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     configured = smem;
   }
   g_launches.fetch_add(1, std::memory_order_relaxed);
-  vote_kernel<P, SPARSE><<<grid_ctas, kPassThreads, smem, s>>>(L);
+  vote_kernel<P, SPARSE, PADDED><<<grid_ctas, kPassThreads, smem, s>>>(L);
   return cudaGetLastError();
+}
+
+template <bool PADDED>
+cudaError_t launch_vote_padded(const PassLaunch& L, int points_per_thread, bool sparse, int grid_ctas,
+                               cudaStream_t s) {
+  if (sparse) {
+    switch (points_per_thread) {
+      case 1: return launch_vote_p<1, true, PADDED>(L, grid_ctas, s);
+      case 2: return launch_vote_p<2, true, PADDED>(L, grid_ctas, s);
+      case 4: return launch_vote_p<4, true, PADDED>(L, grid_ctas, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  switch (points_per_thread) {
+    case 1: return launch_vote_p<1, false, PADDED>(L, grid_ctas, s);
+    case 2: return launch_vote_p<2, false, PADDED>(L, grid_ctas, s);
+    case 4: return launch_vote_p<4, false, PADDED>(L, grid_ctas, s);
+    case 8: return launch_vote_p<8, false, PADDED>(L, grid_ctas, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
@@ -723,21 +775,8 @@ cudaError_t launch_vote_p(const PassLaunch& L, int grid_ctas, cudaStream_t s) {
 int pass_smem_bytes(int hist_bytes) { return hist_bytes + kSrcChunk * (int)sizeof(float4); }
 
 cudaError_t launch_vote(const PassLaunch& L, int points_per_thread, bool sparse, int grid_ctas, cudaStream_t s) {
-  if (sparse) {
-    switch (points_per_thread) {
-      case 1: return launch_vote_p<1, true>(L, grid_ctas, s);
-      case 2: return launch_vote_p<2, true>(L, grid_ctas, s);
-      case 4: return launch_vote_p<4, true>(L, grid_ctas, s);
-      default: return cudaErrorInvalidValue;
-    }
-  }
-  switch (points_per_thread) {
-    case 1: return launch_vote_p<1, false>(L, grid_ctas, s);
-    case 2: return launch_vote_p<2, false>(L, grid_ctas, s);
-    case 4: return launch_vote_p<4, false>(L, grid_ctas, s);
-    case 8: return launch_vote_p<8, false>(L, grid_ctas, s);
-    default: return cudaErrorInvalidValue;
-  }
+  return L.padded ? launch_vote_padded<true>(L, points_per_thread, sparse, grid_ctas, s)
+                  : launch_vote_padded<false>(L, points_per_thread, sparse, grid_ctas, s);
 }
 
 cudaError_t launch_count(const PassLaunch& L, int total_rot, cudaStream_t s) {

@@ -221,6 +221,32 @@ def test_small_box_lane_private_counters(ctx):
     ctx.destroy_target(t)
 
 
+@pytest.mark.parametrize("hist_mode", [0, 1])
+def test_even_extent_box_matches_oracle(ctx, hist_mode):
+    # a box centred half a cell off the lattice has even extents (90 x 89 x 90
+    # here); the vote layout is padded to odd extents and the scan skips the
+    # padding: every rotation against the oracle, packed 16-bit and 32-bit slabs
+    p = synth.tiny_problem(3)
+    t = ctx.create_target(p.Y, grid_cap=2 * p.tau)
+    gp = gpu_params(p, nn_mode="grid", t_center=(0.01, 0.0, -0.01))
+    pb = ctx.problem(t, p.X, capi.hopf_grid(p.hopf_n), gp)
+    P = oracle_params(p, gp, 2 * p.tau)
+    lo, hi = oracle.lattice_box(P.t_center[:], P.t_half[:], P.delta_t)
+    assert ((hi - lo + 1) % 2 == 0).sum() == 2
+    ctx.set_option("hist_mode", hist_mode)
+    try:
+        k, V, M, C, r = ctx.debug(pb, 72 * p.hopf_n**3)
+    finally:
+        ctx.set_option("hist_mode", 0)
+    grid = oracle.hopf_grid(p.hopf_n)
+    ref = oracle.register(p.X, p.Y, grid, P)
+    g = oracle.dist_grid(p.Y, 128, P.grid_cap)
+    rep = check_rotations(p.X, p.Y, grid, P, k, V, M, C, range(len(grid)), ref=ref, dist_grid=g)
+    assert rep.ok(), rep.summary()
+    assert rep.vote_exact >= 0.98 * rep.checked, rep.summary()
+    ctx.destroy_target(t)
+
+
 def test_lane_private_counters_refused_when_they_do_not_fit(ctx):
     p = synth.tiny_problem(2, hopf_n=1)
     t = ctx.create_target(p.Y, grid_cap=2 * p.tau)
