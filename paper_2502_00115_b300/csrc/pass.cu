@@ -131,18 +131,21 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
   return v;
 }
 
-// Shared-memory histogram increment, predicated (no branch) on the pair lying
-// inside the centred box: |w_a| < h_a on all three axes.
-__device__ __forceinline__ void red_if_inside(uint32_t addr, uint32_t inc, float wx, float wy, float wz, float hx,
-                                              float hy, float hz) {
+// Shared-memory histogram increment of a pair whose box-relative lattice
+// coordinates are w (inside the centred box iff |w_a| < h_a on all three axes),
+// made unconditional: a pair outside the box adds to `sink` (a word outside
+// the histogram) instead, so no branch wraps the atomic.
+__device__ __forceinline__ void red_or_sink(uint32_t addr, uint32_t inc, uint32_t sink, float wx, float wy,
+                                            float wz, float hx, float hy, float hz) {
   asm volatile(
-      "{\n\t.reg .pred p;\n\t.reg .f32 ax, ay, az;\n\t"
-      "abs.f32 ax, %2;\n\tabs.f32 ay, %3;\n\tabs.f32 az, %4;\n\t"
-      "setp.lt.f32 p, ax, %5;\n\t"
-      "setp.lt.and.f32 p, ay, %6, p;\n\t"
-      "setp.lt.and.f32 p, az, %7, p;\n\t"
-      "@p red.shared.add.u32 [%0], %1;\n\t}" ::"r"(addr),
-      "r"(inc), "f"(wx), "f"(wy), "f"(wz), "f"(hx), "f"(hy), "f"(hz));
+      "{\n\t.reg .pred p;\n\t.reg .f32 ax, ay, az;\n\t.reg .b32 a;\n\t"
+      "abs.f32 ax, %3;\n\tabs.f32 ay, %4;\n\tabs.f32 az, %5;\n\t"
+      "setp.lt.f32 p, ax, %6;\n\t"
+      "setp.lt.and.f32 p, ay, %7, p;\n\t"
+      "setp.lt.and.f32 p, az, %8, p;\n\t"
+      "selp.b32 a, %0, %2, p;\n\t"
+      "red.shared.add.u32 [a], %1;\n\t}" ::"r"(addr),
+      "r"(inc), "r"(sink), "f"(wx), "f"(wy), "f"(wz), "f"(hx), "f"(hy), "f"(hz));
 }
 
 // Next vote item of this CTA (dynamic balance across warps).
@@ -173,7 +176,8 @@ __device__ __forceinline__ void load_targets(const float4* __restrict__ Y, int M
 // then three multiply-adds of those bit patterns.
 template <int P, bool U16>
 __device__ __forceinline__ void vote_centred(const PassDesc& d, const float4* __restrict__ srcc, int nsrc,
-                                             unsigned SX, uint32_t hist_base, int* item_ctr, int lane) {
+                                             unsigned SX, uint32_t hist_base, int* item_ctr, int lane,
+                                             uint32_t sink) {
   const int n_tchunks = d.n_tchunks, n_sgroups = d.n_sgroups;
   const int n_items = n_tchunks * n_sgroups;
   const int spg = (nsrc + n_sgroups - 1) / n_sgroups;
@@ -189,6 +193,7 @@ __device__ __forceinline__ void vote_centred(const PassDesc& d, const float4* __
   const uint32_t EyzU = Eyz * unit, EzU = Ez * unit;
   const uint32_t abase32 = hist_base + (d.hist_lanes ? 4u * (uint32_t)lane : 0u) - unit * bias;
   const uint32_t abase16 = hist_base - 2u * bias;
+  const uint32_t sinkl = sink + 4u * (uint32_t)lane;
   for (int it = next_item(item_ctr, lane); it < n_items; it = next_item(item_ctr, lane)) {
     const int tc = it % n_tchunks, sg = it / n_tchunks;
     float ty[P][3];
@@ -209,10 +214,10 @@ __device__ __forceinline__ void vote_centred(const PassDesc& d, const float4* __
           const uint32_t b = bx * Eyz + (by * Ez + bz);  // bin + bias (bias even)
           const uint32_t addr = abase16 + ((b >> 1) << 2);
           const uint32_t inc = 1u + (b & 1u) * 0xffffu;
-          red_if_inside(addr, inc, wx, wy, wz, hx, hy, hz);
+          red_or_sink(addr, inc, sinkl, wx, wy, wz, hx, hy, hz);
         } else {
           const uint32_t addr = abase32 + bx * EyzU + (by * EzU + bz * unit);
-          red_if_inside(addr, 1u, wx, wy, wz, hx, hy, hz);
+          red_or_sink(addr, 1u, sinkl, wx, wy, wz, hx, hy, hz);
         }
       }
     }
@@ -347,7 +352,7 @@ constexpr float kCullMargin = 1e-3f;
 template <int P, bool U16>
 __device__ __forceinline__ void vote_centred_sparse(const PassDesc& d, const float4* __restrict__ srcc, int nsrc,
                                                     unsigned SX, uint32_t hist_base, int* item_ctr, int lane,
-                                                    float* __restrict__ thr) {
+                                                    float* __restrict__ thr, uint32_t sink) {
   const int n_tchunks = d.n_tchunks, n_sgroups = d.n_sgroups;
   const int n_items = n_tchunks * n_sgroups;
   const int spg = (nsrc + n_sgroups - 1) / n_sgroups;
@@ -361,6 +366,7 @@ __device__ __forceinline__ void vote_centred_sparse(const PassDesc& d, const flo
   const uint32_t EyzU = Eyz * unit, EzU = Ez * unit;
   const uint32_t abase32 = hist_base + (d.hist_lanes ? 4u * (uint32_t)lane : 0u) - unit * bias;
   const uint32_t abase16 = hist_base - 2u * bias;
+  const uint32_t sinkl = sink + 4u * (uint32_t)lane;
   for (int it = next_item(item_ctr, lane); it < n_items; it = next_item(item_ctr, lane)) {
     const int tc = it % n_tchunks, sg = it / n_tchunks;
     float ty[P][3];
@@ -409,9 +415,9 @@ __device__ __forceinline__ void vote_centred_sparse(const PassDesc& d, const flo
           const uint32_t bz = __float_as_uint(__fadd_rn(wz, mz));
           if (U16) {
             const uint32_t b = bx * Eyz + (by * Ez + bz);
-            red_if_inside(abase16 + ((b >> 1) << 2), 1u + (b & 1u) * 0xffffu, wx, wy, wz, hx, hy, hz);
+            red_or_sink(abase16 + ((b >> 1) << 2), 1u + (b & 1u) * 0xffffu, sinkl, wx, wy, wz, hx, hy, hz);
           } else {
-            red_if_inside(abase32 + bx * EyzU + (by * EzU + bz * unit), 1u, wx, wy, wz, hx, hy, hz);
+            red_or_sink(abase32 + bx * EyzU + (by * EzU + bz * unit), 1u, sinkl, wx, wy, wz, hx, hy, hz);
           }
         }
       }
@@ -554,10 +560,10 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
           if (SPARSE && centred && d.sparse) {
             if (d.hist_u16)
               vote_centred_sparse<P, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane,
-                                           s_thr[SPARSE ? warp : 0]);
+                                           s_thr[SPARSE ? warp : 0], (uint32_t)__cvta_generic_to_shared(s_sink));
             else
               vote_centred_sparse<P, false>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane,
-                                            s_thr[SPARSE ? warp : 0]);
+                                            s_thr[SPARSE ? warp : 0], (uint32_t)__cvta_generic_to_shared(s_sink));
           } else if (centred) {
             constexpr int PP = P >= 2 ? P : 2;  // the P = 1 instance never takes the packed path
             if (packed) {
@@ -568,9 +574,11 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
                 vote_centred_x2<PP, false>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane,
                                                (uint32_t)__cvta_generic_to_shared(s_sink));
             } else if (d.hist_u16) {
-              vote_centred<P, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane);
+              vote_centred<P, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane,
+                                    (uint32_t)__cvta_generic_to_shared(s_sink));
             } else {
-              vote_centred<P, false>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane);
+              vote_centred<P, false>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane,
+                                     (uint32_t)__cvta_generic_to_shared(s_sink));
             }
           } else {
             if (d.hist_u16)
