@@ -451,13 +451,29 @@ def serving(args, ws, rank, local):
                 units += u
         time.sleep(0.0005)
     wall = time.perf_counter() - t0
+    # the same requests as sequential single-problem launches (blocking
+    # dses_register one after another): measured service times, and the
+    # latencies of a first-come first-served queue with the same arrivals
+    svc = []
+    for (_, pb, _) in reqs:
+        t1 = time.perf_counter()
+        ctx.register(pb)
+        svc.append(time.perf_counter() - t1)
     ctx.close()
+    finish, seq_lat = 0.0, []
+    for (t_arr, _, _), sv in zip(reqs, svc):
+        finish = max(finish, t_arr) + sv
+        seq_lat.append(finish - t_arr)
     print(json.dumps({
         "workload": "serving", "metric": METRIC, "value": units / wall, "unit": UNIT,
         "offered_rate": args.rate, "requests": len(reqs), "registrations_per_s": len(reqs) / wall,
         "latency_ms": {"p50": 1000 * float(np.percentile(lat, 50)), "p99": 1000 * float(np.percentile(lat, 99)),
                        "max": 1000 * max(lat)},
         "wall_s": wall, "arrival_window_s": args.duration,
+        "sequential": {"registrations_per_s": len(reqs) / max(finish, sum(svc)),
+                       "service_ms_mean": 1000 * statistics.mean(svc),
+                       "latency_ms": {"p50": 1000 * float(np.percentile(seq_lat, 50)),
+                                      "p99": 1000 * float(np.percentile(seq_lat, 99))}},
     }), flush=True)
 
 

@@ -180,7 +180,7 @@ struct dses_ctx {
   int64_t vote_sparse_jobs = 0;  // problems of the last blocking call on the culled vote
   int64_t graph_count = 0;       // snapshot for the "graphs_cached" option
   // host staging: blocking calls, the serving worker, and the one in use
-  Stage stage, serve_stage;
+  Stage stage, serve_stage[2];  // the serving worker alternates two (two iterations in flight)
   Stage* cur_stage = nullptr;
   bool capturing = false;
   // captured batch graphs by problem signature
@@ -721,7 +721,9 @@ PassDesc make_desc(const Job& j, int P, bool second) {
 // keep the work counter cold.
 int tile_rotations(dses_ctx* c, int64_t total_rot) {
   if (c->opt.tile_rotations > 0) return (int)c->opt.tile_rotations;
-  const int64_t t = total_rot / ((int64_t)c->sms * 8);
+  // at least ~32 tiles per SM, so the launch's tail (SMs idle while the last
+  // tiles finish) stays a few percent of the launch; at most 16 rotations
+  const int64_t t = total_rot / ((int64_t)c->sms * 32);
   return (int)std::max<int64_t>(1, std::min<int64_t>(16, t));
 }
 
@@ -1015,11 +1017,55 @@ void worker_loop(dses_ctx* c) {
   cudaSetDevice(c->device);
   std::vector<std::shared_ptr<Request>> active;
   size_t mem_used = 0;
+  // Iterations in flight (at most two): the host admits requests and builds and
+  // launches the next iteration while the device runs the current one. Each
+  // iteration records an event; once it has completed, the requests that
+  // finished in it are retired. Iterations alternate between two pinned stages,
+  // so a stage is refilled only after the iteration that read it has completed.
+  struct Flight {
+    cudaEvent_t ev = nullptr;
+    std::vector<std::shared_ptr<Request>> done;
+  };
+  std::deque<Flight> flights;
+  int cur = 0;
+  auto release = [&](const std::shared_ptr<Request>& r) {
+    mem_used -= std::min(mem_used, job_bytes(r->job));
+    {
+      std::lock_guard<std::recursive_mutex> g(c->mu);
+      r->job.mem.release();  // stream-ordered: after the work already queued
+    }
+    r->job.T->inflight--;
+    r->state = 2;  // visible to dses_poll only now
+  };
+  auto retire_oldest = [&]() {
+    Flight f = flights.front();
+    flights.pop_front();
+    const cudaError_t e = cudaEventSynchronize(f.ev);
+    cudaEventDestroy(f.ev);
+    for (auto& r : f.done) {
+      if (e != cudaSuccess) {
+        fail_request(*r, Error{DSES_ERR_CUDA, std::string("serving iteration: ") + cudaGetErrorString(e)});
+      } else {
+        r->result = *r->host_res;
+        r->status = (dses_status)r->result.status;
+      }
+      release(r);
+      const auto it = std::find(active.begin(), active.end(), r);
+      if (it != active.end()) active.erase(it);
+    }
+  };
+  auto schedulable = [&]() {
+    for (auto& r : active) {
+      const int st = r->state.load();
+      if (st == 0 || (st == 1 && r->next < r->job.n_first)) return true;
+    }
+    return false;
+  };
   for (;;) {
     {
       std::unique_lock<std::mutex> lk(c->smu);
-      if (active.empty()) c->scv.wait(lk, [&] { return c->stop || !c->queue.empty(); });
-      if (c->stop && active.empty()) return;
+      if (active.empty() && flights.empty()) c->scv.wait(lk, [&] { return c->stop || !c->queue.empty(); });
+      if (c->stop && active.empty() && flights.empty()) return;
       // admission: batch slots and device-memory budget
       while (!c->queue.empty() && (int64_t)active.size() < c->opt.serve_max_batch) {
         auto r = c->queue.front();
@@ -1031,22 +1077,24 @@ void worker_loop(dses_ctx* c) {
         active.push_back(r);
       }
     }
-    bool launched = false;
-    {
+    if (schedulable()) {
       std::lock_guard<std::recursive_mutex> g(c->mu);
+      Flight f;
+      bool launched = false;
       {
         std::vector<Job*> all;
         for (auto& r : active) all.push_back(&r->job);
-        c->cur_stage = &c->serve_stage;
+        c->cur_stage = &c->serve_stage[cur];
         try {
-          c->serve_stage.reserve(2 * stage_bytes(all));
+          c->serve_stage[cur].reserve(2 * stage_bytes(all));
         } catch (const Error& e) {
-          for (auto& r : active) {
-            fail_request(*r, e);
-            r->state = 2;
-          }
+          for (auto& r : active)
+            if (r->state.load() < 2) {
+              fail_request(*r, e);
+              r->state = 4;  // failed, to be released below
+            }
         }
-        c->serve_stage.used = 0;
+        c->serve_stage[cur].used = 0;
       }
       // set up newly admitted requests
       for (auto& r : active) {
@@ -1056,93 +1104,83 @@ void worker_loop(dses_ctx* c) {
           r->state = 1;
         } catch (const Error& e) {
           fail_request(*r, e);
-          r->state = 2;
+          r->state = 4;
         }
       }
       // one iteration: requests in admission order take rotations until the
       // iteration's pair-vote budget is spent (the oldest request finishes
-      // first; the next one starts in the same launch when budget is left)
-      std::vector<PassPart> parts;
-      std::vector<Job*> jobs;
+      // first; the next one starts in the same iteration when budget is left);
+      // one launch per points-per-thread shape
+      std::map<int, std::vector<PassPart>> parts;
       const int64_t slice = std::max<int64_t>(1, c->opt.serve_tile_rotations);
       double budget = (double)c->opt.serve_iter_pairs;
-      for (auto& r : active) {
-        if (r->state.load() != 1) continue;
-        if (budget <= 0) break;
-        const double per_rot = (double)r->job.N * (double)r->job.T->m;
-        const int64_t want = std::max<int64_t>(1, (int64_t)(budget / per_rot));
-        const int64_t a = r->next, b = std::min({r->job.n_first, a + slice, a + want});
-        parts.push_back({&r->job, false, a, b});
-        jobs.push_back(&r->job);
-        r->next = b;
-        budget -= (double)(b - a) * per_rot;
-      }
       try {
-        if (!parts.empty()) launch_pass(c, parts, choose_p(c, jobs));
+        for (auto& r : active) {
+          if (r->state.load() != 1 || r->next >= r->job.n_first) continue;
+          if (budget <= 0) break;
+          const double per_rot = (double)r->job.N * (double)r->job.T->m;
+          const int64_t want = std::max<int64_t>(1, (int64_t)(budget / per_rot));
+          const int64_t a0 = r->next, b0 = std::min({r->job.n_first, a0 + slice, a0 + want});
+          parts[pick_p(c, r->job)].push_back({&r->job, false, a0, b0});
+          r->next = b0;
+          budget -= (double)(b0 - a0) * per_rot;
+        }
+        for (auto& kv : parts) launch_pass(c, kv.second, kv.first);
         std::vector<Job*> fin;
-        std::vector<PassPart> fine;
+        std::map<int, std::vector<PassPart>> fine;
         for (auto& r : active) {
           if (r->state.load() != 1 || r->next < r->job.n_first) continue;
           stage_candidates(c, r->job, false);
           if (r->job.rtop > 0) {
             stage_refine_grid(c, r->job);
-            fine.push_back({&r->job, true, 0, r->job.n_fine});
+            fine[pick_p(c, r->job)].push_back({&r->job, true, 0, r->job.n_fine});
           }
           fin.push_back(&r->job);
         }
-        if (!fine.empty()) {
-          std::vector<Job*> fj;
-          for (auto& f : fine) fj.push_back(f.job);
-          launch_pass(c, fine, choose_p(c, fj));
-          for (auto* j : fj) stage_candidates(c, *j, true);
+        for (auto& kv : fine) {
+          launch_pass(c, kv.second, kv.first);
+          for (auto& pp : kv.second) stage_candidates(c, *pp.job, true);
         }
         if (!fin.empty()) stage_finalize(c, fin);
         for (auto& r : active) {
           if (r->state.load() != 1 || r->next < r->job.n_first) continue;
           CK(cudaMemcpyAsync(r->host_res, r->job.res, sizeof(dses_result), cudaMemcpyDeviceToHost, c->stream));
           r->state = 3;  // finishing on the device
+          f.done.push_back(r);
         }
+        CK(cudaEventCreateWithFlags(&f.ev, cudaEventDisableTiming));
+        CK(cudaEventRecord(f.ev, c->stream));
         launched = true;
       } catch (const Error& e) {
+        if (f.ev) cudaEventDestroy(f.ev);
+        f.ev = nullptr;
+        // the stream may hold this iteration's work: let it drain first
+        cudaStreamSynchronize(c->stream);
+        cudaGetLastError();
         for (auto& r : active)
           if (r->state.load() == 1 || r->state.load() == 3) {
             fail_request(*r, e);
-            r->state = 2;
+            r->state = 4;
           }
       }
-    }
-    if (launched) {
-      const cudaError_t e = cudaStreamSynchronize(c->stream);
-      if (e != cudaSuccess) {
-        const Error err{DSES_ERR_CUDA, std::string("serving iteration: ") + cudaGetErrorString(e)};
-        for (auto& r : active)
-          if (r->state.load() == 1 || r->state.load() == 3) {
-            fail_request(*r, err);
-            r->state = 2;
-          }
+      if (launched) {
+        flights.push_back(f);
+        cur ^= 1;
       }
-    }
-    // retire finished requests
-    std::vector<std::shared_ptr<Request>> keep;
-    for (auto& r : active) {
-      const int st = r->state.load();
-      if (st == 3) {
-        r->result = *r->host_res;
-        r->status = (dses_status)r->result.status;
-      }
-      if (st == 2 || st == 3) {
-        mem_used -= std::min(mem_used, job_bytes(r->job));
-        {
-          std::lock_guard<std::recursive_mutex> g(c->mu);
-          r->job.mem.release();
+      // release requests that failed in this iteration
+      for (size_t i = 0; i < active.size();) {
+        if (active[i]->state.load() == 4) {
+          auto r = active[i];
+          release(r);
+          for (auto& fl : flights) fl.done.erase(std::remove(fl.done.begin(), fl.done.end(), r), fl.done.end());
+          active.erase(active.begin() + (long)i);
+        } else {
+          ++i;
         }
-        r->job.T->inflight--;
-        r->state = 2;  // visible to dses_poll only now
-      } else {
-        keep.push_back(r);
       }
     }
-    active.swap(keep);
+    // retire: keep at most two iterations in flight; drain when nothing is left to launch
+    if (!flights.empty() && (flights.size() >= 2 || !schedulable())) retire_oldest();
   }
 }
 
@@ -1389,7 +1427,8 @@ dses_status dses_destroy(dses_ctx* c) {
   if (c->pinned_res) cudaFreeHost(c->pinned_res);
   for (auto& g : c->graphs) free_graph(g.second);
   c->stage.release();
-  c->serve_stage.release();
+  c->serve_stage[0].release();
+  c->serve_stage[1].release();
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
   return DSES_OK;

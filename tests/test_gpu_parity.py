@@ -553,6 +553,45 @@ def test_forced_16bit_counters_refused_when_they_could_overflow(ctx):
 # serving: results alone and in the mix
 
 
+def test_serving_staggered_arrivals_with_second_pass_equal_solo(ctx):
+    # requests arriving while others run, split over several iterations (two
+    # in flight), some with the Euler-box second pass: each result equals the
+    # blocking call's
+    import time
+
+    probs = [synth.modelnet_like_problem(s, m=400 + 150 * s, hopf_n=3) for s in range(5)]
+    targets = [ctx.create_target(p.Y, grid_cap=2 * p.tau) for p in probs]
+    pbs = [ctx.problem(t, p.X, capi.hopf_grid(3),
+                       gpu_params(p, nn_mode="grid", refine_top_k=4 if i % 2 else 0, refine_K=1,
+                                  refine_delta_r=math.radians(1.0)))
+           for i, (t, p) in enumerate(zip(targets, probs))]
+    solo = [capi.result_dict(ctx.register(pb)) for pb in pbs]
+    ctx.set_option("serve_iter_pairs", 20_000_000)
+    try:
+        tickets = [ctx.submit(pb) for pb in pbs[:2]]
+        time.sleep(0.01)
+        tickets += [ctx.submit(pb) for pb in pbs[2:]]
+        out = {}
+        deadline = time.time() + 120
+        while len(out) < len(tickets) and time.time() < deadline:
+            for tk in tickets:
+                if tk not in out:
+                    st, r = ctx.poll(tk)
+                    if st != capi.DSES_NOT_READY:
+                        assert st == capi.DSES_OK
+                        out[tk] = capi.result_dict(r)
+            time.sleep(0.002)
+        assert len(out) == len(tickets)
+    finally:
+        ctx.set_option("serve_iter_pairs", 30_000_000_000)
+    for tk, a in zip(tickets, solo):
+        b = out[tk]
+        assert a["rot_index"] == b["rot_index"] and a["inliers"] == b["inliers"] and a["votes"] == b["votes"]
+        assert np.array_equal(a["t"], b["t"]) and a["cost"] == b["cost"]
+    for t in targets:
+        ctx.destroy_target(t)
+
+
 def test_serving_results_equal_solo(ctx):
     import time
 
