@@ -910,12 +910,24 @@ int pick_p(dses_ctx* c, Job& j) {
   if (it != c->tuned_p.end()) return it->second;
   if (c->capturing) return choose_p(c, one);
   const int64_t slice = std::min<int64_t>(j.n_first, (int64_t)c->sms * 16);
+  // the slice samples the whole grid at an even stride (the grid's first
+  // rotations are one corner of SO(3), which can favour another shape)
+  DevMem strided;
+  const float* rot = j.rot;
+  const int64_t stride = j.n_first / slice;
+  if (stride > 1) {
+    strided.alloc(36 * (size_t)slice, c->stream);
+    CK(cudaMemcpy2DAsync(strided.p, 36, j.rot, 36 * (size_t)stride, 36, (size_t)slice, cudaMemcpyDeviceToDevice,
+                         c->stream));
+    rot = (const float*)strided.p;
+  }
   float best_ms = 1e30f;
   int best_p = choose_p(c, one);
   const int cands[4] = {1, 2, 4, 8};
   for (int P : cands) {
     if (j.sparse && P == 8) continue;
     std::vector<PassDesc> d{make_desc(j, P, false)};
+    d[0].rot = rot;
     d[0].n_rot = (int)slice;
     const int tile = 1;
     std::vector<int> tp{0, (int)slice}, rp{0, (int)slice};

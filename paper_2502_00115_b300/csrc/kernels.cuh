@@ -23,8 +23,9 @@ __device__ __forceinline__ float robust_rho(int metric, float d, float eps, floa
 
 // Threads of the rotation-pass CTA (one CTA per SM, 32 warps).
 constexpr int kPassThreads = 1024;
-// Source points staged per chunk in shared memory (float4 each).
-constexpr int kSrcChunk = 1024;
+// Source points staged per chunk in shared memory (a float4 each; the packed
+// vote stages two, so half as many per chunk): 32 KB of staging.
+constexpr int kSrcChunk = 2048;
 // Target points per bounding-box group of the Morton-ordered targets.
 constexpr int kGroup = 32;
 // Largest dynamic shared memory a CTA may request on sm_103a (227 KB).
