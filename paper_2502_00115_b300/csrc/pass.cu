@@ -42,19 +42,23 @@ __device__ __forceinline__ unsigned floor_bits(float v) {
 
 // Trilinear value of the distance grid at q (interpolation between voxel
 // centres, clamped at the outermost centres; the cap outside the grid box),
-// together with bounds on the exact nearest-target distance d(q): the stored values are
-// min(d, cap) at voxel centres and d is 1-Lipschitz, so every corner c_k used
-// gives D_k - |q - c_k| <= d(q), and, if D_k < cap, d(q) <= D_k + |q - c_k|.
-__device__ __forceinline__ float grid_lookup_bounds(const PassDesc& d, float qx, float qy, float qz, float* lb,
-                                                    float* ub) {
+// together with two decisions from bounds on the exact nearest-target distance
+// d(q): the stored values are min(d, cap) at voxel centres and d is
+// 1-Lipschitz, so every corner c_k used gives D_k - |q - c_k| <= d(q), and, if
+// D_k < cap, d(q) <= D_k + |q - c_k|. *far: some corner proves d(q) >= e_far;
+// *near: some corner proves d(q) < e_near. Both tests compare squares
+// (D_k - e_far >= |q - c_k| iff D_k >= e_far and (D_k - e_far)^2 >= |q - c_k|^2),
+// so no square root is taken.
+__device__ __forceinline__ float grid_lookup_decide(const PassDesc& d, float qx, float qy, float qz, float e_far,
+                                                    float e_near, bool* far, bool* near) {
   const float G = (float)d.G;
   const float ux = (qx - d.glo[0]) * d.ginv_h[0];
   const float uy = (qy - d.glo[1]) * d.ginv_h[1];
   const float uz = (qz - d.glo[2]) * d.ginv_h[2];
   if (!(ux >= 0.f && ux <= G && uy >= 0.f && uy <= G && uz >= 0.f && uz <= G)) {
     // outside the grid box every target lies at least cap + h away
-    *lb = d.gcap;
-    *ub = INFINITY;
+    *far = d.gcap >= e_far;
+    *near = false;
     return d.gcap;
   }
   const float gx = fminf(fmaxf(ux - 0.5f, 0.f), G - 1.f);
@@ -70,16 +74,17 @@ __device__ __forceinline__ float grid_lookup_bounds(const PassDesc& d, float qx,
   // q - corner per axis, in world units (corner i at lo + (i + 1/2) h)
   const float h0 = 1.f / d.ginv_h[0], h1 = 1.f / d.ginv_h[1], h2 = 1.f / d.ginv_h[2];
   const float dx0 = (ux - 0.5f - (float)ix) * h0, dy0 = (uy - 0.5f - (float)iy) * h1, dz0 = (uz - 0.5f - (float)iz) * h2;
-  float l = 0.f, u = INFINITY;
+  bool f = false, n = false;
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     const float ex = (k & 4) ? dx0 - h0 : dx0, ey = (k & 2) ? dy0 - h1 : dy0, ez = (k & 1) ? dz0 - h2 : dz0;
-    const float r = sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
-    l = fmaxf(l, v[k] - r);
-    if (v[k] < d.gcap) u = fminf(u, v[k] + r);
+    const float r2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+    const float a = v[k] - e_far, c = e_near - v[k];
+    f |= a >= 0.f && a * a >= r2;
+    n |= v[k] < d.gcap && c > 0.f && c * c > r2;
   }
-  *lb = l;
-  *ub = u;
+  *far = f;
+  *near = n;
   const float c00 = v[0] + fz * (v[1] - v[0]);
   const float c01 = v[2] + fz * (v[3] - v[2]);
   const float c10 = v[4] + fz * (v[5] - v[4]);
@@ -714,12 +719,12 @@ __global__ void __launch_bounds__(256) count_kernel(PassLaunch L) {
       // Bounds on the exact nearest-target distance from the grid's corners
       // decide most queries; those within kBoundMargin of epsilon take the
       // exact cell-list search.
-      float lb, ub;
-      const float dg = grid_lookup_bounds(d, qx, qy, qz, &lb, &ub);
+      bool far, near;
+      const float dg = grid_lookup_decide(d, qx, qy, qz, d.eps + d.grid_err, d.eps - d.grid_err, &far, &near);
       bool inl;
-      if (lb >= d.eps + d.grid_err)
+      if (far)
         inl = false;
-      else if (ub < d.eps - d.grid_err)
+      else if (near)
         inl = true;
       else
         inl = has_inlier(d, qx, qy, qz);
