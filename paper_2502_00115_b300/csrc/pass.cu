@@ -641,21 +641,34 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
             }
           }
         } else if (d.hist_u16) {
-          const unsigned words = (nbins + 1) >> 1;
-          for (unsigned w = tid; w < words; w += kPassThreads) {
-            const uint32_t v = hist[w];
-            hist[w] = 0u;
-            const unsigned a = v & 0xffffu, b = v >> 16;
-            vsum += a + b;
-            if (a > bc) { bc = a; bb = 2 * w; }
-            if (b > bc) { bc = b; bb = 2 * w + 1; }
+          // 16-byte reads: the histogram's bytes are a multiple of 16 and the
+          // words past this slab's bins are zero (never voted, or cleared)
+          const unsigned q4 = (((nbins + 1) >> 1) + 3) >> 2;
+          uint4* h4 = reinterpret_cast<uint4*>(hist);
+          for (unsigned w4 = tid; w4 < q4; w4 += kPassThreads) {
+            const uint4 v4 = h4[w4];
+            h4[w4] = make_uint4(0u, 0u, 0u, 0u);
+            const uint32_t vv[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const unsigned a = vv[k] & 0xffffu, b = vv[k] >> 16;
+              vsum += a + b;
+              if (a > bc) { bc = a; bb = 8 * w4 + 2 * k; }
+              if (b > bc) { bc = b; bb = 8 * w4 + 2 * k + 1; }
+            }
           }
         } else {
-          for (unsigned w = tid; w < nbins; w += kPassThreads) {
-            const uint32_t v = hist[w];
-            hist[w] = 0u;
-            vsum += v;
-            if (v > bc) { bc = v; bb = w; }
+          const unsigned q4 = (nbins + 3) >> 2;
+          uint4* h4 = reinterpret_cast<uint4*>(hist);
+          for (unsigned w4 = tid; w4 < q4; w4 += kPassThreads) {
+            const uint4 v4 = h4[w4];
+            h4[w4] = make_uint4(0u, 0u, 0u, 0u);
+            const uint32_t vv[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              vsum += vv[k];
+              if (vv[k] > bc) { bc = vv[k]; bb = 4 * w4 + k; }
+            }
           }
         }
         vtotal += warp_sum_u32(vsum);
@@ -710,26 +723,35 @@ __global__ void __launch_bounds__(256) count_kernel(PassLaunch L) {
     const bool grid_cost = d.fuse_score && d.metric != 0;
     int cnt = 0;
     float csum = 0.f;
-    for (int i = lane; i < d.N; i += 32) {
-      const float x = __ldg(d.X + 3 * (size_t)i), y = __ldg(d.X + 3 * (size_t)i + 1),
-                  z = __ldg(d.X + 3 * (size_t)i + 2);
-      const float qx = fmaf(R[0], x, fmaf(R[1], y, R[2] * z)) + tx;
-      const float qy = fmaf(R[3], x, fmaf(R[4], y, R[5] * z)) + ty;
-      const float qz = fmaf(R[6], x, fmaf(R[7], y, R[8] * z)) + tz;
-      // Bounds on the exact nearest-target distance from the grid's corners
-      // decide most queries; those within kBoundMargin of epsilon take the
-      // exact cell-list search.
-      bool far, near;
-      const float dg = grid_lookup_decide(d, qx, qy, qz, d.eps + d.grid_err, d.eps - d.grid_err, &far, &near);
-      bool inl;
-      if (far)
-        inl = false;
-      else if (near)
-        inl = true;
-      else
-        inl = has_inlier(d, qx, qy, qz);
-      cnt += inl ? 1 : 0;
-      if (grid_cost) csum += robust_rho(d.metric, dg, d.eps, d.tau, d.huber_h, d.p_exp);
+    // two source points per lane and iteration: both points' 16 distance-grid
+    // gathers are in flight together (the kernel waits on L2 latency)
+    for (int i = lane; i < d.N; i += 64) {
+      const bool two = i + 32 < d.N;
+      const int i2 = two ? i + 32 : i;
+      const float xa = __ldg(d.X + 3 * (size_t)i), ya = __ldg(d.X + 3 * (size_t)i + 1),
+                  za = __ldg(d.X + 3 * (size_t)i + 2);
+      const float xb = __ldg(d.X + 3 * (size_t)i2), yb = __ldg(d.X + 3 * (size_t)i2 + 1),
+                  zb = __ldg(d.X + 3 * (size_t)i2 + 2);
+      const float qxa = fmaf(R[0], xa, fmaf(R[1], ya, R[2] * za)) + tx;
+      const float qya = fmaf(R[3], xa, fmaf(R[4], ya, R[5] * za)) + ty;
+      const float qza = fmaf(R[6], xa, fmaf(R[7], ya, R[8] * za)) + tz;
+      const float qxb = fmaf(R[0], xb, fmaf(R[1], yb, R[2] * zb)) + tx;
+      const float qyb = fmaf(R[3], xb, fmaf(R[4], yb, R[5] * zb)) + ty;
+      const float qzb = fmaf(R[6], xb, fmaf(R[7], yb, R[8] * zb)) + tz;
+      // bounds on the exact nearest-target distance from the grid's corners
+      // decide most queries; those within grid_err of epsilon take the exact
+      // cell-list search
+      bool fara, neara, farb, nearb;
+      const float e_far = d.eps + d.grid_err, e_near = d.eps - d.grid_err;
+      const float dga = grid_lookup_decide(d, qxa, qya, qza, e_far, e_near, &fara, &neara);
+      const float dgb = grid_lookup_decide(d, qxb, qyb, qzb, e_far, e_near, &farb, &nearb);
+      const bool ina = fara ? false : (neara ? true : has_inlier(d, qxa, qya, qza));
+      const bool inb = two && (farb ? false : (nearb ? true : has_inlier(d, qxb, qyb, qzb)));
+      cnt += (ina ? 1 : 0) + (inb ? 1 : 0);
+      if (grid_cost) {
+        csum += robust_rho(d.metric, dga, d.eps, d.tau, d.huber_h, d.p_exp);
+        if (two) csum += robust_rho(d.metric, dgb, d.eps, d.tau, d.huber_h, d.p_exp);
+      }
     }
 #pragma unroll
     for (int k = 16; k > 0; k >>= 1) {
