@@ -105,6 +105,7 @@ def test_tiny_every_rotation_matches_oracle(ctx, metric, nn):
     ref = oracle.register(p.X, p.Y, grid, P)
     g = oracle.dist_grid(p.Y, 128, P.grid_cap) if nn == "grid" and metric != "inlier" else None
     rep = check_rotations(p.X, p.Y, grid, P, k, V, M, C, range(len(grid)), ref=ref, dist_grid=g)
+    print("parity:", rep.summary())  # counted boundary cases, reported with -s
     assert rep.ok(), rep.summary()
     assert rep.vote_exact >= 0.98 * rep.checked, rep.summary()
     assert np.all(np.isfinite(C))  # every rotation is a candidate (q = 0)
@@ -123,6 +124,7 @@ def test_tiny_candidate_filters_match_oracle(ctx, over):
     ref = oracle.register(p.X, p.Y, grid, P)
     g = oracle.dist_grid(p.Y, 128, P.grid_cap) if nn == "grid" else None
     rep = check_rotations(p.X, p.Y, grid, P, k, V, M, C, range(len(grid)), ref=ref, dist_grid=g)
+    print("parity:", rep.summary())
     assert rep.ok(), rep.summary()
     cand_gpu = set(np.flatnonzero(np.isfinite(C)).tolist())
     cand_ref = set(np.flatnonzero(np.isfinite(ref.costs)).tolist())
@@ -145,6 +147,7 @@ def test_tiny_refinement_pass_matches_oracle(ctx):
     fine = np.concatenate([oracle.euler_box(grid[c], 1, math.radians(3.0)) for c in order])
     allR = np.concatenate([grid, fine])
     rep = check_rotations(p.X, p.Y, allR, P, k, V, M, C, range(len(allR)), ref=ref)
+    print("parity:", rep.summary())
     assert rep.ok(), rep.summary()
     assert r.rot_index == ref.rot_index or cost_close(ref.costs[r.rot_index], ref.costs[ref.rot_index], 1)
     assert r.cost <= np.nanmin(C[: len(grid)]) + 1e-7
@@ -203,6 +206,7 @@ def test_small_box_lane_private_counters(ctx):
             g = oracle.dist_grid(p.Y, 128, P.grid_cap)
             rep = check_rotations(p.X, p.Y, grid, P, base[0], base[1], base[2], base[3], range(0, n, 12),
                                   dist_grid=g)
+            print("parity:", rep.summary())
             assert rep.ok(), rep.summary()
         defaults = {k: ctx.get_option(k) for k in ("hist_mode", "points_per_thread", "vote_sparse")}
         try:
@@ -242,6 +246,7 @@ def test_even_extent_box_matches_oracle(ctx, hist_mode):
     ref = oracle.register(p.X, p.Y, grid, P)
     g = oracle.dist_grid(p.Y, 128, P.grid_cap)
     rep = check_rotations(p.X, p.Y, grid, P, k, V, M, C, range(len(grid)), ref=ref, dist_grid=g)
+    print("parity:", rep.summary())
     assert rep.ok(), rep.summary()
     assert rep.vote_exact >= 0.98 * rep.checked, rep.summary()
     ctx.destroy_target(t)
@@ -281,6 +286,7 @@ def test_modelnet_full_size_sampled_rotations(ctx):
     Rs = np.stack([oracle.hopf_rotation(p.hopf_n, i) for i in idx])
     g = oracle.dist_grid(p.Y, 128, P.grid_cap)
     rep = check_rotations(p.X, p.Y, Rs, P, k, V, M, C, idx, dist_grid=g)
+    print("parity:", rep.summary())
     assert rep.ok(), rep.summary()
     # the winner is a plausible pose (grid resolution ~3.75 degrees)
     ang = np.degrees(np.arccos(np.clip((np.trace(np.array(r.R[:]).reshape(3, 3).T @ p.R_true) - 1) / 2, -1, 1)))
@@ -305,6 +311,7 @@ def test_robot_like_full_size_sampled_rotations(ctx):
     idx = sorted(set(rng.choice(n1, size=8, replace=False).tolist()) | {int(np.argmax(V[:n1]))})
     Rs = np.stack([oracle.hopf_rotation(p.hopf_n, i) for i in idx])
     rep = check_rotations(p.X, p.Y, Rs, P, k, V, M, None, idx)
+    print("parity:", rep.summary())
     assert rep.ok(), rep.summary()
     # each second-pass box is centred on one of the best first-pass candidates
     B = (2 * p.refine_K + 1) ** 3
@@ -462,12 +469,14 @@ def test_explicit_and_euler_grids_match_oracle(ctx):
     k, V, M, C, r = ctx.debug(ctx.problem(t, p.X, g, gp), 50)
     ref = oracle.register(p.X, p.Y, Rx.astype(np.float32).astype(np.float64), P)
     rep = check_rotations(p.X, p.Y, Rx.astype(np.float32).astype(np.float64), P, k, V, M, C, range(50), ref=ref)
+    print("parity:", rep.summary())
     assert rep.ok(), rep.summary()
     eg = capi.euler_box_grid(p.R_true, 2, math.radians(4))
     k, V, M, C, r = ctx.debug(ctx.problem(t, p.X, eg, gp), 125)
     Re = oracle.euler_box(p.R_true, 2, math.radians(4))
     ref = oracle.register(p.X, p.Y, Re, P)
     rep = check_rotations(p.X, p.Y, Re, P, k, V, M, C, range(125), ref=ref)
+    print("parity:", rep.summary())
     assert rep.ok(), rep.summary()
     ctx.destroy_target(t)
 
