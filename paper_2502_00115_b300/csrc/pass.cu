@@ -7,9 +7,15 @@
 //   2. votes every pair (i, j): the lattice index k = ROUND((y_j - R x_i)/delta)
 //      relative to the box corner; pairs inside the lattice box increment a
 //      shared-memory histogram (Lemma 1, Eq. 5: the translation mode of the
-//      rotated pairwise differences, discretised as in Section IV-B);
-//   3. scans and clears the histogram for the mode: V = max count, k* = the
-//      lexicographically smallest bin holding V; publishes (k*, V).
+//      rotated pairwise differences, discretised as in Section IV-B) -- 16-bit
+//      packed or 32-bit counters, or a 32-bit copy per lane for small boxes,
+//      in x-slabs when the box does not fit, the layout padded to odd extents;
+//      pairs outside the box add to a per-lane sink word instead, so the
+//      atomic needs no branch; boxes small against the target cull (source,
+//      32-point target group) pairs first;
+//   3. scans and clears the histogram for the mode (skipping padding bins):
+//      V = max count, k* = the lexicographically smallest bin holding V;
+//      publishes (k*, V).
 // Work items are (problem, rotation tile) pairs taken from a global counter, so
 // one persistent launch serves one problem or a batch of uneven problems.
 //
@@ -432,7 +438,8 @@ __device__ __forceinline__ void vote_centred_sparse(const PassDesc& d, const flo
 }
 
 // Generic path (any extents): k_a = floor(w_a) by a round-down add, box test on
-// the integer indices.
+// the integer indices. The engine pads every layout to odd extents (centred
+// paths); this serves dses_vote_static boxes with an even extent.
 template <int P, bool U16>
 __device__ __forceinline__ void vote_generic(const PassDesc& d, const float4* __restrict__ srcc, int nsrc,
                                              unsigned SX, uint32_t* __restrict__ hist, int* item_ctr, int lane) {
