@@ -243,8 +243,10 @@ dses_status dses_exhaustive_search(dses_ctx* ctx, const dses_problem* problem, f
  *   "serve_tile_rotations" most rotations one request takes per serving iteration
  *   "serve_iter_pairs"     pair votes per serving iteration (requests in arrival
  *                          order fill it; default 3e10, ~20 ms of vote work)
- *   "vote_sparse"          0 auto, 1 dense vote, 2 cull (source, target group) pairs
- *                          outside the translation window (pays for small boxes)
+ *   "vote_sparse"          0 auto, 1 dense vote, 2 cull (source, 32-point target
+ *                          group) pairs outside the translation window (pays for
+ *                          small boxes), 3 the same with 64-point groups voted as
+ *                          packed pairs (pays when the window spans many groups)
  *   "record_timing"        1: time every rotation pass with CUDA events on the
  *                          context's stream
  *   "last_pass_ns"         (read-only) summed duration of the vote kernels of the
@@ -255,6 +257,7 @@ dses_status dses_exhaustive_search(dses_ctx* ctx, const dses_problem* problem, f
  *                          the translation box) of the last blocking call
  *   "last_vote_sparse"     (read-only) how many problems of the last blocking call
  *                          ran the culled (windowed) vote
+ *   "last_vote_paired"     (read-only) ... of which its 64-point-group form
  *   "graphs_cached"        (read-only) captured CUDA graphs held by the context
  *                          (dses_destroy_target drops those that read the target)
  *   "kernel_launches"      (read-only) kernels this library has launched in the

@@ -131,6 +131,9 @@ struct dses_target {
   float4* gbox = nullptr;   // per group of kGroup Morton-consecutive points: min, max
   int n_groups = 0;
   float gext[3] = {0, 0, 0};  // mean group bounding-box extent per axis
+  float4* gbox2 = nullptr;  // the same for groups of 2 kGroup points (paired culled vote)
+  int n_groups2 = 0;
+  float gext2[3] = {0, 0, 0};
   float* D = nullptr;       // G^3 distance grid
   int G = 0;
   float glo[3], gh[3], gcap = 0;
@@ -178,6 +181,7 @@ struct dses_ctx {
   int64_t launch_snapshot = 0;
   int64_t votes_total = 0;  // in-box pair votes of the last blocking call
   int64_t vote_sparse_jobs = 0;  // problems of the last blocking call on the culled vote
+  int64_t vote_paired_jobs = 0;  // ... of which on its paired 64-point-group form
   int64_t graph_count = 0;       // snapshot for the "graphs_cached" option
   // host staging: blocking calls, the serving worker, and the one in use
   Stage stage, serve_stage[2];  // the serving worker alternates two (two iterations in flight)
@@ -283,24 +287,34 @@ void build_morton_groups(dses_ctx* c, dses_target* T) {
     const float* p = &T->host[3 * (size_t)code[(size_t)j].second];
     ym[(size_t)j] = make_float4(p[0], p[1], p[2], 0.f);
   }
-  T->n_groups = (m + kGroup - 1) / kGroup;
-  std::vector<float4> box(2 * (size_t)T->n_groups);
-  for (int g = 0; g < T->n_groups; ++g) {
-    float4 lo = ym[(size_t)g * kGroup], hi = lo;
-    for (int j = g * kGroup; j < std::min(m, (g + 1) * kGroup); ++j) {
-      lo.x = std::min(lo.x, ym[j].x); lo.y = std::min(lo.y, ym[j].y); lo.z = std::min(lo.z, ym[j].z);
-      hi.x = std::max(hi.x, ym[j].x); hi.y = std::max(hi.y, ym[j].y); hi.z = std::max(hi.z, ym[j].z);
+  // group boxes for groups of kGroup and of 2 kGroup consecutive points
+  auto boxes = [&](int gsize, int* n_out, float* ext, std::vector<float4>& box) {
+    const int n = (m + gsize - 1) / gsize;
+    *n_out = n;
+    box.assign(2 * (size_t)n, make_float4(0.f, 0.f, 0.f, 0.f));
+    ext[0] = ext[1] = ext[2] = 0.f;
+    for (int g = 0; g < n; ++g) {
+      float4 lo = ym[(size_t)g * gsize], hi = lo;
+      for (int j = g * gsize; j < std::min(m, (g + 1) * gsize); ++j) {
+        lo.x = std::min(lo.x, ym[j].x); lo.y = std::min(lo.y, ym[j].y); lo.z = std::min(lo.z, ym[j].z);
+        hi.x = std::max(hi.x, ym[j].x); hi.y = std::max(hi.y, ym[j].y); hi.z = std::max(hi.z, ym[j].z);
+      }
+      box[2 * (size_t)g] = lo;
+      box[2 * (size_t)g + 1] = hi;
+      ext[0] += (hi.x - lo.x) / n;
+      ext[1] += (hi.y - lo.y) / n;
+      ext[2] += (hi.z - lo.z) / n;
     }
-    box[2 * (size_t)g] = lo;
-    box[2 * (size_t)g + 1] = hi;
-    T->gext[0] += (hi.x - lo.x) / T->n_groups;
-    T->gext[1] += (hi.y - lo.y) / T->n_groups;
-    T->gext[2] += (hi.z - lo.z) / T->n_groups;
-  }
+  };
+  std::vector<float4> box, box2;
+  boxes(kGroup, &T->n_groups, T->gext, box);
+  boxes(2 * kGroup, &T->n_groups2, T->gext2, box2);
   CK(cudaMalloc(&T->Ym, sizeof(float4) * (size_t)m));
   CK(cudaMalloc(&T->gbox, sizeof(float4) * box.size()));
+  CK(cudaMalloc(&T->gbox2, sizeof(float4) * box2.size()));
   CK(cudaMemcpyAsync(T->Ym, ym.data(), sizeof(float4) * (size_t)m, cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(T->gbox, box.data(), sizeof(float4) * box.size(), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(T->gbox2, box2.data(), sizeof(float4) * box2.size(), cudaMemcpyHostToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));
 }
 
@@ -362,7 +376,7 @@ struct Job {
   int u16 = 0, lanes = 0, slab_x = 0, n_slabs = 1, hist_bytes = 0;
   int Ep[3] = {0, 0, 0};  // vote layout extents: E padded to odd values
   bool fused = false;
-  bool sparse = false;
+  int sparse = 0;  // culled vote: 0 no, 1 32-point groups, 2 paired 64-point groups
   // device scratch
   DevMem mem;
   int4* kv = nullptr;
@@ -550,14 +564,25 @@ void plan(dses_ctx* c, Job& j) {
     const double win = (double)j.E[a] * j.delta + j.T->gext[a];
     keep *= ext > 0 ? std::min(1.0, win / ext) : 1.0;
   }
-  j.sparse = c->opt.vote_sparse == 2 || (c->opt.vote_sparse == 0 && keep < 0.35);
+  const bool cull = c->opt.vote_sparse >= 2 || (c->opt.vote_sparse == 0 && keep < 0.35);
+  // paired 64-point groups when the window is at least 1.5 group extents wide
+  // on every axis (each kept source then votes 64 targets in one packed step;
+  // robot-like: 2.2, the 32-point groups win below ~1 on ModelNet-shaped
+  // small boxes)
+  double span = 1e300;
+  for (int a = 0; a < 3; ++a)
+    span = std::min(span, (double)j.E[a] * j.delta / std::max(1e-12, (double)j.T->gext2[a]));
+  j.sparse = !cull ? 0 : c->opt.vote_sparse == 2 ? 1 : c->opt.vote_sparse == 3 ? 2 : (span >= 1.5 ? 2 : 1);
 }
 
 int choose_p(dses_ctx* c, const std::vector<Job*>& jobs) {
   if (c->opt.points_per_thread > 0) return (int)c->opt.points_per_thread;
   int64_t mmax = 0;
   for (auto* j : jobs) mmax = std::max<int64_t>(mmax, j->T->m);
-  return mmax <= 128 ? 1 : (mmax <= 512 ? 2 : 4);
+  const int P = mmax <= 128 ? 1 : (mmax <= 512 ? 2 : 4);
+  bool paired = false;
+  for (auto* j : jobs) paired |= j->sparse == 2;
+  return paired && P == 1 ? 2 : P;  // the paired culled vote is built for 2 and 4
 }
 
 int gcd(int a, int b) { return b ? gcd(b, a % b) : a; }
@@ -652,8 +677,8 @@ PassDesc make_desc(const Job& j, int P, bool second) {
   d.X = j.X;
   d.Y = j.cl->sorted;
   d.Yv = j.T->Ym;
-  d.gbox = j.T->gbox;
-  d.n_groups = j.T->n_groups;
+  d.gbox = j.sparse == 2 ? j.T->gbox2 : j.T->gbox;
+  d.n_groups = j.sparse == 2 ? j.T->n_groups2 : j.T->n_groups;
   d.N = j.N;
   d.M = j.T->m;
   if (!second) {
@@ -678,7 +703,7 @@ PassDesc make_desc(const Job& j, int P, bool second) {
   d.n_slabs = j.n_slabs;
   d.hist_u16 = j.u16;
   d.hist_lanes = j.lanes;
-  d.sparse = j.sparse ? 1 : 0;
+  d.sparse = j.sparse;
   d.n_tchunks = (j.T->m + 32 * P - 1) / (32 * P);
   // dense: items a multiple of the 32 warps (equal work per item); sparse:
   // items are uneven anyway and the CTA's item counter balances them, so keep
@@ -781,10 +806,14 @@ void launch_pass(dses_ctx* c, const std::vector<PassPart>& parts, int P) {
     for (auto& e : ev) CK(cudaEventCreate(&e));
     CK(cudaEventRecord(ev[0], s));
   }
-  bool any_sparse = false;
-  for (auto& pp : parts) any_sparse |= pp.job->sparse;
-  if (any_sparse && P == 8) throw Error{DSES_ERR_CUDA, "internal: culled vote planned with 8 points per thread"};
-  CK(launch_vote(L, P, any_sparse, ctas, s));
+  // one culled mode per launch (the engine groups launches by shape and mode)
+  int mode = 0;
+  for (auto& pp : parts) mode = std::max(mode, pp.job->sparse);
+  for (auto& pp : parts)
+    if (pp.job->sparse && pp.job->sparse != mode) throw Error{DSES_ERR_CUDA, "internal: mixed culled modes"};
+  if ((mode == 1 && P == 8) || (mode == 2 && P != 2 && P != 4))
+    throw Error{DSES_ERR_CUDA, "internal: culled vote planned with an unsupported points-per-thread shape"};
+  CK(launch_vote(L, P, mode, ctas, s));
   if (ev[0]) CK(cudaEventRecord(ev[1], s));
   CK(launch_count(L, (int)total_rot, s));
   if (ev[0]) {
@@ -898,6 +927,7 @@ int pick_p(dses_ctx* c, Job& j) {
   // here, before any descriptor is built for it
   if (c->opt.points_per_thread > 0) {
     const int P = (int)c->opt.points_per_thread;
+    if (j.sparse == 2) return P >= 4 ? 4 : 2;
     return j.sparse && P == 8 ? 4 : P;
   }
   std::vector<Job*> one{&j};
@@ -925,7 +955,7 @@ int pick_p(dses_ctx* c, Job& j) {
   int best_p = choose_p(c, one);
   const int cands[4] = {1, 2, 4, 8};
   for (int P : cands) {
-    if (j.sparse && P == 8) continue;
+    if ((j.sparse && P == 8) || (j.sparse == 2 && P == 1)) continue;
     std::vector<PassDesc> d{make_desc(j, P, false)};
     d[0].rot = rot;
     d[0].n_rot = (int)slice;
@@ -974,19 +1004,20 @@ int pick_p(dses_ctx* c, Job& j) {
 // result slot. No host synchronisation inside (except autotuner trials).
 void run_pipeline(dses_ctx* c, std::vector<Job*>& jobs) {
   for (auto* j : jobs) stage_setup(c, *j);
-  // one persistent launch per points-per-thread shape (normally one)
+  // one persistent launch per (points-per-thread shape, culled mode): key
+  // 4 P + mode (normally one launch)
   std::map<int, std::vector<PassPart>> first, fine;
   std::map<Job*, int> shape;
-  for (auto* j : jobs) shape[j] = pick_p(c, *j);
+  for (auto* j : jobs) shape[j] = 4 * pick_p(c, *j) + j->sparse;
   for (auto* j : jobs) first[shape[j]].push_back({j, false, 0, j->n_first});
-  for (auto& kv : first) launch_pass(c, kv.second, kv.first);
+  for (auto& kv : first) launch_pass(c, kv.second, kv.first / 4);
   for (auto* j : jobs) stage_candidates(c, *j, false);
   for (auto* j : jobs)
     if (j->rtop > 0) {
       stage_refine_grid(c, *j);
       fine[shape[j]].push_back({j, true, 0, j->n_fine});
     }
-  for (auto& kv : fine) launch_pass(c, kv.second, kv.first);
+  for (auto& kv : fine) launch_pass(c, kv.second, kv.first / 4);
   for (auto* j : jobs)
     if (j->rtop > 0) stage_candidates(c, *j, true);
   stage_finalize(c, jobs);
@@ -1122,7 +1153,7 @@ void worker_loop(dses_ctx* c) {
       // one iteration: requests in admission order take rotations until the
       // iteration's pair-vote budget is spent (the oldest request finishes
       // first; the next one starts in the same iteration when budget is left);
-      // one launch per points-per-thread shape
+      // one launch per (points-per-thread shape, culled mode): key 4 P + mode
       std::map<int, std::vector<PassPart>> parts;
       const int64_t slice = std::max<int64_t>(1, c->opt.serve_tile_rotations);
       double budget = (double)c->opt.serve_iter_pairs;
@@ -1133,11 +1164,11 @@ void worker_loop(dses_ctx* c) {
           const double per_rot = (double)r->job.N * (double)r->job.T->m;
           const int64_t want = std::max<int64_t>(1, (int64_t)(budget / per_rot));
           const int64_t a0 = r->next, b0 = std::min({r->job.n_first, a0 + slice, a0 + want});
-          parts[pick_p(c, r->job)].push_back({&r->job, false, a0, b0});
+          parts[4 * pick_p(c, r->job) + r->job.sparse].push_back({&r->job, false, a0, b0});
           r->next = b0;
           budget -= (double)(b0 - a0) * per_rot;
         }
-        for (auto& kv : parts) launch_pass(c, kv.second, kv.first);
+        for (auto& kv : parts) launch_pass(c, kv.second, kv.first / 4);
         std::vector<Job*> fin;
         std::map<int, std::vector<PassPart>> fine;
         for (auto& r : active) {
@@ -1145,12 +1176,12 @@ void worker_loop(dses_ctx* c) {
           stage_candidates(c, r->job, false);
           if (r->job.rtop > 0) {
             stage_refine_grid(c, r->job);
-            fine[pick_p(c, r->job)].push_back({&r->job, true, 0, r->job.n_fine});
+            fine[4 * pick_p(c, r->job) + r->job.sparse].push_back({&r->job, true, 0, r->job.n_fine});
           }
           fin.push_back(&r->job);
         }
         for (auto& kv : fine) {
-          launch_pass(c, kv.second, kv.first);
+          launch_pass(c, kv.second, kv.first / 4);
           for (auto& pp : kv.second) stage_candidates(c, *pp.job, true);
         }
         if (!fin.empty()) stage_finalize(c, fin);
@@ -1358,6 +1389,8 @@ dses_status finish_results(dses_ctx* c, std::vector<Job*>& jobs, dses_result* ou
   for (auto v : votes) c->votes_total += (int64_t)v;
   c->vote_sparse_jobs = 0;
   for (auto* j : jobs) c->vote_sparse_jobs += j->sparse ? 1 : 0;
+  c->vote_paired_jobs = 0;
+  for (auto* j : jobs) c->vote_paired_jobs += j->sparse == 2 ? 1 : 0;
   collect_timing(c);
   dses_status st = DSES_OK;
   for (size_t i = 0; i < jobs.size(); ++i) {
@@ -1419,6 +1452,7 @@ static void free_target(dses_target* T) {
   if (T->Y) cudaFree(T->Y);
   if (T->Ym) cudaFree(T->Ym);
   if (T->gbox) cudaFree(T->gbox);
+  if (T->gbox2) cudaFree(T->gbox2);
   if (T->D) cudaFree(T->D);
   for (auto& kv : T->cells) {
     cudaFree(kv.second.start);
@@ -1894,6 +1928,7 @@ static int64_t* option_slot(dses_ctx* c, const char* key) {
   if (k == "last_count_ns") return &c->count_ns;
   if (k == "last_votes_total") return &c->votes_total;
   if (k == "last_vote_sparse") return &c->vote_sparse_jobs;
+  if (k == "last_vote_paired") return &c->vote_paired_jobs;
   if (k == "graphs_cached") {
     c->graph_count = (int64_t)c->graphs.size();
     return &c->graph_count;
@@ -1914,13 +1949,14 @@ dses_status dses_set_option(dses_ctx* c, const char* key, int64_t value) {
     const std::string k(key);
     bool ok = true;
     if (k == "hist_mode") ok = value >= 0 && value <= 3;
-    else if (k == "vote_sparse") ok = value >= 0 && value <= 2;
+    else if (k == "vote_sparse") ok = value >= 0 && value <= 3;
     else if (k == "hist_budget_bytes") ok = value >= 1024 && value <= kHistBudget;
     else if (k == "points_per_thread") ok = value == 0 || value == 1 || value == 2 || value == 4 || value == 8;
     else if (k == "fuse_score" || k == "autotune" || k == "use_graphs" || k == "record_timing")
       ok = value == 0 || value == 1;
     else if (k == "last_pass_ns" || k == "last_pass_launches" || k == "kernel_launches" || k == "last_count_ns" ||
-             k == "last_votes_total" || k == "last_vote_sparse" || k == "graphs_cached")
+             k == "last_votes_total" || k == "last_vote_sparse" || k == "last_vote_paired" ||
+             k == "graphs_cached")
       ok = false;  // read-only
     else if (k == "tile_rotations") ok = value >= 0 && value <= 4096;
     else ok = value >= 1;

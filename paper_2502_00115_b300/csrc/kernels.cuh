@@ -57,7 +57,8 @@ struct PassDesc {
   int n_slabs;
   int hist_u16;          // 1: two 16-bit counters per 32-bit word
   int hist_lanes;        // 1: 32-bit counters, one copy per lane: word bin * 32 + lane
-  int sparse;            // 1: cull (source, target group) pairs outside the window
+  int sparse;            // culled vote: 0 no, 1 32-point groups, 2 paired 64-point
+                         // groups (gbox / n_groups hold that mode's group boxes)
   // vote work decomposition per rotation: items = n_tchunks x n_sgroups
   int n_tchunks;         // target chunks of 32 * P points
   int n_sgroups;         // source groups
@@ -99,9 +100,10 @@ struct PassLaunch {
 };
 
 // Hot path, kernel 1: vote -> mode (k*, V) per rotation (persistent, one CTA per SM).
-// sparse: launch the instance that also carries the culled path (any problem
-// of the launch with d.sparse set); points_per_thread 8 only without it.
-cudaError_t launch_vote(const PassLaunch& L, int points_per_thread, bool sparse, int grid_ctas, cudaStream_t s);
+// sparse: 0 dense; 1 the instance that also carries the culled path (points
+// per thread 1, 2, 4); 2 the paired culled path (2, 4). Problems of the launch
+// with d.sparse set must use that mode; dense launches take 1, 2, 4 or 8.
+cudaError_t launch_vote(const PassLaunch& L, int points_per_thread, int sparse, int grid_ctas, cudaStream_t s);
 // Kernel 2: inlier count M at t* and, on the fused path, grid score + argmin.
 cudaError_t launch_count(const PassLaunch& L, int total_rot, cudaStream_t s);
 int pass_smem_bytes(int hist_bytes);

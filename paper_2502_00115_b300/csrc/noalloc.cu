@@ -171,7 +171,7 @@ extern "C" dses_status dses_vote_static(int device, void* cuda_stream, const flo
     L.work_counter = reinterpret_cast<int*>(base + kOffCounter);
     L.hist_bytes = hist_bytes;
     L.padded = 0;
-    if (launch_vote(L, ppt, false, std::max(1, std::min(sms, tiles)), s) != cudaSuccess) {
+    if (launch_vote(L, ppt, 0, std::max(1, std::min(sms, tiles)), s) != cudaSuccess) {
       cudaGetLastError();
       st = DSES_ERR_CUDA;
       break;

@@ -437,6 +437,96 @@ __device__ __forceinline__ void vote_centred_sparse(const PassDesc& d, const flo
   }
 }
 
+// Paired culled path, for windows that span many target groups (large
+// targets: the robot-like problem): groups of 64 Morton-consecutive targets
+// (d.gbox / d.n_groups hold the 64-point boxes in this mode), a lane holding
+// two of each of its item's P / 2 groups (points 64 g + lane and 64 g + 32 +
+// lane) as a packed FP32 pair; one ballot per (32 sources, group), and each
+// kept source votes the group's 64 targets in one packed step. Against the
+// 32-point path this halves the iterations per kept target but keeps more
+// (source, group) pairs, so it pays only when the window is large against a
+// group. Sources are staged duplicated as for vote_centred_x2.
+template <int P, bool U16>
+__device__ __forceinline__ void vote_centred_paired(const PassDesc& d, const float4* __restrict__ srcd, int nsrc,
+                                                    unsigned SX, uint32_t hist_base, int* item_ctr, int lane,
+                                                    float* __restrict__ thr, uint32_t sink) {
+  static_assert(P == 2 || P == 4, "two targets of each of P / 2 groups per lane");
+  constexpr int Q = P / 2;  // 64-point groups per item
+  const int n_tchunks = d.n_tchunks, n_sgroups = d.n_sgroups;
+  const int n_items = n_tchunks * n_sgroups;
+  const int spg = (nsrc + n_sgroups - 1) / n_sgroups;
+  const unsigned Ey = (unsigned)d.E[1], Ez = (unsigned)d.E[2], Eyz = Ey * Ez;
+  const float inv = d.inv_delta;
+  const float hx = 0.5f * (float)SX, hy = 0.5f * (float)Ey, hz = 0.5f * (float)Ez;
+  const float mx = kMagic + (float)((SX - 1) / 2), my = kMagic + (float)((Ey - 1) / 2),
+              mz = kMagic + (float)((Ez - 1) / 2);
+  const uint64_t inv2 = pack2(inv, inv), mx2 = pack2(mx, mx), my2 = pack2(my, my), mz2 = pack2(mz, mz);
+  const uint32_t bias = kMagicBits * (Eyz + Ez + 1u);
+  const uint32_t unit = d.hist_lanes ? 128u : 4u;
+  const uint32_t abase = U16 ? hist_base - 2u * bias
+                             : hist_base + (d.hist_lanes ? 4u * (uint32_t)lane : 0u) - unit * bias;
+  const uint32_t adummy = sink + 4u * (uint32_t)lane;
+  for (int it = next_item(item_ctr, lane); it < n_items; it = next_item(item_ctr, lane)) {
+    const int tc = it % n_tchunks, sg = it / n_tchunks;
+    // keep (source, group) iff s1_a <= c_a <= s2_a on every axis
+    if (lane < Q) {
+      const int g = tc * Q + lane;
+      float* t = thr + 8 * lane;
+      if (g < d.n_groups) {
+        const float4 lo = __ldg(d.gbox + 2 * g), hi = __ldg(d.gbox + 2 * g + 1);
+        t[0] = -hx - kCullMargin - hi.x * inv; t[1] = hx + kCullMargin - lo.x * inv;
+        t[2] = -hy - kCullMargin - hi.y * inv; t[3] = hy + kCullMargin - lo.y * inv;
+        t[4] = -hz - kCullMargin - hi.z * inv; t[5] = hz + kCullMargin - lo.z * inv;
+      } else {
+        t[0] = t[2] = t[4] = INFINITY;
+        t[1] = t[3] = t[5] = -INFINITY;
+      }
+    }
+    __syncwarp();
+    // the lane's target pairs, one per group; padding lanes never vote
+    uint64_t yx[Q], yy[Q], yz[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int j0 = (tc * Q + q) * 64 + lane, j1 = j0 + 32;
+      const float4 a = j0 < d.M ? __ldg(d.Yv + j0) : make_float4(1e30f, 1e30f, 1e30f, 0.f);
+      const float4 b = j1 < d.M ? __ldg(d.Yv + j1) : make_float4(1e30f, 1e30f, 1e30f, 0.f);
+      yx[q] = pack2(a.x, b.x);
+      yy[q] = pack2(a.y, b.y);
+      yz[q] = pack2(a.z, b.z);
+    }
+    const int i0 = sg * spg, i1 = min(i0 + spg, nsrc);
+    for (int s0 = i0; s0 < i1; s0 += 32) {
+      const int mine = s0 + lane;
+      const bool valid = mine < i1;
+      const int ms = valid ? mine : i0;
+      const float4 cm = srcd[2 * ms];  // (c_x, c_x, c_y, c_y)
+      const float cmz = srcd[2 * ms + 1].x;
+      uint32_t kmask[Q];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const float4 ta = *reinterpret_cast<const float4*>(thr + 8 * q);
+        const float2 tb = *reinterpret_cast<const float2*>(thr + 8 * q + 4);
+        const bool keep = valid && cm.x >= ta.x && cm.x <= ta.y && cm.z >= ta.z && cm.z <= ta.w && cmz >= tb.x &&
+                          cmz <= tb.y;
+        kmask[q] = __ballot_sync(0xffffffffu, keep);
+      }
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        uint32_t m = kmask[q];
+        while (m) {
+          const int j = s0 + __ffs(m) - 1;
+          m &= m - 1;
+          const float4 ca = srcd[2 * j];
+          const float2 cb = *reinterpret_cast<const float2*>(srcd + 2 * j + 1);
+          vote_two_pairs<U16>(yx[q], yy[q], yz[q], inv2, pack2(ca.x, ca.y), pack2(ca.z, ca.w), pack2(cb.x, cb.y),
+                              mx2, my2, mz2, Eyz, Ez, abase, hx, hy, hz, hx, adummy, unit);
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
 // Generic path (any extents): k_a = floor(w_a) by a round-down add, box test on
 // the integer indices. The engine pads every layout to odd extents (centred
 // paths); this serves dses_vote_static boxes with an even extent.
@@ -473,9 +563,10 @@ __device__ __forceinline__ void vote_generic(const PassDesc& d, const float4* __
   }
 }
 
-// SPARSE: this instance also carries the culled path (problems with
-// d.sparse); the dense instance leaves it out so it keeps its registers.
-template <int P, bool SPARSE, bool PADDED>
+// SPARSE: 0 dense; 1 this instance also carries the culled path, 2 the paired
+// culled path (for problems with d.sparse set to that mode); the dense
+// instance leaves them out so it keeps its registers.
+template <int P, int SPARSE, bool PADDED>
 __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ PassDesc sd;
@@ -547,7 +638,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
           off2 = 0.5f - (float)d.lo[2];
         }
         // the packed path stages 32 bytes per source: half as many per chunk
-        const bool packed = P >= 2 && centred && !(SPARSE && d.sparse);
+        const bool packed = P >= 2 && centred && !(SPARSE == 1 && d.sparse);
         const int chunk = packed ? kSrcChunk / 2 : kSrcChunk;
         for (int c0 = 0; c0 < d.N; c0 += chunk) {
           const int c1 = min(c0 + chunk, d.N);
@@ -569,7 +660,15 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
             }
           }
           __syncthreads();
-          if (SPARSE && centred && d.sparse) {
+          if (SPARSE == 2 && centred && d.sparse) {
+            constexpr int PS = P >= 4 ? 4 : 2;  // paired instances are built for 2 and 4
+            if (d.hist_u16)
+              vote_centred_paired<PS, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane,
+                                            s_thr[SPARSE ? warp : 0], (uint32_t)__cvta_generic_to_shared(s_sink));
+            else
+              vote_centred_paired<PS, false>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane,
+                                             s_thr[SPARSE ? warp : 0], (uint32_t)__cvta_generic_to_shared(s_sink));
+          } else if (SPARSE == 1 && centred && d.sparse) {
             if (d.hist_u16)
               vote_centred_sparse<P, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane,
                                            s_thr[SPARSE ? warp : 0], (uint32_t)__cvta_generic_to_shared(s_sink));
@@ -777,7 +876,7 @@ __global__ void __launch_bounds__(256) count_kernel(PassLaunch L) {
   }
 }
 
-template <int P, bool SPARSE, bool PADDED>
+template <int P, int SPARSE, bool PADDED>
 cudaError_t launch_vote_p(const PassLaunch& L, int grid_ctas, cudaStream_t s) {
   const int smem = pass_smem_bytes(L.hist_bytes);
   static int configured = 0;
@@ -793,21 +892,28 @@ cudaError_t launch_vote_p(const PassLaunch& L, int grid_ctas, cudaStream_t s) {
 }
 
 template <bool PADDED>
-cudaError_t launch_vote_padded(const PassLaunch& L, int points_per_thread, bool sparse, int grid_ctas,
+cudaError_t launch_vote_padded(const PassLaunch& L, int points_per_thread, int sparse, int grid_ctas,
                                cudaStream_t s) {
-  if (sparse) {
+  if (sparse == 2) {
     switch (points_per_thread) {
-      case 1: return launch_vote_p<1, true, PADDED>(L, grid_ctas, s);
-      case 2: return launch_vote_p<2, true, PADDED>(L, grid_ctas, s);
-      case 4: return launch_vote_p<4, true, PADDED>(L, grid_ctas, s);
+      case 2: return launch_vote_p<2, 2, PADDED>(L, grid_ctas, s);
+      case 4: return launch_vote_p<4, 2, PADDED>(L, grid_ctas, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  if (sparse == 1) {
+    switch (points_per_thread) {
+      case 1: return launch_vote_p<1, 1, PADDED>(L, grid_ctas, s);
+      case 2: return launch_vote_p<2, 1, PADDED>(L, grid_ctas, s);
+      case 4: return launch_vote_p<4, 1, PADDED>(L, grid_ctas, s);
       default: return cudaErrorInvalidValue;
     }
   }
   switch (points_per_thread) {
-    case 1: return launch_vote_p<1, false, PADDED>(L, grid_ctas, s);
-    case 2: return launch_vote_p<2, false, PADDED>(L, grid_ctas, s);
-    case 4: return launch_vote_p<4, false, PADDED>(L, grid_ctas, s);
-    case 8: return launch_vote_p<8, false, PADDED>(L, grid_ctas, s);
+    case 1: return launch_vote_p<1, 0, PADDED>(L, grid_ctas, s);
+    case 2: return launch_vote_p<2, 0, PADDED>(L, grid_ctas, s);
+    case 4: return launch_vote_p<4, 0, PADDED>(L, grid_ctas, s);
+    case 8: return launch_vote_p<8, 0, PADDED>(L, grid_ctas, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -816,7 +922,7 @@ cudaError_t launch_vote_padded(const PassLaunch& L, int points_per_thread, bool 
 
 int pass_smem_bytes(int hist_bytes) { return hist_bytes + kSrcChunk * (int)sizeof(float4); }
 
-cudaError_t launch_vote(const PassLaunch& L, int points_per_thread, bool sparse, int grid_ctas, cudaStream_t s) {
+cudaError_t launch_vote(const PassLaunch& L, int points_per_thread, int sparse, int grid_ctas, cudaStream_t s) {
   return L.padded ? launch_vote_padded<true>(L, points_per_thread, sparse, grid_ctas, s)
                   : launch_vote_padded<false>(L, points_per_thread, sparse, grid_ctas, s);
 }

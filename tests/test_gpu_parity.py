@@ -166,7 +166,8 @@ def test_histogram_modes_and_launch_shapes_agree(ctx):
     variants = [dict(hist_mode=1), dict(hist_mode=2), dict(hist_mode=1, hist_budget_bytes=20000),
                 dict(hist_mode=2, hist_budget_bytes=9000), dict(points_per_thread=1), dict(points_per_thread=2),
                 dict(points_per_thread=8), dict(fuse_score=0), dict(tile_rotations=1), dict(vote_sparse=2),
-                dict(vote_sparse=2, points_per_thread=2)]
+                dict(vote_sparse=2, points_per_thread=2), dict(vote_sparse=3), dict(vote_sparse=3, points_per_thread=2),
+                dict(vote_sparse=3, hist_mode=1)]
     defaults = {k: ctx.get_option(k) for k in ("hist_mode", "hist_budget_bytes", "points_per_thread", "fuse_score",
                                                "tile_rotations", "vote_sparse")}
     try:
@@ -211,7 +212,8 @@ def test_small_box_lane_private_counters(ctx):
         defaults = {k: ctx.get_option(k) for k in ("hist_mode", "points_per_thread", "vote_sparse")}
         try:
             for v in (dict(hist_mode=1), dict(hist_mode=3, points_per_thread=1), dict(hist_mode=3, points_per_thread=8),
-                      dict(hist_mode=3, vote_sparse=2), dict(hist_mode=1, vote_sparse=2)):
+                      dict(hist_mode=3, vote_sparse=2), dict(hist_mode=1, vote_sparse=2), dict(hist_mode=3, vote_sparse=3),
+                      dict(hist_mode=1, vote_sparse=3, points_per_thread=4)):
                 for key, val in v.items():
                     ctx.set_option(key, val)
                 k, V, M, C, r = ctx.debug(pb, n)
@@ -306,6 +308,7 @@ def test_robot_like_full_size_sampled_rotations(ctx):
     n = p.n_rotations
     k, V, M, C, r = ctx.debug(pb, n)
     assert r.status == 0
+    assert ctx.get_option("last_vote_paired") == 1  # the window spans many 64-point groups
     P = oracle_params(p, gp, p.grid_cap)
     rng = np.random.default_rng(1)
     idx = sorted(set(rng.choice(n1, size=8, replace=False).tolist()) | {int(np.argmax(V[:n1]))})
@@ -321,6 +324,26 @@ def test_robot_like_full_size_sampled_rotations(ctx):
     assert r.cost <= C[:n1].min() + 1e-7
     ang = np.degrees(np.arccos(np.clip((np.trace(np.array(r.R[:]).reshape(3, 3).T @ p.R_true) - 1) / 2, -1, 1)))
     assert ang < 3.0, ang
+    ctx.destroy_target(t)
+
+
+def test_culled_modes_agree_on_robot_like(ctx):
+    # the paired 64-point-group culling (auto here), the 32-point culling and
+    # the dense vote give bit-identical per-rotation (k*, V, M)
+    p = synth.robot_like_problem(0, hopf_n=2, refine_top_k=0)
+    t = ctx.create_target(p.Y, grid_cap=p.grid_cap)
+    pb = ctx.problem(t, p.X, capi.hopf_grid(2), gpu_params(p, nn_mode="grid", huber_h=p.huber_h, refine_top_k=0))
+    n = 72 * 8
+    base = ctx.debug(pb, n)
+    assert ctx.get_option("last_vote_paired") == 1
+    try:
+        for mode in (2, 1):
+            ctx.set_option("vote_sparse", mode)
+            k, V, M, C, r = ctx.debug(pb, n)
+            assert ctx.get_option("last_vote_paired") == 0
+            assert np.array_equal(k, base[0]) and np.array_equal(V, base[1]) and np.array_equal(M, base[2]), mode
+    finally:
+        ctx.set_option("vote_sparse", 0)
     ctx.destroy_target(t)
 
 
