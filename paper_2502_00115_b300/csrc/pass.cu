@@ -337,8 +337,7 @@ __device__ __forceinline__ void vote_centred_x2(const PassDesc& d, const float4*
       yz[q] = pack2(ty[2 * q][2], ty[2 * q + 1][2]);
     }
     const int i0 = sg * spg, i1 = min(i0 + spg, nsrc);
-    constexpr int kUnroll = P >= 8 ? 1 : 4;  // P = 8 spills when unrolled
-#pragma unroll kUnroll
+#pragma unroll 4
     for (int i = i0; i < i1; ++i) {
       const float4 ca = srcd[2 * i];
       const float2 cb = *reinterpret_cast<const float2*>(srcd + 2 * i + 1);
