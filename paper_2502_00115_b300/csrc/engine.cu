@@ -1151,8 +1151,8 @@ void worker_loop(dses_ctx* c) {
         }
       }
       // one iteration: requests in admission order take rotations until the
-      // iteration's pair-vote budget is spent (the oldest request finishes
-      // first; the next one starts in the same iteration when budget is left);
+      // iteration's pair-vote budget is spent or one of them completes its
+      // first pass (the oldest request finishes first);
       // one launch per (points-per-thread shape, culled mode): key 4 P + mode
       std::map<int, std::vector<PassPart>> parts;
       const int64_t slice = std::max<int64_t>(1, c->opt.serve_tile_rotations);
@@ -1167,6 +1167,10 @@ void worker_loop(dses_ctx* c) {
           parts[4 * pick_p(c, r->job) + r->job.sparse].push_back({&r->job, false, a0, b0});
           r->next = b0;
           budget -= (double)(b0 - a0) * per_rot;
+          // a request that completes its first pass here ends the iteration:
+          // its result is then ready when its own work is, and the next
+          // request starts in the following iteration (already in flight)
+          if (b0 == r->job.n_first) break;
         }
         for (auto& kv : parts) launch_pass(c, kv.second, kv.first / 4);
         std::vector<Job*> fin;
