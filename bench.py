@@ -331,6 +331,7 @@ def ours(args, ws, rank, local):
                      "kernel_ms": pass_s * 1000,
                      "count_kernel_ms": statistics.mean(count_ns) / 1e6,
                      "peak_source": "recipe unit counts: 148 SMs x 128 lanes x 2032 MHz",
+                     "frac_of_measured_ffma": (achieved / pk["ffma_per_s"]) if "ffma_per_s" in pk else None,
                      "ops_per_launch": ops},
         "smem_atomic_roofline": {
             "kernel": "vote_kernel", "achieved": votes / pass_s,
