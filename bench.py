@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--points-per-thread", type=int, default=0, help="vote launch shape (0: library default)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["modelnet_like", "batched", "serving", "robot_like", "quality", "sweep"],
+    ap.add_argument("--workload", choices=["modelnet_like", "batched", "serving", "robot_like", "quality", "sweep", "tiny"],
                     default="modelnet_like",
                     help="modelnet_like: the benchmark line; batched / serving: the other configurations")
     ap.add_argument("--batch-count", type=int, default=64)
@@ -635,6 +635,60 @@ def sweep(args, ws, rank, local):
                       "source_points": len(p.X), "target_points": len(p.Y), "points": rows}), flush=True)
 
 
+def tiny_cpu_baseline(p, threads):
+    """cpu_baseline leg of the tiny workload: the FP64 oracle's whole
+    registration of the same problem, single-threaded and on every host core."""
+    import oracle
+
+    oracle.build()
+    P = oracle.make_params(metric=p.metric, epsilon=float(np.float32(p.epsilon)), tau=float(np.float32(p.tau)),
+                           t_half=[float(np.float32(v)) for v in p.t_half], grid_cap=float(np.float32(2 * p.tau)))
+    grid = oracle.hopf_grid(p.hopf_n)
+    t0 = time.perf_counter()
+    oracle.register(p.X, p.Y, grid, P)
+    single = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.register_threads(p.X, p.Y, grid, P, threads)
+    multi = time.perf_counter() - t0
+    return {"value": len(grid) * len(p.X) / multi, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"the whole registration ({len(grid)} rotations), distance grid built inside; "
+                      f"{multi:.2f} s on {threads} threads, {single:.2f} s on one"}
+
+
+def tiny(args, ws, rank, local):
+    """The tiny configuration (256-point target, 128-point source, 4,608
+    rotations) in full on the GPU, beside the oracle's whole registration."""
+    import torch
+
+    from paper_2502_00115_b300 import build, capi, synth
+
+    torch.cuda.set_device(local)
+    build.build()
+    p = synth.tiny_problem(args.seed)
+    ctx = capi.Context(local)
+    t = ctx.create_target(p.Y, grid_cap=2 * p.tau)
+    pr = capi.make_params(metric=p.metric, epsilon=p.epsilon, tau=p.tau, t_half=p.t_half)
+    pb = ctx.problem(t, p.X, capi.hopf_grid(p.hopf_n), pr)
+    for _ in range(max(1, args.warmup)):
+        ctx.register(pb)
+    ts = []
+    for _ in range(max(1, args.steps)):
+        t0 = time.perf_counter()
+        ctx.register(pb)
+        ts.append(time.perf_counter() - t0)
+    ctx.close()
+    n_rot = 72 * p.hopf_n**3
+    gpu_s = statistics.median(ts)
+    line = {
+        "workload": "tiny", "metric": METRIC, "value": n_rot * len(p.X) / gpu_s, "unit": UNIT,
+        "ms_per_registration": 1e3 * gpu_s, "rotations": n_rot, "source_points": len(p.X),
+        "target_points": len(p.Y), "data": "synthetic",
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = tiny_cpu_baseline(p, os.cpu_count() or 1)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args.gpus)
@@ -651,6 +705,8 @@ def main():
         quality(args, ws, rank, local)
     elif args.workload == "sweep":
         sweep(args, ws, rank, local)
+    elif args.workload == "tiny":
+        tiny(args, ws, rank, local)
     else:
         ours(args, ws, rank, local)
 
