@@ -778,6 +778,10 @@ void launch_pass(dses_ctx* c, const std::vector<PassPart>& parts, int P) {
     rprefix.push_back(rprefix.back() + d.n_rot);
     hist = std::max(hist, pp.job->hist_bytes);
   }
+  int max_n = 1;
+  for (auto& pp : parts) max_n = std::max(max_n, pp.job->N);
+  const int src_bytes = pass_src_bytes(hist, max_n);
+  for (auto& d : descs) set_chunks(d, src_bytes);
   const size_t db = align256(sizeof(PassDesc) * descs.size()), pb = align256(sizeof(int) * prefix.size());
   DevMem m;
   m.alloc(db + 2 * pb + 256, s);
@@ -797,6 +801,7 @@ void launch_pass(dses_ctx* c, const std::vector<PassPart>& parts, int P) {
   L.tile_rot = tile;
   L.work_counter = (int*)(base + db + 2 * pb);
   L.hist_bytes = hist;
+  L.src_bytes = src_bytes;
   L.padded = 0;
   for (auto& pp : parts)
     for (int a = 0; a < 3; ++a) L.padded |= pp.job->Ep[a] != pp.job->E[a] ? 1 : 0;
@@ -959,6 +964,7 @@ int pick_p(dses_ctx* c, Job& j) {
     std::vector<PassDesc> d{make_desc(j, P, false)};
     d[0].rot = rot;
     d[0].n_rot = (int)slice;
+    set_chunks(d[0], pass_src_bytes(j.hist_bytes, j.N));
     const int tile = 1;
     std::vector<int> tp{0, (int)slice}, rp{0, (int)slice};
     DevMem m;
@@ -977,6 +983,7 @@ int pick_p(dses_ctx* c, Job& j) {
     L.tile_rot = tile;
     L.work_counter = (int*)(base + 3072);
     L.hist_bytes = j.hist_bytes;
+    L.src_bytes = pass_src_bytes(j.hist_bytes, j.N);
     L.padded = 0;
     for (int a = 0; a < 3; ++a) L.padded |= j.Ep[a] != j.E[a] ? 1 : 0;
     cudaEvent_t e0, e1;

@@ -57,6 +57,8 @@ struct PassDesc {
   int n_slabs;
   int hist_u16;          // 1: two 16-bit counters per 32-bit word
   int hist_lanes;        // 1: 32-bit counters, one copy per lane: word bin * 32 + lane
+  int chunk[2];          // sources staged per chunk: [0] plain (16 bytes each), [1]
+                         // packed (32 bytes each); equal chunks that fit the staging
   int sparse;            // culled vote: 0 no, 1 32-point groups, 2 paired 64-point
                          // groups (gbox / n_groups hold that mode's group boxes)
   // vote work decomposition per rotation: items = n_tchunks x n_sgroups
@@ -95,6 +97,7 @@ struct PassLaunch {
   int tile_rot;            // rotations per work item
   int* work_counter;       // device, zeroed before the launch
   int hist_bytes;          // histogram bytes of shared memory (max over problems)
+  int src_bytes;           // source staging bytes (>= kSrcChunk * 16, a multiple of 32)
   int padded;              // 1: some problem's layout is padded (E != Ev): the
                            // instance whose mode scan skips padding bins
 };
@@ -106,7 +109,20 @@ struct PassLaunch {
 cudaError_t launch_vote(const PassLaunch& L, int points_per_thread, int sparse, int grid_ctas, cudaStream_t s);
 // Kernel 2: inlier count M at t* and, on the fused path, grid score + argmin.
 cudaError_t launch_count(const PassLaunch& L, int total_rot, cudaStream_t s);
-int pass_smem_bytes(int hist_bytes);
+int pass_smem_bytes(int hist_bytes, int src_bytes);
+// Staging bytes for sources of up to n_src points next to a histogram of
+// hist_bytes: enough for all of them (32 bytes each) when shared memory
+// allows, at least kSrcChunk * 16.
+int pass_src_bytes(int hist_bytes, int n_src);
+// Equal chunks of the problem's sources that fit src_bytes of staging, plain
+// and packed (d.chunk).
+inline void set_chunks(PassDesc& d, int src_bytes) {
+  for (int k = 0; k < 2; ++k) {
+    const int cap = src_bytes / (k ? 32 : 16);
+    const int n = (d.N + cap - 1) / cap;
+    d.chunk[k] = (d.N + n - 1) / n;
+  }
+}
 
 // --- rotation grids (FP64 arithmetic, FP32 output) -------------------------
 cudaError_t launch_hopf_grid(int n, float* out, cudaStream_t s);

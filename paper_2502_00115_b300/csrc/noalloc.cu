@@ -136,6 +136,7 @@ extern "C" dses_status dses_vote_static(int device, void* cuda_stream, const flo
     d.Y = reinterpret_cast<const float4*>(base + kOffY);
     d.Yv = d.Y;
     d.N = N;
+    set_chunks(d, kSrcChunk * 16);
     d.M = M;
     d.rot = rot_dev;
     d.n_rot = (int)n_rot;
@@ -170,6 +171,7 @@ extern "C" dses_status dses_vote_static(int device, void* cuda_stream, const flo
     L.tile_rot = tile;
     L.work_counter = reinterpret_cast<int*>(base + kOffCounter);
     L.hist_bytes = hist_bytes;
+    L.src_bytes = kSrcChunk * 16;
     L.padded = 0;
     if (launch_vote(L, ppt, 0, std::max(1, std::min(sms, tiles)), s) != cudaSuccess) {
       cudaGetLastError();

@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <atomic>
 
 #include "kernels.cuh"
@@ -636,9 +637,10 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
           off1 = 0.5f - (float)d.lo[1];
           off2 = 0.5f - (float)d.lo[2];
         }
-        // the packed path stages 32 bytes per source: half as many per chunk
+        // the packed path stages 32 bytes per source; the sources are split
+        // into equal chunks that fit the staging region
         const bool packed = P >= 2 && centred && !(SPARSE == 1 && d.sparse);
-        const int chunk = packed ? kSrcChunk / 2 : kSrcChunk;
+        const int chunk = max(1, d.chunk[packed ? 1 : 0]);  // >= 1 whatever the descriptor holds
         for (int c0 = 0; c0 < d.N; c0 += chunk) {
           const int c1 = min(c0 + chunk, d.N);
           __syncthreads();  // previous chunk's readers are done
@@ -877,7 +879,7 @@ __global__ void __launch_bounds__(256) count_kernel(PassLaunch L) {
 
 template <int P, int SPARSE, bool PADDED>
 cudaError_t launch_vote_p(const PassLaunch& L, int grid_ctas, cudaStream_t s) {
-  const int smem = pass_smem_bytes(L.hist_bytes);
+  const int smem = pass_smem_bytes(L.hist_bytes, L.src_bytes);
   static int configured = 0;
   if (configured < smem) {
     cudaError_t e =
@@ -919,7 +921,13 @@ cudaError_t launch_vote_padded(const PassLaunch& L, int points_per_thread, int s
 
 }  // namespace
 
-int pass_smem_bytes(int hist_bytes) { return hist_bytes + kSrcChunk * (int)sizeof(float4); }
+int pass_smem_bytes(int hist_bytes, int src_bytes) { return hist_bytes + src_bytes; }
+
+int pass_src_bytes(int hist_bytes, int n_src) {
+  const int room = (kMaxSmem - kPassStaticSmem - hist_bytes) & ~31;
+  const long long want = 32LL * n_src;
+  return (int)std::max<long long>(kSrcChunk * 16, std::min<long long>(want, room));
+}
 
 cudaError_t launch_vote(const PassLaunch& L, int points_per_thread, int sparse, int grid_ctas, cudaStream_t s) {
   return L.padded ? launch_vote_padded<true>(L, points_per_thread, sparse, grid_ctas, s)
