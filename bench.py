@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--points-per-thread", type=int, default=0, help="vote launch shape (0: library default)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["modelnet_like", "batched", "serving", "robot_like", "quality", "sweep", "tiny"],
+    ap.add_argument("--workload", choices=["modelnet_like", "batched", "serving", "robot_like", "robot_local", "quality", "sweep", "tiny"],
                     default="modelnet_like",
                     help="modelnet_like: the benchmark line; batched / serving: the other configurations")
     ap.add_argument("--batch-count", type=int, default=64)
@@ -635,6 +635,52 @@ def sweep(args, ws, rank, local):
                       "source_points": len(p.X), "target_points": len(p.Y), "points": rows}), flush=True)
 
 
+def robot_local(args, ws, rank, local):
+    """The paper's robot-experiment search ranges (local search of +-5 deg and
+    +-1.6 cm around a prior pose) on the synthetic robot-like clouds: Euler box
+    of 0.5 deg steps (21^3 rotations) around a prior 2.7 deg and 5.4 mm off
+    the true pose, 3 mm lattice."""
+    import torch
+
+    from paper_2502_00115_b300 import build, capi, synth
+
+    torch.cuda.set_device(local)
+    build.build()
+    p = synth.robot_like_problem(args.seed, hopf_n=2, refine_top_k=0)
+    ctx = capi.Context(local)
+    ctx.set_option("record_timing", 1)
+    t = ctx.create_target(p.Y, grid_cap=p.grid_cap)
+    a, b, c = np.radians([2.0, -1.5, 1.0])
+    Rz = np.array([[math.cos(a), -math.sin(a), 0], [math.sin(a), math.cos(a), 0], [0, 0, 1]])
+    Ry = np.array([[math.cos(b), 0, math.sin(b)], [0, 1, 0], [-math.sin(b), 0, math.cos(b)]])
+    Rx = np.array([[1, 0, 0], [0, math.cos(c), -math.sin(c)], [0, math.sin(c), math.cos(c)]])
+    R0 = np.asarray(p.R_true) @ Rz @ Ry @ Rx
+    t0 = tuple(float(v) for v in np.asarray(p.t_true) + np.array([0.004, -0.003, 0.002]))
+    K, step = 10, math.radians(0.5)
+    pr = capi.make_params(metric=p.metric, epsilon=p.epsilon, delta_t=p.delta_t, tau=p.tau, huber_h=p.huber_h,
+                          t_center=t0, t_half=(0.016, 0.016, 0.016))
+    pb = ctx.problem(t, p.X, capi.euler_box_grid(R0, K, step), pr)
+    for _ in range(max(1, args.warmup)):
+        ctx.register(pb)
+    ts, vote = [], []
+    for _ in range(max(1, args.steps)):
+        t1 = time.perf_counter()
+        r = capi.result_dict(ctx.register(pb))
+        ts.append(time.perf_counter() - t1)
+        vote.append(ctx.get_option("last_pass_ns") / 1e6)
+    modes = {"culled": ctx.get_option("last_vote_sparse"), "paired": ctx.get_option("last_vote_paired")}
+    ctx.close()
+    n_rot = (2 * K + 1) ** 3
+    e = pose_errors(r["R"], r["t"], p.R_true, p.t_true)
+    print(json.dumps({
+        "workload": "robot_local", "metric": METRIC, "value": n_rot * len(p.X) / statistics.median(ts),
+        "unit": UNIT, "ms_per_registration": 1e3 * statistics.median(ts), "vote_ms": statistics.median(vote),
+        "rotations": n_rot, "source_points": len(p.X), "target_points": len(p.Y),
+        "search": "+-5 deg (Euler box, 0.5 deg) x +-1.6 cm (3 mm lattice)", "vote_modes": modes,
+        "rotation_error_deg": e["mie_r"], "translation_error_m": e["mie_t"], "data": "synthetic",
+    }), flush=True)
+
+
 def tiny_cpu_baseline(p, threads):
     """cpu_baseline leg of the tiny workload: the FP64 oracle's whole
     registration of the same problem, single-threaded and on every host core."""
@@ -707,6 +753,8 @@ def main():
         sweep(args, ws, rank, local)
     elif args.workload == "tiny":
         tiny(args, ws, rank, local)
+    elif args.workload == "robot_local":
+        robot_local(args, ws, rank, local)
     else:
         ours(args, ws, rank, local)
 
