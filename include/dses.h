@@ -227,8 +227,8 @@ dses_status dses_exhaustive_search(dses_ctx* ctx, const dses_problem* problem, f
 
 /* Tuning and engine options (key = value). Keys:
  *   "hist_mode"            0 auto, 1 force 32-bit counters, 2 force packed 16-bit,
- *                          3 force lane-private 32-bit counters (a copy of every
- *                          bin per lane, for small boxes: 128 bytes per bin)
+ *                          3 lane-private 32-bit counters (a copy of every bin
+ *                          per lane, 128 bytes per bin; never chosen by 0)
  *   "hist_budget_bytes"    shared-memory bytes for the vote histogram (slabs below it)
  *   "points_per_thread"    0 auto, or 1, 2, 4, 8 target points held per lane
  *                          (a problem on the culled vote uses 4 for 8)

@@ -538,13 +538,14 @@ void plan(dses_ctx* c, Job& j) {
   const int64_t hb = u16 ? ((bins + 1) / 2) * 4 : bins * 4;
   j.hist_bytes = (int)((hb + 15) & ~15LL);
   j.lanes = 0;
-  // Small boxes: one 32-bit copy of every bin per lane (word bin * 32 + lane,
-  // so a warp's increments never share a bank). Auto when the copies fit and a
-  // rotation's pair votes outnumber the words its scan reads 16 to 1.
+  // One 32-bit copy of every bin per lane (word bin * 32 + lane, so a warp's
+  // increments never share a bank), on request only: measured slower than
+  // shared 32-bit counters on every small box tried (dense 9^3: 13.2 vs
+  // 12.4 ms; culled ModelNet-shaped and robot boxes: 1-13%), the scan of
+  // 32 copies per bin costing more than the bank conflicts it removes.
   const int64_t all = (Ex | 1) * Ey * Ez;
   const bool lanes_fit = all * 128 + 8 <= budget;
-  const bool lanes = c->opt.hist_mode == 3 ||
-                     (c->opt.hist_mode == 0 && lanes_fit && (int64_t)j.N * M >= 16 * 32 * all);
+  const bool lanes = c->opt.hist_mode == 3;
   if (lanes) {
     if (!lanes_fit) invalid("lane-private counters need 128 bytes per lattice bin within the histogram budget");
     j.u16 = 0;
@@ -565,14 +566,15 @@ void plan(dses_ctx* c, Job& j) {
     keep *= ext > 0 ? std::min(1.0, win / ext) : 1.0;
   }
   const bool cull = c->opt.vote_sparse >= 2 || (c->opt.vote_sparse == 0 && keep < 0.35);
-  // paired 64-point groups when the window is at least 1.5 group extents wide
-  // on every axis (each kept source then votes 64 targets in one packed step;
-  // robot-like: 2.2, the 32-point groups win below ~1 on ModelNet-shaped
-  // small boxes)
+  // paired 64-point groups when the window is at least 0.6 mean group extents
+  // wide on every axis (each kept source then votes 64 targets in one packed
+  // step). Measured: paired faster at 0.73 (robot search ranges, 11%) and 2.2
+  // (robot-like, 9%); 32-point groups faster at 0.14-0.5 (ModelNet-shaped
+  // small boxes, 8-10%).
   double span = 1e300;
   for (int a = 0; a < 3; ++a)
     span = std::min(span, (double)j.E[a] * j.delta / std::max(1e-12, (double)j.T->gext2[a]));
-  j.sparse = !cull ? 0 : c->opt.vote_sparse == 2 ? 1 : c->opt.vote_sparse == 3 ? 2 : (span >= 1.5 ? 2 : 1);
+  j.sparse = !cull ? 0 : c->opt.vote_sparse == 2 ? 1 : c->opt.vote_sparse == 3 ? 2 : (span >= 0.6 ? 2 : 1);
 }
 
 int choose_p(dses_ctx* c, const std::vector<Job*>& jobs) {

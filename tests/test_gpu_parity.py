@@ -188,10 +188,10 @@ def test_histogram_modes_and_launch_shapes_agree(ctx):
 
 def test_small_box_lane_private_counters(ctx):
     # a translation box of a few thousand bins (a local search around a prior):
-    # lane-private counters (auto here: the pair votes outnumber the scanned
-    # words) against the oracle on every rotation, and bit-identical to shared
-    # 32-bit counters under every vote path: packed (odd extents), scalar
-    # (1 point per lane), generic (an even extent) and culled
+    # the planner's choice against the oracle on sampled rotations, and
+    # lane-private counters (hist_mode 3) bit-identical to shared 32-bit
+    # counters under every vote path: packed, scalar (1 point per lane),
+    # culled and paired culled, odd and padded (even-extent) layouts
     p = synth.modelnet_like_problem(7, hopf_n=2)
     centre = tuple(float(v) for v in np.round(np.asarray(p.t_true) / 0.04) * 0.04)
     t = ctx.create_target(p.Y, grid_cap=2 * p.tau)
