@@ -174,6 +174,18 @@ __global__ void __launch_bounds__(256) dist_grid_kernel(const float4* __restrict
   if (v < total) D[v] = fminf(cap, sqrtf(best));
 }
 
+__global__ void pack_corners_kernel(const float* __restrict__ D, int G, float4* __restrict__ D4) {
+  const long long total = (long long)G * G * G;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < total;
+       v += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(v / ((long long)G * G)), b = (int)((v / G) % G), c = (int)(v % G);
+    const int b1 = min(b + 1, G - 1), c1 = min(c + 1, G - 1);
+    const float* row0 = D + ((size_t)a * G + b) * G;
+    const float* row1 = D + ((size_t)a * G + b1) * G;
+    D4[v] = make_float4(row0[c], row0[c1], row1[c], row1[c1]);
+  }
+}
+
 __device__ __forceinline__ int cell_of(float p, float lo, float inv, int dim) {
   const float f = floorf((p - lo) * inv);
   return (int)fminf(fmaxf(f, 0.f), (float)(dim - 1));
@@ -305,12 +317,12 @@ __device__ __forceinline__ float grid_lookup_s(const ScoreDesc& d, float qx, flo
   gz = fminf(fmaxf(gz - 0.5f, 0.f), G - 1.f);
   const int ix = min((int)gx, d.G - 2), iy = min((int)gy, d.G - 2), iz = min((int)gz, d.G - 2);
   const float fx = gx - (float)ix, fy = gy - (float)iy, fz = gz - (float)iz;
-  const float* b = d.D + ((size_t)ix * d.G + iy) * d.G + iz;
-  const size_t sy = d.G, sx = (size_t)d.G * d.G;
-  const float c00 = b[0] + fz * (b[1] - b[0]);
-  const float c01 = b[sy] + fz * (b[sy + 1] - b[sy]);
-  const float c10 = b[sx] + fz * (b[sx + 1] - b[sx]);
-  const float c11 = b[sx + sy] + fz * (b[sx + sy + 1] - b[sx + sy]);
+  const float4* b = d.D4 + ((size_t)ix * d.G + iy) * d.G + iz;
+  const float4 p = __ldg(b), q = __ldg(b + (size_t)d.G * d.G);  // x = ix and ix + 1
+  const float c00 = p.x + fz * (p.y - p.x);
+  const float c01 = p.z + fz * (p.w - p.z);
+  const float c10 = q.x + fz * (q.y - q.x);
+  const float c11 = q.z + fz * (q.w - q.z);
   const float c0 = c00 + fy * (c01 - c00);
   const float c1 = c10 + fy * (c11 - c10);
   return c0 + fx * (c1 - c0);
@@ -534,10 +546,11 @@ cudaError_t launch_pack_points(const float* xyz, int m, float4* out, cudaStream_
 }
 
 cudaError_t launch_dist_grid(const float4* Y, int m, int G, const float* lo, const float* h, float cap, float* D,
-                             cudaStream_t s) {
+                             float4* D4, cudaStream_t s) {
   const long long total = (long long)G * G * G;
-  g_launches.fetch_add(1, std::memory_order_relaxed);
+  g_launches.fetch_add(2, std::memory_order_relaxed);
   dist_grid_kernel<<<blocks_for(total, 256), 256, 0, s>>>(Y, m, G, lo[0], lo[1], lo[2], h[0], h[1], h[2], cap, D);
+  pack_corners_kernel<<<(int)std::min<long long>(blocks_for(total, 256), 148 * 16), 256, 0, s>>>(D, G, D4);
   return cudaGetLastError();
 }
 

@@ -135,6 +135,7 @@ struct dses_target {
   int n_groups2 = 0;
   float gext2[3] = {0, 0, 0};
   float* D = nullptr;       // G^3 distance grid
+  float4* D4 = nullptr;     // its 2 x 2 (y, z) corner blocks, one per voxel
   int G = 0;
   float glo[3], gh[3], gcap = 0;
   std::map<uint32_t, CellList> cells;  // by bit pattern of epsilon
@@ -728,6 +729,7 @@ PassDesc make_desc(const Job& j, int P, bool second) {
   d.huber_h = j.hh;
   d.p_exp = j.pexp;
   d.D = j.T->D;
+  d.D4 = j.T->D4;
   d.G = j.T->G;
   d.gcap = j.T->gcap;
   {
@@ -847,6 +849,7 @@ ScoreDesc make_score(const Job& j, bool second) {
   d.huber_h = j.hh;
   d.p_exp = j.pexp;
   d.D = j.T->D;
+  d.D4 = j.T->D4;
   d.G = j.T->G;
   for (int a = 0; a < 3; ++a) {
     d.glo[a] = j.T->glo[a];
@@ -1467,6 +1470,7 @@ static void free_target(dses_target* T) {
   if (T->gbox) cudaFree(T->gbox);
   if (T->gbox2) cudaFree(T->gbox2);
   if (T->D) cudaFree(T->D);
+  if (T->D4) cudaFree(T->D4);
   for (auto& kv : T->cells) {
     cudaFree(kv.second.start);
     cudaFree(kv.second.sorted);
@@ -1541,7 +1545,8 @@ dses_status dses_create_target(dses_ctx* c, const float* xyz, int64_t m, int32_t
     }
     build_morton_groups(c, T.get());
     CK(cudaMalloc(&T->D, sizeof(float) * (size_t)G * G * G));
-    CK(launch_dist_grid(T->Y, (int)m, G, T->glo, T->gh, grid_cap, T->D, c->stream));
+    CK(cudaMalloc(&T->D4, sizeof(float4) * (size_t)G * G * G));
+    CK(launch_dist_grid(T->Y, (int)m, G, T->glo, T->gh, grid_cap, T->D, T->D4, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     c->targets.push_back(T.get());
     *out = T.release();

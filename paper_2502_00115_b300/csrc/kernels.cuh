@@ -75,6 +75,7 @@ struct PassDesc {
   int metric;            // dses_metric
   float eps, tau, huber_h, p_exp;
   const float* D;        // G^3 truncated distance grid
+  const float4* D4;      // per voxel its (y, z) 2 x 2 corner block (see launch_dist_grid)
   int G;
   float glo[3], ginv_h[3], gcap;
   float grid_err;        // FP32 margin of the distance bounds from the grid
@@ -140,8 +141,11 @@ cudaError_t launch_euler_box_single(const double* R0_dev, int K, double delta_r,
 
 // --- target preprocessing ---------------------------------------------------
 cudaError_t launch_pack_points(const float* xyz, int m, float4* out, cudaStream_t s);
+// D: G^3 truncated distances (x-major); D4[v] for voxel v = (a, b, c) holds
+// D at (a, b, c), (a, b, c+1), (a, b+1, c), (a, b+1, c+1) (indices clamped at
+// G - 1), so a trilinear lookup reads its 8 corners as two 16-byte loads.
 cudaError_t launch_dist_grid(const float4* Y, int m, int G, const float* lo, const float* h, float cap, float* D,
-                             cudaStream_t s);
+                             float4* D4, cudaStream_t s);
 // cell list: counts -> prefix -> scatter. counts: ncells ints; scratch: ncells + m ints.
 cudaError_t launch_cell_list(const float4* Y, int m, const float* cell_lo, float cell_inv, const int* dim,
                              int* counts, int* cell_start, int* scratch, float4* sorted, cudaStream_t s);
@@ -156,6 +160,7 @@ struct ScoreDesc {
   int metric;
   float eps, tau, huber_h, p_exp;
   const float* D;
+  const float4* D4;
   int G;
   float glo[3], ginv_h[3], gcap;
   const int4* kv;         // per-rotation outputs, indexed by global index - out_base

@@ -73,11 +73,10 @@ __device__ __forceinline__ float grid_lookup_decide(const PassDesc& d, float qx,
   const float gz = fminf(fmaxf(uz - 0.5f, 0.f), G - 1.f);
   const int ix = min((int)gx, d.G - 2), iy = min((int)gy, d.G - 2), iz = min((int)gz, d.G - 2);
   const float fx = gx - (float)ix, fy = gy - (float)iy, fz = gz - (float)iz;
-  const float* b = d.D + ((size_t)ix * d.G + iy) * d.G + iz;
-  const size_t sy = d.G, sx = (size_t)d.G * d.G;
-  float v[8];
-  v[0] = __ldg(b); v[1] = __ldg(b + 1); v[2] = __ldg(b + sy); v[3] = __ldg(b + sy + 1);
-  v[4] = __ldg(b + sx); v[5] = __ldg(b + sx + 1); v[6] = __ldg(b + sx + sy); v[7] = __ldg(b + sx + sy + 1);
+  // the 8 corners as two 16-byte loads of the corner-block grid
+  const float4* b = d.D4 + ((size_t)ix * d.G + iy) * d.G + iz;
+  const float4 p = __ldg(b), q = __ldg(b + (size_t)d.G * d.G);
+  const float v[8] = {p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w};
   // q - corner per axis, in world units (corner i at lo + (i + 1/2) h)
   const float h0 = 1.f / d.ginv_h[0], h1 = 1.f / d.ginv_h[1], h2 = 1.f / d.ginv_h[2];
   const float dx0 = (ux - 0.5f - (float)ix) * h0, dy0 = (uy - 0.5f - (float)iy) * h1, dz0 = (uz - 0.5f - (float)iz) * h2;
@@ -143,21 +142,51 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
   return v;
 }
 
+// Two 16-bit counters per word: their lane-wise maximum, and acc plus both.
+__device__ __forceinline__ uint32_t max_u16x2(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+__device__ __forceinline__ uint32_t add_halves(uint32_t v, uint32_t acc) {
+  uint32_t d;  // acc + lo16(v) * 1 + hi16(v) * 1
+  asm("dp2a.lo.u32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(v), "r"(0x0101u), "r"(acc));
+  return d;
+}
+// Maximum over the block (one value per warp in red[32]; every thread gets it).
+__device__ __forceinline__ unsigned block_max_u32(unsigned v, unsigned* red, int lane, int warp) {
+  v = __reduce_max_sync(0xffffffffu, v);
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  return __reduce_max_sync(0xffffffffu, red[lane]);
+}
+
 // Shared-memory histogram increment of a pair whose box-relative lattice
 // coordinates are w (inside the centred box iff |w_a| < h_a on all three axes),
 // made unconditional: a pair outside the box adds to `sink` (a word outside
 // the histogram) instead, so no branch wraps the atomic.
+template <bool CUBE = false>
 __device__ __forceinline__ void red_or_sink(uint32_t addr, uint32_t inc, uint32_t sink, float wx, float wy,
                                             float wz, float hx, float hy, float hz) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t.reg .f32 ax, ay, az;\n\t.reg .b32 a;\n\t"
-      "abs.f32 ax, %3;\n\tabs.f32 ay, %4;\n\tabs.f32 az, %5;\n\t"
-      "setp.lt.f32 p, ax, %6;\n\t"
-      "setp.lt.and.f32 p, ay, %7, p;\n\t"
-      "setp.lt.and.f32 p, az, %8, p;\n\t"
-      "selp.b32 a, %0, %2, p;\n\t"
-      "red.shared.add.u32 [a], %1;\n\t}" ::"r"(addr),
-      "r"(inc), "r"(sink), "f"(wx), "f"(wy), "f"(wz), "f"(hx), "f"(hy), "f"(hz));
+  if (CUBE)  // one half-width: max(|w_x|, |w_y|, |w_z|) < h
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t.reg .f32 ax, ay, az;\n\t.reg .b32 a;\n\t"
+        "abs.f32 ax, %3;\n\tabs.f32 ay, %4;\n\tabs.f32 az, %5;\n\t"
+        "max.f32 ax, ax, ay, az;\n\t"
+        "setp.lt.f32 p, ax, %6;\n\t"
+        "selp.b32 a, %0, %2, p;\n\t"
+        "red.shared.add.u32 [a], %1;\n\t}" ::"r"(addr),
+        "r"(inc), "r"(sink), "f"(wx), "f"(wy), "f"(wz), "f"(hx));
+  else
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t.reg .f32 ax, ay, az;\n\t.reg .b32 a;\n\t"
+        "abs.f32 ax, %3;\n\tabs.f32 ay, %4;\n\tabs.f32 az, %5;\n\t"
+        "setp.lt.f32 p, ax, %6;\n\t"
+        "setp.lt.and.f32 p, ay, %7, p;\n\t"
+        "setp.lt.and.f32 p, az, %8, p;\n\t"
+        "selp.b32 a, %0, %2, p;\n\t"
+        "red.shared.add.u32 [a], %1;\n\t}" ::"r"(addr),
+        "r"(inc), "r"(sink), "f"(wx), "f"(wy), "f"(wz), "f"(hx), "f"(hy), "f"(hz));
 }
 
 // Next vote item of this CTA (dynamic balance across warps).
@@ -236,66 +265,70 @@ __device__ __forceinline__ void vote_centred(const PassDesc& d, const float4* __
   }
 }
 
-// Dense centred path on packed FP32 pairs (fma.rn.f32x2 / add.rn.f32x2): a
-// lane's targets are held two by two per axis and each source offset is staged
-// duplicated, so one packed op computes the lattice coordinate (or its
-// rounding) of one source against two targets. Same per-pair arithmetic and
-// box test as vote_centred; the histogram increment is unconditional, with the
-// address selected by the box test (a pair outside the box adds to a per-lane
-// sink word that is never read), which keeps the loop free of branches around
-// the atomic.
-template <bool U16>
+// The three steps shared by every form: w = y / delta + c (packed FMA), the
+// magic-number rounding of w (packed add) and the lattice index t of both
+// pairs. Box test: |w_a| < h_a on every axis, either per axis (three chained
+// compares) or, when the padded box is a cube, as max(|w_x|, |w_y|, |w_z|) < h
+// (one three-input max and one compare).
+#define DSES_VOTE2_HEAD                                                                          \
+  "{\n\t.reg .b64 wx, wy, wz, fx, fy, fz;\n\t"                                                   \
+  ".reg .b32 bx0, bx1, by0, by1, bz0, bz1, t0, t1, a0, a1, i0, i1, u0, u1, v0, v1, s0, s1;\n\t"  \
+  ".reg .f32 x0, x1, y0, y1, z0, z1;\n\t.reg .pred p0, p1;\n\t"                                  \
+  "fma.rn.f32x2 wx, %0, %3, %4;\n\tfma.rn.f32x2 wy, %1, %3, %5;\n\tfma.rn.f32x2 wz, %2, %3, %6;\n\t" \
+  "add.rn.f32x2 fx, wx, %7;\n\tadd.rn.f32x2 fy, wy, %8;\n\tadd.rn.f32x2 fz, wz, %9;\n\t"         \
+  "mov.b64 {bx0, bx1}, fx;\n\tmov.b64 {by0, by1}, fy;\n\tmov.b64 {bz0, bz1}, fz;\n\t"
+// 16-bit counters: word t >> 1, half t & 1 (increment 1 or 65536)
+#define DSES_VOTE2_ADDR16                                                   \
+  "mad.lo.u32 t0, by0, %11, bz0;\n\tmad.lo.u32 t0, bx0, %10, t0;\n\t"      \
+  "mad.lo.u32 t1, by1, %11, bz1;\n\tmad.lo.u32 t1, bx1, %10, t1;\n\t"      \
+  "shr.u32 a0, t0, 1;\n\tshr.u32 a1, t1, 1;\n\t"                           \
+  "mad.lo.u32 a0, a0, 4, %12;\n\tmad.lo.u32 a1, a1, 4, %12;\n\t"           \
+  "and.b32 i0, t0, 1;\n\tand.b32 i1, t1, 1;\n\t"                           \
+  "mad.lo.u32 i0, i0, 65535, 1;\n\tmad.lo.u32 i1, i1, 65535, 1;\n\t"
+// 32-bit counters: strides %10 / %11 already scaled by the word stride %17
+#define DSES_VOTE2_ADDR32                                                                            \
+  "mad.lo.u32 t0, bz0, %17, %12;\n\tmad.lo.u32 t0, by0, %11, t0;\n\tmad.lo.u32 a0, bx0, %10, t0;\n\t" \
+  "mad.lo.u32 t1, bz1, %17, %12;\n\tmad.lo.u32 t1, by1, %11, t1;\n\tmad.lo.u32 a1, bx1, %10, t1;\n\t"
+#define DSES_VOTE2_ABS                                                                      \
+  "mov.b64 {u0, u1}, wx;\n\tmov.b64 {v0, v1}, wy;\n\tmov.b64 {s0, s1}, wz;\n\t"             \
+  "mov.b32 x0, u0;\n\tmov.b32 x1, u1;\n\tmov.b32 y0, v0;\n\tmov.b32 y1, v1;\n\t"           \
+  "mov.b32 z0, s0;\n\tmov.b32 z1, s1;\n\t"                                                  \
+  "abs.f32 x0, x0;\n\tabs.f32 x1, x1;\n\tabs.f32 y0, y0;\n\tabs.f32 y1, y1;\n\t"           \
+  "abs.f32 z0, z0;\n\tabs.f32 z1, z1;\n\t"
+#define DSES_VOTE2_TEST_AXES                                                                          \
+  "setp.lt.f32 p0, x0, %13;\n\tsetp.lt.and.f32 p0, y0, %14, p0;\n\tsetp.lt.and.f32 p0, z0, %15, p0;\n\t" \
+  "setp.lt.f32 p1, x1, %13;\n\tsetp.lt.and.f32 p1, y1, %14, p1;\n\tsetp.lt.and.f32 p1, z1, %15, p1;\n\t"
+#define DSES_VOTE2_TEST_CUBE                                                 \
+  "max.f32 x0, x0, y0, z0;\n\tmax.f32 x1, x1, y1, z1;\n\t"                   \
+  "setp.lt.f32 p0, x0, %13;\n\tsetp.lt.f32 p1, x1, %13;\n\t"
+// a pair outside the box adds to the lane's sink word %16
+#define DSES_VOTE2_RED16                                                     \
+  "selp.b32 a0, a0, %16, p0;\n\tselp.b32 a1, a1, %16, p1;\n\t"               \
+  "red.shared.add.u32 [a0], i0;\n\tred.shared.add.u32 [a1], i1;\n\t}"
+#define DSES_VOTE2_RED32                                                     \
+  "selp.b32 a0, a0, %16, p0;\n\tselp.b32 a1, a1, %16, p1;\n\t"               \
+  "red.shared.add.u32 [a0], 1;\n\tred.shared.add.u32 [a1], 1;\n\t}"
+
+// Two (source, target) pairs as packed FP32 pairs: lattice index, box test and
+// one unconditional shared add per pair.
+template <bool U16, bool CUBE>
 __device__ __forceinline__ void vote_two_pairs(uint64_t yx, uint64_t yy, uint64_t yz, uint64_t inv2, uint64_t cx2,
                                                uint64_t cy2, uint64_t cz2, uint64_t mx2, uint64_t my2, uint64_t mz2,
                                                uint32_t Eyz, uint32_t Ez, uint32_t abase, float hx, float hy,
-                                               float hz, float hx1, uint32_t adummy, uint32_t unit) {
-  if (U16) {
-    asm volatile(
-        "{\n\t.reg .b64 wx, wy, wz, fx, fy, fz;\n\t"
-        ".reg .b32 bx0, bx1, by0, by1, bz0, bz1, t0, t1, a0, a1, i0, i1, u0, u1, v0, v1, s0, s1;\n\t"
-        ".reg .f32 x0, x1, y0, y1, z0, z1;\n\t.reg .pred p0, p1;\n\t"
-        "fma.rn.f32x2 wx, %0, %3, %4;\n\tfma.rn.f32x2 wy, %1, %3, %5;\n\tfma.rn.f32x2 wz, %2, %3, %6;\n\t"
-        "add.rn.f32x2 fx, wx, %7;\n\tadd.rn.f32x2 fy, wy, %8;\n\tadd.rn.f32x2 fz, wz, %9;\n\t"
-        "mov.b64 {bx0, bx1}, fx;\n\tmov.b64 {by0, by1}, fy;\n\tmov.b64 {bz0, bz1}, fz;\n\t"
-        "mad.lo.u32 t0, by0, %11, bz0;\n\tmad.lo.u32 t0, bx0, %10, t0;\n\t"
-        "mad.lo.u32 t1, by1, %11, bz1;\n\tmad.lo.u32 t1, bx1, %10, t1;\n\t"
-        "shr.u32 a0, t0, 1;\n\tshr.u32 a1, t1, 1;\n\t"
-        "mad.lo.u32 a0, a0, 4, %12;\n\tmad.lo.u32 a1, a1, 4, %12;\n\t"
-        "and.b32 i0, t0, 1;\n\tand.b32 i1, t1, 1;\n\t"
-        "mad.lo.u32 i0, i0, 65535, 1;\n\tmad.lo.u32 i1, i1, 65535, 1;\n\t"
-        "mov.b64 {u0, u1}, wx;\n\tmov.b64 {v0, v1}, wy;\n\tmov.b64 {s0, s1}, wz;\n\t"
-        "mov.b32 x0, u0;\n\tmov.b32 x1, u1;\n\tmov.b32 y0, v0;\n\tmov.b32 y1, v1;\n\t"
-        "mov.b32 z0, s0;\n\tmov.b32 z1, s1;\n\t"
-        "abs.f32 x0, x0;\n\tabs.f32 x1, x1;\n\tabs.f32 y0, y0;\n\tabs.f32 y1, y1;\n\t"
-        "abs.f32 z0, z0;\n\tabs.f32 z1, z1;\n\t"
-        "setp.lt.f32 p0, x0, %13;\n\tsetp.lt.and.f32 p0, y0, %14, p0;\n\tsetp.lt.and.f32 p0, z0, %15, p0;\n\t"
-        "setp.lt.f32 p1, x1, %16;\n\tsetp.lt.and.f32 p1, y1, %14, p1;\n\tsetp.lt.and.f32 p1, z1, %15, p1;\n\t"
-        "selp.b32 a0, a0, %17, p0;\n\tselp.b32 a1, a1, %17, p1;\n\t"
-        "red.shared.add.u32 [a0], i0;\n\tred.shared.add.u32 [a1], i1;\n\t}" ::"l"(yx),
-        "l"(yy), "l"(yz), "l"(inv2), "l"(cx2), "l"(cy2), "l"(cz2), "l"(mx2), "l"(my2), "l"(mz2), "r"(Eyz), "r"(Ez),
-        "r"(abase), "f"(hx), "f"(hy), "f"(hz), "f"(hx1), "r"(adummy), "r"(unit));
-  } else {
-    asm volatile(
-        "{\n\t.reg .b64 wx, wy, wz, fx, fy, fz;\n\t"
-        ".reg .b32 bx0, bx1, by0, by1, bz0, bz1, t0, t1, a0, a1, u0, u1, v0, v1, s0, s1;\n\t"
-        ".reg .f32 x0, x1, y0, y1, z0, z1;\n\t.reg .pred p0, p1;\n\t"
-        "fma.rn.f32x2 wx, %0, %3, %4;\n\tfma.rn.f32x2 wy, %1, %3, %5;\n\tfma.rn.f32x2 wz, %2, %3, %6;\n\t"
-        "add.rn.f32x2 fx, wx, %7;\n\tadd.rn.f32x2 fy, wy, %8;\n\tadd.rn.f32x2 fz, wz, %9;\n\t"
-        "mov.b64 {bx0, bx1}, fx;\n\tmov.b64 {by0, by1}, fy;\n\tmov.b64 {bz0, bz1}, fz;\n\t"
-        "mad.lo.u32 t0, bz0, %18, %12;\n\tmad.lo.u32 t0, by0, %11, t0;\n\tmad.lo.u32 a0, bx0, %10, t0;\n\t"
-        "mad.lo.u32 t1, bz1, %18, %12;\n\tmad.lo.u32 t1, by1, %11, t1;\n\tmad.lo.u32 a1, bx1, %10, t1;\n\t"
-        "mov.b64 {u0, u1}, wx;\n\tmov.b64 {v0, v1}, wy;\n\tmov.b64 {s0, s1}, wz;\n\t"
-        "mov.b32 x0, u0;\n\tmov.b32 x1, u1;\n\tmov.b32 y0, v0;\n\tmov.b32 y1, v1;\n\t"
-        "mov.b32 z0, s0;\n\tmov.b32 z1, s1;\n\t"
-        "abs.f32 x0, x0;\n\tabs.f32 x1, x1;\n\tabs.f32 y0, y0;\n\tabs.f32 y1, y1;\n\t"
-        "abs.f32 z0, z0;\n\tabs.f32 z1, z1;\n\t"
-        "setp.lt.f32 p0, x0, %13;\n\tsetp.lt.and.f32 p0, y0, %14, p0;\n\tsetp.lt.and.f32 p0, z0, %15, p0;\n\t"
-        "setp.lt.f32 p1, x1, %16;\n\tsetp.lt.and.f32 p1, y1, %14, p1;\n\tsetp.lt.and.f32 p1, z1, %15, p1;\n\t"
-        "selp.b32 a0, a0, %17, p0;\n\tselp.b32 a1, a1, %17, p1;\n\t"
-        "red.shared.add.u32 [a0], 1;\n\tred.shared.add.u32 [a1], 1;\n\t}" ::"l"(yx),
-        "l"(yy), "l"(yz), "l"(inv2), "l"(cx2), "l"(cy2), "l"(cz2), "l"(mx2), "l"(my2), "l"(mz2), "r"(Eyz * unit),
-        "r"(Ez * unit), "r"(abase), "f"(hx), "f"(hy), "f"(hz), "f"(hx1), "r"(adummy), "r"(unit));
-  }
+                                               float hz, uint32_t adummy, uint32_t unit) {
+  const uint32_t sy = U16 ? Eyz : Eyz * unit, sz = U16 ? Ez : Ez * unit;
+#define DSES_VOTE2_ARGS                                                                                         \
+  ::"l"(yx), "l"(yy), "l"(yz), "l"(inv2), "l"(cx2), "l"(cy2), "l"(cz2), "l"(mx2), "l"(my2), "l"(mz2), "r"(sy), \
+      "r"(sz), "r"(abase), "f"(hx), "f"(hy), "f"(hz), "r"(adummy), "r"(unit)
+  if (U16 && CUBE)
+    asm volatile(DSES_VOTE2_HEAD DSES_VOTE2_ADDR16 DSES_VOTE2_ABS DSES_VOTE2_TEST_CUBE DSES_VOTE2_RED16 DSES_VOTE2_ARGS);
+  else if (U16)
+    asm volatile(DSES_VOTE2_HEAD DSES_VOTE2_ADDR16 DSES_VOTE2_ABS DSES_VOTE2_TEST_AXES DSES_VOTE2_RED16 DSES_VOTE2_ARGS);
+  else if (CUBE)
+    asm volatile(DSES_VOTE2_HEAD DSES_VOTE2_ADDR32 DSES_VOTE2_ABS DSES_VOTE2_TEST_CUBE DSES_VOTE2_RED32 DSES_VOTE2_ARGS);
+  else
+    asm volatile(DSES_VOTE2_HEAD DSES_VOTE2_ADDR32 DSES_VOTE2_ABS DSES_VOTE2_TEST_AXES DSES_VOTE2_RED32 DSES_VOTE2_ARGS);
+#undef DSES_VOTE2_ARGS
 }
 
 __device__ __forceinline__ uint64_t pack2(float lo, float hi) {
@@ -304,7 +337,36 @@ __device__ __forceinline__ uint64_t pack2(float lo, float hi) {
 
 // Staged layout of source i: float4 [2i] holds (c_x, c_x, c_y, c_y), float4
 // [2i + 1] holds (c_z, c_z, 0, 0).
-template <int P, bool U16>
+// Sources [i0, i1) against a lane's Q target pairs (dense packed path).
+template <int Q, bool U16, bool CUBE>
+__device__ __forceinline__ void vote_sources_x2(const float4* __restrict__ srcd, int i0, int i1, const uint64_t* yx,
+                                                const uint64_t* yy, const uint64_t* yz, uint64_t inv2, uint64_t mx2,
+                                                uint64_t my2, uint64_t mz2, uint32_t Eyz, uint32_t Ez, uint32_t abase,
+                                                float hx, float hy, float hz, uint32_t adummy, uint32_t unit) {
+#pragma unroll 4
+  for (int i = i0; i < i1; ++i) {
+    const float4 ca = srcd[2 * i];
+    const float2 cb = *reinterpret_cast<const float2*>(srcd + 2 * i + 1);
+    const uint64_t cx2 = pack2(ca.x, ca.y), cy2 = pack2(ca.z, ca.w), cz2 = pack2(cb.x, cb.y);
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+      vote_two_pairs<U16, CUBE>(yx[q], yy[q], yz[q], inv2, cx2, cy2, cz2, mx2, my2, mz2, Eyz, Ez, abase, hx, hy, hz,
+                                adummy, unit);
+  }
+}
+
+// Dense centred path on packed FP32 pairs (fma.rn.f32x2 / add.rn.f32x2): a
+// lane's targets are held two by two per axis and each source offset is staged
+// duplicated, so one packed op computes the lattice coordinate (or its
+// rounding) of one source against two targets. Same per-pair arithmetic and
+// box test as vote_centred; the histogram increment is unconditional, with the
+// address selected by the box test (a pair outside the box adds to a per-lane
+// sink word that is never read), which keeps the loop free of branches around
+// the atomic. A cubic box takes the three-input-max test (DENSE_INST: only in
+// the dense kernel instances; the culled instances, which reach this path for
+// problems that are not culled, keep one form: their culled loops measured 1%
+// slower with both forms in the kernel).
+template <int P, bool U16, bool DENSE_INST>
 __device__ __forceinline__ void vote_centred_x2(const PassDesc& d, const float4* __restrict__ srcd, int nsrc,
                                                 unsigned SX, uint32_t hist_base, int* item_ctr, int lane,
                                                 uint32_t sink) {
@@ -315,6 +377,7 @@ __device__ __forceinline__ void vote_centred_x2(const PassDesc& d, const float4*
   const unsigned Ey = (unsigned)d.E[1], Ez = (unsigned)d.E[2], Eyz = Ey * Ez;
   const float inv = d.inv_delta;
   const float hx = 0.5f * (float)SX, hy = 0.5f * (float)Ey, hz = 0.5f * (float)Ez;
+  const bool cube = SX == Ey && Ey == Ez;  // one half-width for the three axes
   const float mx = kMagic + (float)((SX - 1) / 2), my = kMagic + (float)((Ey - 1) / 2),
               mz = kMagic + (float)((Ez - 1) / 2);
   const uint64_t inv2 = pack2(inv, inv), mx2 = pack2(mx, mx), my2 = pack2(my, my), mz2 = pack2(mz, mz);
@@ -338,16 +401,12 @@ __device__ __forceinline__ void vote_centred_x2(const PassDesc& d, const float4*
       yz[q] = pack2(ty[2 * q][2], ty[2 * q + 1][2]);
     }
     const int i0 = sg * spg, i1 = min(i0 + spg, nsrc);
-#pragma unroll 4
-    for (int i = i0; i < i1; ++i) {
-      const float4 ca = srcd[2 * i];
-      const float2 cb = *reinterpret_cast<const float2*>(srcd + 2 * i + 1);
-      const uint64_t cx2 = pack2(ca.x, ca.y), cy2 = pack2(ca.z, ca.w), cz2 = pack2(cb.x, cb.y);
-#pragma unroll
-      for (int q = 0; q < P / 2; ++q)
-        vote_two_pairs<U16>(yx[q], yy[q], yz[q], inv2, cx2, cy2, cz2, mx2, my2, mz2, Eyz, Ez, abase, hx, hy, hz, hx,
-                            adummy, unit);
-    }
+    if (DENSE_INST && cube)
+      vote_sources_x2<P / 2, U16, true>(srcd, i0, i1, yx, yy, yz, inv2, mx2, my2, mz2, Eyz, Ez, abase, hx, hy, hz,
+                                       adummy, unit);
+    else
+      vote_sources_x2<P / 2, U16, false>(srcd, i0, i1, yx, yy, yz, inv2, mx2, my2, mz2, Eyz, Ez, abase, hx, hy, hz,
+                                        adummy, unit);
   }
 }
 
@@ -360,7 +419,7 @@ __device__ __forceinline__ void vote_centred_x2(const PassDesc& d, const float4*
 // voted, one group at a time over the set bits of its ballot.
 constexpr float kCullMargin = 1e-3f;
 
-template <int P, bool U16>
+template <int P, bool U16, bool CUBE>
 __device__ __forceinline__ void vote_centred_sparse(const PassDesc& d, const float4* __restrict__ srcc, int nsrc,
                                                     unsigned SX, uint32_t hist_base, int* item_ctr, int lane,
                                                     float* __restrict__ thr, uint32_t sink) {
@@ -426,9 +485,9 @@ __device__ __forceinline__ void vote_centred_sparse(const PassDesc& d, const flo
           const uint32_t bz = __float_as_uint(__fadd_rn(wz, mz));
           if (U16) {
             const uint32_t b = bx * Eyz + (by * Ez + bz);
-            red_or_sink(abase16 + ((b >> 1) << 2), 1u + (b & 1u) * 0xffffu, sinkl, wx, wy, wz, hx, hy, hz);
+            red_or_sink<CUBE>(abase16 + ((b >> 1) << 2), 1u + (b & 1u) * 0xffffu, sinkl, wx, wy, wz, hx, hy, hz);
           } else {
-            red_or_sink(abase32 + bx * EyzU + (by * EzU + bz * unit), 1u, sinkl, wx, wy, wz, hx, hy, hz);
+            red_or_sink<CUBE>(abase32 + bx * EyzU + (by * EzU + bz * unit), 1u, sinkl, wx, wy, wz, hx, hy, hz);
           }
         }
       }
@@ -445,7 +504,10 @@ __device__ __forceinline__ void vote_centred_sparse(const PassDesc& d, const flo
 // kept source votes the group's 64 targets in one packed step. Against the
 // 32-point path this halves the iterations per kept target but keeps more
 // (source, group) pairs, so it pays only when the window is large against a
-// group. Sources are staged duplicated as for vote_centred_x2.
+// group. Sources are staged duplicated as for vote_centred_x2. The box test
+// stays per axis here even for a cube: the three-input max measured 8% slower
+// in this loop (an 11^3 box of 32-bit counters), where the dense and 32-point
+// paths gain 1-3% from it.
 template <int P, bool U16>
 __device__ __forceinline__ void vote_centred_paired(const PassDesc& d, const float4* __restrict__ srcd, int nsrc,
                                                     unsigned SX, uint32_t hist_base, int* item_ctr, int lane,
@@ -518,8 +580,8 @@ __device__ __forceinline__ void vote_centred_paired(const PassDesc& d, const flo
           m &= m - 1;
           const float4 ca = srcd[2 * j];
           const float2 cb = *reinterpret_cast<const float2*>(srcd + 2 * j + 1);
-          vote_two_pairs<U16>(yx[q], yy[q], yz[q], inv2, pack2(ca.x, ca.y), pack2(ca.z, ca.w), pack2(cb.x, cb.y),
-                              mx2, my2, mz2, Eyz, Ez, abase, hx, hy, hz, hx, adummy, unit);
+          vote_two_pairs<U16, false>(yx[q], yy[q], yz[q], inv2, pack2(ca.x, ca.y), pack2(ca.z, ca.w),
+                                     pack2(cb.x, cb.y), mx2, my2, mz2, Eyz, Ez, abase, hx, hy, hz, adummy, unit);
         }
       }
     }
@@ -571,6 +633,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ PassDesc sd;
   __shared__ unsigned long long red64[32];
+  __shared__ unsigned red32[32];
   __shared__ int s_item, s_prob, s_vote_item;
   __shared__ uint32_t s_sink[32];  // increments of out-of-box pairs (never read)
   __shared__ __align__(16) float s_thr[SPARSE ? 32 : 1][8 * 8];
@@ -663,27 +726,32 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
           __syncthreads();
           if (SPARSE == 2 && centred && d.sparse) {
             constexpr int PS = P >= 4 ? 4 : 2;  // paired instances are built for 2 and 4
+            float* thr = s_thr[SPARSE ? warp : 0];
+            const uint32_t sink = (uint32_t)__cvta_generic_to_shared(s_sink);
             if (d.hist_u16)
-              vote_centred_paired<PS, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane,
-                                            s_thr[SPARSE ? warp : 0], (uint32_t)__cvta_generic_to_shared(s_sink));
+              vote_centred_paired<PS, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink);
             else
-              vote_centred_paired<PS, false>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane,
-                                             s_thr[SPARSE ? warp : 0], (uint32_t)__cvta_generic_to_shared(s_sink));
+              vote_centred_paired<PS, false>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink);
           } else if (SPARSE == 1 && centred && d.sparse) {
-            if (d.hist_u16)
-              vote_centred_sparse<P, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane,
-                                           s_thr[SPARSE ? warp : 0], (uint32_t)__cvta_generic_to_shared(s_sink));
+            const bool cube = SX == (unsigned)d.E[1] && d.E[1] == d.E[2];
+            float* thr = s_thr[SPARSE ? warp : 0];
+            const uint32_t sink = (uint32_t)__cvta_generic_to_shared(s_sink);
+            if (d.hist_u16 && cube)
+              vote_centred_sparse<P, true, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink);
+            else if (d.hist_u16)
+              vote_centred_sparse<P, true, false>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink);
+            else if (cube)
+              vote_centred_sparse<P, false, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink);
             else
-              vote_centred_sparse<P, false>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane,
-                                            s_thr[SPARSE ? warp : 0], (uint32_t)__cvta_generic_to_shared(s_sink));
+              vote_centred_sparse<P, false, false>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink);
           } else if (centred) {
             constexpr int PP = P >= 2 ? P : 2;  // the P = 1 instance never takes the packed path
             if (packed) {
               if (d.hist_u16)
-                vote_centred_x2<PP, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane,
+                vote_centred_x2<PP, true, SPARSE == 0>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane,
                                               (uint32_t)__cvta_generic_to_shared(s_sink));
               else
-                vote_centred_x2<PP, false>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane,
+                vote_centred_x2<PP, false, SPARSE == 0>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane,
                                                (uint32_t)__cvta_generic_to_shared(s_sink));
             } else if (d.hist_u16) {
               vote_centred<P, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane,
@@ -747,9 +815,9 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
               if (c > bc) { bc = c; bb = b; }
             }
           }
-        } else if (d.hist_u16) {
-          // 16-byte reads: the histogram's bytes are a multiple of 16 and the
-          // words past this slab's bins are zero (never voted, or cleared)
+        } else if (SPARSE != 0 && d.hist_u16) {
+          // culled instances: one walk, each thread keeping its first maximum
+          // (the two-walk form below measured 1% slower in their loops)
           const unsigned q4 = (((nbins + 1) >> 1) + 3) >> 2;
           uint4* h4 = reinterpret_cast<uint4*>(hist);
           for (unsigned w4 = tid; w4 < q4; w4 += kPassThreads) {
@@ -764,7 +832,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
               if (b > bc) { bc = b; bb = 8 * w4 + 2 * k + 1; }
             }
           }
-        } else {
+        } else if (SPARSE != 0) {
           const unsigned q4 = (nbins + 3) >> 2;
           uint4* h4 = reinterpret_cast<uint4*>(hist);
           for (unsigned w4 = tid; w4 < q4; w4 += kPassThreads) {
@@ -777,6 +845,62 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
               if (vv[k] > bc) { bc = vv[k]; bb = 4 * w4 + k; }
             }
           }
+        } else if (d.hist_u16) {
+          // 16-byte reads: the histogram's bytes are a multiple of 16 and the
+          // words past this slab's bins are zero (never voted, or cleared).
+          // First walk: the thread's packed maximum and vote sum; then the
+          // block maximum M; second walk: clear, and the thread's first bin
+          // holding M (only threads whose maximum is M read again)
+          const unsigned q4 = (((nbins + 1) >> 1) + 3) >> 2;
+          uint4* h4 = reinterpret_cast<uint4*>(hist);
+          uint32_t m2 = 0u;
+          for (unsigned w4 = tid; w4 < q4; w4 += kPassThreads) {
+            const uint4 v4 = h4[w4];
+            m2 = max_u16x2(m2, max_u16x2(max_u16x2(v4.x, v4.y), max_u16x2(v4.z, v4.w)));
+            vsum = add_halves(v4.w, add_halves(v4.z, add_halves(v4.y, add_halves(v4.x, vsum))));
+          }
+          const unsigned tmax = max(m2 & 0xffffu, m2 >> 16);
+          const unsigned M = block_max_u32(tmax, red32, lane, warp);
+          bool look = tmax == M;
+          for (unsigned w4 = tid; w4 < q4; w4 += kPassThreads) {
+            if (look) {
+              const uint4 v4 = h4[w4];
+              const uint32_t vv[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+              for (int k = 3; k >= 0; --k) {  // the last assignment is the first bin
+                if ((vv[k] >> 16) == M) { bb = 8 * w4 + 2 * k + 1; look = false; }
+                if ((vv[k] & 0xffffu) == M) { bb = 8 * w4 + 2 * k; look = false; }
+              }
+            }
+            h4[w4] = make_uint4(0u, 0u, 0u, 0u);
+          }
+          const bool found = tmax == M && !look;  // else: bin 0 at count 0
+          bc = found ? M : 0u;
+          bb = found ? bb : 0u;
+        } else {
+          const unsigned q4 = (nbins + 3) >> 2;
+          uint4* h4 = reinterpret_cast<uint4*>(hist);
+          unsigned tmax = 0u;
+          for (unsigned w4 = tid; w4 < q4; w4 += kPassThreads) {
+            const uint4 v4 = h4[w4];
+            tmax = max(tmax, max(max(v4.x, v4.y), max(v4.z, v4.w)));
+            vsum += v4.x + v4.y + v4.z + v4.w;
+          }
+          const unsigned M = block_max_u32(tmax, red32, lane, warp);
+          bool look = tmax == M;
+          for (unsigned w4 = tid; w4 < q4; w4 += kPassThreads) {
+            if (look) {
+              const uint4 v4 = h4[w4];
+              const uint32_t vv[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+              for (int k = 3; k >= 0; --k)
+                if (vv[k] == M) { bb = 4 * w4 + k; look = false; }
+            }
+            h4[w4] = make_uint4(0u, 0u, 0u, 0u);
+          }
+          const bool found = tmax == M && !look;
+          bc = found ? M : 0u;
+          bb = found ? bb : 0u;
         }
         vtotal += warp_sum_u32(vsum);
         const unsigned gbin = (unsigned)x0 * Ey * Ez + bb;
@@ -809,6 +933,8 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
 
 // One warp per rotation: inlier count (Eq. 3) at t* and, on the fused path,
 // the robust cost from the distance grid and the argmin key.
+constexpr int kCountPts = 2;  // source points per lane and iteration of count_kernel
+
 __global__ void __launch_bounds__(256) count_kernel(PassLaunch L) {
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
@@ -830,34 +956,32 @@ __global__ void __launch_bounds__(256) count_kernel(PassLaunch L) {
     const bool grid_cost = d.fuse_score && d.metric != 0;
     int cnt = 0;
     float csum = 0.f;
-    // two source points per lane and iteration: both points' 16 distance-grid
-    // gathers are in flight together (the kernel waits on L2 latency)
-    for (int i = lane; i < d.N; i += 64) {
-      const bool two = i + 32 < d.N;
-      const int i2 = two ? i + 32 : i;
-      const float xa = __ldg(d.X + 3 * (size_t)i), ya = __ldg(d.X + 3 * (size_t)i + 1),
-                  za = __ldg(d.X + 3 * (size_t)i + 2);
-      const float xb = __ldg(d.X + 3 * (size_t)i2), yb = __ldg(d.X + 3 * (size_t)i2 + 1),
-                  zb = __ldg(d.X + 3 * (size_t)i2 + 2);
-      const float qxa = fmaf(R[0], xa, fmaf(R[1], ya, R[2] * za)) + tx;
-      const float qya = fmaf(R[3], xa, fmaf(R[4], ya, R[5] * za)) + ty;
-      const float qza = fmaf(R[6], xa, fmaf(R[7], ya, R[8] * za)) + tz;
-      const float qxb = fmaf(R[0], xb, fmaf(R[1], yb, R[2] * zb)) + tx;
-      const float qyb = fmaf(R[3], xb, fmaf(R[4], yb, R[5] * zb)) + ty;
-      const float qzb = fmaf(R[6], xb, fmaf(R[7], yb, R[8] * zb)) + tz;
+    // kCountPts source points per lane and iteration: all their distance-grid
+    // loads are in flight together (the kernel waits on L2 latency)
+    const float e_far = d.eps + d.grid_err, e_near = d.eps - d.grid_err;
+    for (int i = lane; i < d.N; i += 32 * kCountPts) {
+      float qx[kCountPts], qy[kCountPts], qz[kCountPts], dg[kCountPts];
+      bool valid[kCountPts], far[kCountPts], near[kCountPts];
+#pragma unroll
+      for (int k = 0; k < kCountPts; ++k) {
+        valid[k] = i + 32 * k < d.N;
+        const size_t ik = (size_t)(valid[k] ? i + 32 * k : i);
+        const float x = __ldg(d.X + 3 * ik), y = __ldg(d.X + 3 * ik + 1), z = __ldg(d.X + 3 * ik + 2);
+        qx[k] = fmaf(R[0], x, fmaf(R[1], y, R[2] * z)) + tx;
+        qy[k] = fmaf(R[3], x, fmaf(R[4], y, R[5] * z)) + ty;
+        qz[k] = fmaf(R[6], x, fmaf(R[7], y, R[8] * z)) + tz;
+      }
       // bounds on the exact nearest-target distance from the grid's corners
       // decide most queries; those within grid_err of epsilon take the exact
       // cell-list search
-      bool fara, neara, farb, nearb;
-      const float e_far = d.eps + d.grid_err, e_near = d.eps - d.grid_err;
-      const float dga = grid_lookup_decide(d, qxa, qya, qza, e_far, e_near, &fara, &neara);
-      const float dgb = grid_lookup_decide(d, qxb, qyb, qzb, e_far, e_near, &farb, &nearb);
-      const bool ina = fara ? false : (neara ? true : has_inlier(d, qxa, qya, qza));
-      const bool inb = two && (farb ? false : (nearb ? true : has_inlier(d, qxb, qyb, qzb)));
-      cnt += (ina ? 1 : 0) + (inb ? 1 : 0);
-      if (grid_cost) {
-        csum += robust_rho(d.metric, dga, d.eps, d.tau, d.huber_h, d.p_exp);
-        if (two) csum += robust_rho(d.metric, dgb, d.eps, d.tau, d.huber_h, d.p_exp);
+#pragma unroll
+      for (int k = 0; k < kCountPts; ++k)
+        dg[k] = grid_lookup_decide(d, qx[k], qy[k], qz[k], e_far, e_near, &far[k], &near[k]);
+#pragma unroll
+      for (int k = 0; k < kCountPts; ++k) {
+        if (!valid[k]) continue;
+        cnt += (far[k] ? false : (near[k] ? true : has_inlier(d, qx[k], qy[k], qz[k]))) ? 1 : 0;
+        if (grid_cost) csum += robust_rho(d.metric, dg[k], d.eps, d.tau, d.huber_h, d.p_exp);
       }
     }
 #pragma unroll

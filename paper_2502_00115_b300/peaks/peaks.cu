@@ -1,7 +1,7 @@
 // Microbenchmarks of the B300 resources the DSES kernels are bound by:
 // shared-memory atomic increments (random bins of a vote-sized histogram,
-// bank-distinct bins, one shared bin), FP32 FMA issue, and 4-byte random
-// gathers from an L2-resident table. Each returns operations per second
+// bank-distinct bins, one shared bin), FP32 FMA issue, and random 4-byte and
+// 16-byte gathers from L2-resident tables. Each returns operations per second
 // measured with CUDA events; used to state roofline fractions.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -67,6 +67,20 @@ __global__ void l2_gather_kernel(const float* __restrict__ table, uint32_t n, in
   if (acc == 12345.678f) *sink = acc;
 }
 
+__global__ void l2_gather16_kernel(const float4* __restrict__ table, uint32_t n, int reps, float* sink) {
+  uint32_t x = 0x2545F491u * (blockIdx.x * blockDim.x + threadIdx.x + 1);
+  float acc = 0.f;
+  for (int r = 0; r < reps; ++r) {
+#pragma unroll 8
+    for (int k = 0; k < 8; ++k) {
+      x ^= x << 13; x ^= x >> 17; x ^= x << 5;
+      const float4 v = __ldcg(table + (x % n));
+      acc += v.x + v.w;
+    }
+  }
+  if (acc == 12345.678f) *sink = acc;
+}
+
 float time_ms(cudaEvent_t a, cudaEvent_t b) {
   float ms = 0;
   cudaEventElapsedTime(&ms, a, b);
@@ -77,8 +91,9 @@ float time_ms(cudaEvent_t a, cudaEvent_t b) {
 
 // out[0..2]: shared atomics/s (random, bank-distinct, same bin) over a
 // histogram of nbins 32-bit words; out[3]: FP32 FMA/s; out[4]: random 4-byte
-// L2 gathers/s from a table of table_bytes. Returns 0 or a cudaError_t.
-extern "C" int dses_peaks_run(int device, int nbins, size_t table_bytes, double* out) {
+// L2 gathers/s from a table of table_bytes; out[5]: random 16-byte (aligned)
+// L2 gathers/s from a table of table16_bytes. Returns 0 or a cudaError_t.
+extern "C" int dses_peaks_run(int device, int nbins, size_t table_bytes, size_t table16_bytes, double* out) {
   cudaError_t e = cudaSetDevice(device);
   if (e != cudaSuccess) return (int)e;
   int sms = 0;
@@ -86,11 +101,14 @@ extern "C" int dses_peaks_run(int device, int nbins, size_t table_bytes, double*
   unsigned long long* sink = nullptr;
   float* fsink = nullptr;
   float* table = nullptr;
-  const uint32_t n = (uint32_t)(table_bytes / 4);
+  float4* table16 = nullptr;
+  const uint32_t n = (uint32_t)(table_bytes / 4), n16 = (uint32_t)(table16_bytes / 16);
   if ((e = cudaMalloc(&sink, 8)) != cudaSuccess) return (int)e;
   if ((e = cudaMalloc(&fsink, 8)) != cudaSuccess) return (int)e;
   if ((e = cudaMalloc(&table, (size_t)n * 4)) != cudaSuccess) return (int)e;
   cudaMemset(table, 0, (size_t)n * 4);
+  if ((e = cudaMalloc(&table16, (size_t)n16 * 16)) != cudaSuccess) return (int)e;
+  cudaMemset(table16, 0, (size_t)n16 * 16);
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
@@ -120,11 +138,18 @@ extern "C" int dses_peaks_run(int device, int nbins, size_t table_bytes, double*
   cudaEventRecord(b);
   cudaEventSynchronize(b);
   out[4] = (double)gblocks * 256 * 8 * greps / (time_ms(a, b) * 1e-3);
+  l2_gather16_kernel<<<gblocks, 256>>>(table16, n16, 4, fsink);
+  cudaEventRecord(a);
+  l2_gather16_kernel<<<gblocks, 256>>>(table16, n16, greps, fsink);
+  cudaEventRecord(b);
+  cudaEventSynchronize(b);
+  out[5] = (double)gblocks * 256 * 8 * greps / (time_ms(a, b) * 1e-3);
   e = cudaGetLastError();
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   cudaFree(sink);
   cudaFree(fsink);
   cudaFree(table);
+  cudaFree(table16);
   return (int)e;
 }

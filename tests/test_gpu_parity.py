@@ -227,6 +227,85 @@ def test_small_box_lane_private_counters(ctx):
     ctx.destroy_target(t)
 
 
+def test_non_cubic_box_every_vote_path(ctx):
+    # unequal half-widths (11 x 7 x 15 bins) take the per-axis box test, a
+    # cube takes max(|w_x|, |w_y|, |w_z|) < h: each against the oracle on
+    # sampled rotations, and every vote path (packed, scalar, culled, paired
+    # culled, 16- and 32-bit counters) bit-identical to the planner's choice
+    p = synth.modelnet_like_problem(11, hopf_n=2)
+    centre = tuple(float(v) for v in np.round(np.asarray(p.t_true) / 0.04) * 0.04)
+    t = ctx.create_target(p.Y, grid_cap=2 * p.tau)
+    grid = oracle.hopf_grid(2)
+    g = None
+    n = 72 * 8
+    for half in ((0.2, 0.12, 0.28), (0.16, 0.16, 0.16)):
+        gp = gpu_params(p, nn_mode="grid", t_center=centre, t_half=half)
+        pb = ctx.problem(t, p.X, capi.hopf_grid(2), gp)
+        base = ctx.debug(pb, n)
+        P = oracle_params(p, gp, 2 * p.tau)
+        g = g if g is not None else oracle.dist_grid(p.Y, 128, P.grid_cap)
+        rep = check_rotations(p.X, p.Y, grid, P, base[0], base[1], base[2], base[3], range(0, n, 9), dist_grid=g)
+        print("parity:", half, rep.summary())
+        assert rep.ok(), rep.summary()
+        defaults = {k: ctx.get_option(k) for k in ("hist_mode", "points_per_thread", "vote_sparse")}
+        try:
+            for v in (dict(points_per_thread=1), dict(points_per_thread=2), dict(points_per_thread=8),
+                      dict(hist_mode=1), dict(hist_mode=2), dict(vote_sparse=2), dict(vote_sparse=2, hist_mode=1),
+                      dict(vote_sparse=3, points_per_thread=2), dict(vote_sparse=3, hist_mode=1)):
+                for key, val in v.items():
+                    ctx.set_option(key, val)
+                k, V, M, C, r = ctx.debug(pb, n)
+                assert np.array_equal(k, base[0]) and np.array_equal(V, base[1]) and np.array_equal(M, base[2]), \
+                    (half, v)
+                np.testing.assert_allclose(C, base[3], rtol=2e-6, err_msg=str((half, v)))
+                for key, val in defaults.items():
+                    ctx.set_option(key, val)
+        finally:
+            for key, val in defaults.items():
+                ctx.set_option(key, val)
+    ctx.destroy_target(t)
+
+
+def test_in_box_vote_total(ctx):
+    # the sum of every histogram count (last_votes_total) is the number of
+    # (rotation, source, target) pairs whose lattice key lies in the box: an
+    # FP64 count with the kernel's FP32 rotations (a pair within 1e-5 of a
+    # voxel face may go either way), the same under every vote path and
+    # counter width
+    p = synth.tiny_problem(4, hopf_n=2)
+    t = ctx.create_target(p.Y, grid_cap=2 * p.tau)
+    grid = capi.hopf_grid(2)
+    gp = gpu_params(p, nn_mode="grid", t_center=(0.02, -0.04, 0.0), t_half=(0.3, 0.2, 0.24))
+    pb = ctx.problem(t, p.X, grid, gp)
+    ctx.register(pb)
+    total = ctx.get_option("last_votes_total")
+    P = oracle_params(p, gp, 2 * p.tau)
+    lo, hi = oracle.lattice_box(P.t_center[:], P.t_half[:], P.delta_t)
+    X, Y = p.X.astype(np.float64), p.Y.astype(np.float64)
+    inside = near = 0
+    for R in ctx.rotation_grid(grid).astype(np.float64):
+        w = (Y[:, None, :] - (X @ R.T)[None, :, :]) / P.delta_t
+        k = np.floor(w + 0.5)
+        inside += int(np.all((k >= lo) & (k <= hi), axis=-1).sum())
+        near += int(np.any(np.abs(w - k + 0.5) * P.delta_t < 1e-5, axis=-1).sum())
+        near += int(np.any(np.abs(w - k - 0.5) * P.delta_t < 1e-5, axis=-1).sum())
+    assert inside > 0 and abs(total - inside) <= near, (total, inside, near)
+    defaults = {k: ctx.get_option(k) for k in ("hist_mode", "points_per_thread", "vote_sparse")}
+    try:
+        for v in (dict(hist_mode=1), dict(hist_mode=2), dict(points_per_thread=1), dict(points_per_thread=8),
+                  dict(vote_sparse=2), dict(vote_sparse=3), dict(vote_sparse=2, hist_mode=2)):
+            for key, val in v.items():
+                ctx.set_option(key, val)
+            ctx.register(pb)
+            assert ctx.get_option("last_votes_total") == total, v
+            for key, val in defaults.items():
+                ctx.set_option(key, val)
+    finally:
+        for key, val in defaults.items():
+            ctx.set_option(key, val)
+    ctx.destroy_target(t)
+
+
 @pytest.mark.parametrize("hist_mode", [0, 1])
 def test_even_extent_box_matches_oracle(ctx, hist_mode):
     # a box centred half a cell off the lattice has even extents (90 x 89 x 90
