@@ -42,7 +42,7 @@ OPS_PER_ROT_SRC = 15
 # DRAM bytes (read + write) of one vote_kernel launch, from an ncu capture of
 # the same kernel on this problem at N_side 4: a launch reads its inputs (KB)
 # once, so the figure does not grow with the rotations and is used unscaled.
-VOTE_DRAM_BYTES = 244480
+VOTE_DRAM_BYTES = 261376
 
 
 def parse():
