@@ -144,8 +144,10 @@ dses_status dses_destroy(dses_ctx* ctx);
  * grid_res^3 FP32 voxels (grid_res in [8, 512]; 0 => 128), truncated at
  * grid_cap (> 0; the TRUNC/HUBER metrics need grid_cap >= tau). Voxel size per
  * axis h = (extent + 2 cap)/(grid_res - 2), origin min - cap - h; voxel centre
- * values are min(cap, exact nearest-target distance). Errors: INVALID_ARG
- * (m < 1, non-finite point, bad size), OOM, CUDA. */
+ * values are min(cap, exact nearest-target distance). Device memory: 20
+ * bytes per voxel (the grid, and a copy holding each voxel's 2 x 2 corner
+ * block for the lookups: 40 MB at 128^3, 2.7 GB at 512^3) plus the points.
+ * Errors: INVALID_ARG (m < 1, non-finite point, bad size), OOM, CUDA. */
 dses_status dses_create_target(dses_ctx* ctx, const float* xyz, int64_t m, int32_t ptr_is_device,
                                float grid_cap, int32_t grid_res, dses_target** out);
 

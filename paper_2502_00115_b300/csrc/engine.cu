@@ -702,6 +702,15 @@ PassDesc make_desc(const Job& j, int P, bool second) {
     d.E[a] = j.Ep[a];
     d.Ev[a] = j.E[a];
   }
+  {
+    // the magnitudes the culled paths' FP32 keep tests round at: target
+    // coordinates and the box's lattice offsets, in lattice units
+    double big = 0;
+    for (int a = 0; a < 3; ++a)
+      big = std::max({big, std::fabs((double)j.T->bbmin[a]) / j.delta, std::fabs((double)j.T->bbmax[a]) / j.delta,
+                      std::fabs((double)j.lo[a]) + (double)j.Ep[a]});
+    d.cull_margin = (float)(1e-3 + std::ldexp(big, -20));
+  }
   d.slab_x = j.slab_x;
   d.n_slabs = j.n_slabs;
   d.hist_u16 = j.u16;

@@ -44,6 +44,10 @@ struct PassDesc {
   const float4* Yv;      // M target points in Morton order (vote)
   const float4* gbox;    // per group of kGroup Morton-consecutive targets: min, max
   int n_groups;
+  // culled paths: keep windows widen by this many lattice units (1e-3 plus
+  // 2^-20 of the largest lattice coordinate of the target and the box: far
+  // above the FP32 roundings of the staged offsets, w and the thresholds)
+  float cull_margin;
   const float* rot;      // rotations of this pass, 9 floats each (row-major)
   int N, M;
   int n_rot;             // rotations in this pass

@@ -414,10 +414,10 @@ __device__ __forceinline__ void vote_centred_x2(const PassDesc& d, const float4*
 // P x 32 targets of an item are P groups of 32 Morton-consecutive points with
 // known bounding boxes. For each block of 32 sources the lanes test (source,
 // group) pairs against the source's translation window, widened by a margin
-// of kCullMargin lattice units (far above the FP32 rounding of w, so no pair
-// that could vote is dropped); only surviving (source, group) pairs are
-// voted, one group at a time over the set bits of its ballot.
-constexpr float kCullMargin = 1e-3f;
+// of d.cull_margin lattice units (far above the FP32 roundings of w, the
+// staged offsets and the thresholds, so no pair that could vote is dropped);
+// only surviving (source, group) pairs are voted, one group at a time over the
+// set bits of its ballot.
 
 template <int P, bool U16, bool CUBE>
 __device__ __forceinline__ void vote_centred_sparse(const PassDesc& d, const float4* __restrict__ srcc, int nsrc,
@@ -447,9 +447,10 @@ __device__ __forceinline__ void vote_centred_sparse(const PassDesc& d, const flo
       float* t = thr + 8 * lane;
       if (g < d.n_groups) {
         const float4 lo = __ldg(d.gbox + 2 * g), hi = __ldg(d.gbox + 2 * g + 1);
-        t[0] = -hx - kCullMargin - hi.x * inv; t[1] = hx + kCullMargin - lo.x * inv;
-        t[2] = -hy - kCullMargin - hi.y * inv; t[3] = hy + kCullMargin - lo.y * inv;
-        t[4] = -hz - kCullMargin - hi.z * inv; t[5] = hz + kCullMargin - lo.z * inv;
+        const float m = d.cull_margin;
+        t[0] = -hx - m - hi.x * inv; t[1] = hx + m - lo.x * inv;
+        t[2] = -hy - m - hi.y * inv; t[3] = hy + m - lo.y * inv;
+        t[4] = -hz - m - hi.z * inv; t[5] = hz + m - lo.z * inv;
       } else {
         t[0] = t[2] = t[4] = INFINITY;
         t[1] = t[3] = t[5] = -INFINITY;
@@ -536,9 +537,10 @@ __device__ __forceinline__ void vote_centred_paired(const PassDesc& d, const flo
       float* t = thr + 8 * lane;
       if (g < d.n_groups) {
         const float4 lo = __ldg(d.gbox + 2 * g), hi = __ldg(d.gbox + 2 * g + 1);
-        t[0] = -hx - kCullMargin - hi.x * inv; t[1] = hx + kCullMargin - lo.x * inv;
-        t[2] = -hy - kCullMargin - hi.y * inv; t[3] = hy + kCullMargin - lo.y * inv;
-        t[4] = -hz - kCullMargin - hi.z * inv; t[5] = hz + kCullMargin - lo.z * inv;
+        const float m = d.cull_margin;
+        t[0] = -hx - m - hi.x * inv; t[1] = hx + m - lo.x * inv;
+        t[2] = -hy - m - hi.y * inv; t[3] = hy + m - lo.y * inv;
+        t[4] = -hz - m - hi.z * inv; t[5] = hz + m - lo.z * inv;
       } else {
         t[0] = t[2] = t[4] = INFINITY;
         t[1] = t[3] = t[5] = -INFINITY;

@@ -213,7 +213,8 @@ def test_small_box_lane_private_counters(ctx):
         try:
             for v in (dict(hist_mode=1), dict(hist_mode=3, points_per_thread=1), dict(hist_mode=3, points_per_thread=8),
                       dict(hist_mode=3, vote_sparse=2), dict(hist_mode=1, vote_sparse=2), dict(hist_mode=3, vote_sparse=3),
-                      dict(hist_mode=1, vote_sparse=3, points_per_thread=4)):
+                      dict(hist_mode=1, vote_sparse=3, points_per_thread=4), dict(vote_sparse=1),
+                      dict(vote_sparse=1, hist_mode=3, points_per_thread=4)):
                 for key, val in v.items():
                     ctx.set_option(key, val)
                 k, V, M, C, r = ctx.debug(pb, n)
@@ -231,7 +232,8 @@ def test_non_cubic_box_every_vote_path(ctx):
     # unequal half-widths (11 x 7 x 15 bins) take the per-axis box test, a
     # cube takes max(|w_x|, |w_y|, |w_z|) < h: each against the oracle on
     # sampled rotations, and every vote path (packed, scalar, culled, paired
-    # culled, 16- and 32-bit counters) bit-identical to the planner's choice
+    # culled, the dense vote forced, 16- and 32-bit counters) bit-identical
+    # to the planner's choice
     p = synth.modelnet_like_problem(11, hopf_n=2)
     centre = tuple(float(v) for v in np.round(np.asarray(p.t_true) / 0.04) * 0.04)
     t = ctx.create_target(p.Y, grid_cap=2 * p.tau)
@@ -251,7 +253,9 @@ def test_non_cubic_box_every_vote_path(ctx):
         try:
             for v in (dict(points_per_thread=1), dict(points_per_thread=2), dict(points_per_thread=8),
                       dict(hist_mode=1), dict(hist_mode=2), dict(vote_sparse=2), dict(vote_sparse=2, hist_mode=1),
-                      dict(vote_sparse=3, points_per_thread=2), dict(vote_sparse=3, hist_mode=1)):
+                      dict(vote_sparse=3, points_per_thread=2), dict(vote_sparse=3, hist_mode=1),
+                      dict(vote_sparse=1), dict(vote_sparse=1, points_per_thread=2),
+                      dict(vote_sparse=1, hist_mode=2, points_per_thread=8)):
                 for key, val in v.items():
                     ctx.set_option(key, val)
                 k, V, M, C, r = ctx.debug(pb, n)
@@ -263,6 +267,40 @@ def test_non_cubic_box_every_vote_path(ctx):
         finally:
             for key, val in defaults.items():
                 ctx.set_option(key, val)
+    ctx.destroy_target(t)
+
+
+def test_culling_is_conservative_far_from_the_origin(ctx):
+    # a target 15,000 lattice units from the origin (the translation box
+    # centred there): the staged offsets and thresholds carry FP32 roundings
+    # near 1e-3 lattice units, so the culling margin must scale with them;
+    # the dense vote, both culled forms and 16-/32-bit counters give
+    # bit-identical per-rotation (k*, V, M)
+    p = synth.tiny_problem(6, hopf_n=2)
+    T = np.array([300.0, -200.0, 100.0])
+    Y = (p.Y.astype(np.float64) + T).astype(np.float32)
+    t = ctx.create_target(Y, grid_cap=2 * p.tau)
+    c = tuple(float(v) for v in np.round((T + np.asarray(p.t_true)) / p.delta_t) * p.delta_t)
+    gp = gpu_params(p, nn_mode="grid", t_center=c, t_half=(0.1, 0.1, 0.1))
+    pb = ctx.problem(t, p.X, capi.hopf_grid(2), gp)
+    n = 72 * 8
+    defaults = {k: ctx.get_option(k) for k in ("hist_mode", "points_per_thread", "vote_sparse")}
+    try:
+        ctx.set_option("vote_sparse", 1)
+        base = ctx.debug(pb, n)
+        assert base[1].max() > 0
+        for v in (dict(vote_sparse=1, points_per_thread=2), dict(vote_sparse=1, hist_mode=2),
+                  dict(vote_sparse=2), dict(vote_sparse=3), dict(vote_sparse=2, hist_mode=2),
+                  dict(vote_sparse=0)):
+            for key, val in v.items():
+                ctx.set_option(key, val)
+            k, V, M, C, r = ctx.debug(pb, n)
+            assert np.array_equal(k, base[0]) and np.array_equal(V, base[1]) and np.array_equal(M, base[2]), v
+            for key, val in defaults.items():
+                ctx.set_option(key, val)
+    finally:
+        for key, val in defaults.items():
+            ctx.set_option(key, val)
     ctx.destroy_target(t)
 
 
