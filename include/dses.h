@@ -165,6 +165,36 @@ dses_status dses_register(dses_ctx* ctx, const dses_problem* problem, dses_resul
  * per-problem status, or OK. */
 dses_status dses_register_batch(dses_ctx* ctx, const dses_problem* problems, int32_t n, dses_result* out);
 
+/* Rotation sharding of one registration (Algorithm 2 treats every rotation of
+ * the grid on its own): shard `rank` of `world` takes the contiguous range
+ * [begin, end) of a grid of n_rot rotations in index order, begin =
+ * floor(n_rot rank / world), end = floor(n_rot (rank + 1) / world). Host
+ * only. INVALID_ARG for a NULL pointer, n_rot < 0, world < 1 or rank outside
+ * [0, world). */
+dses_status dses_shard_range(int64_t n_rot, int32_t rank, int32_t world, int64_t* begin, int64_t* end);
+
+/* Registers shard `rank` of `world` of the problem's grid (the range of
+ * dses_shard_range) on this context's GPU, blocking, with the same rotations
+ * (FP32 values) as the whole grid; out->rot_index is the rotation's index in
+ * the whole grid. Every rotation of the range is scored, so combining the
+ * shards (dses_combine_results) gives dses_register's result only when every
+ * rotation is a candidate: q_milli, top_k and refine_top_k must be 0
+ * (INVALID_ARG otherwise: a q filter, top-k or second pass across shards
+ * needs the global M* or the K best keys first). A shard with no rotations
+ * (world above the grid size) returns NO_CANDIDATE with rot_index = -1.
+ * Errors as dses_register. */
+dses_status dses_register_shard(dses_ctx* ctx, const dses_problem* problem, int32_t rank, int32_t world,
+                                dses_result* out);
+
+/* The result of a sharded registration from its n shards' results (any
+ * order, each from dses_register_shard): the lexicographic minimum of (cost,
+ * rotation index), the order of the kernels' argmin (the last step of
+ * Algorithm 2); status OK when any shard voted inside the translation box,
+ * else NO_CANDIDATE (rot_index = -1 when no shard had a candidate). Host
+ * only: results travel between processes as plain structs (an all-gather).
+ * INVALID_ARG for n < 1, a NULL pointer or a part with another error. */
+dses_status dses_combine_results(const dses_result* parts, int32_t n, dses_result* out);
+
 /* Asynchronous registration: copies the problem (and the source cloud) and
  * queues it for the serving worker, which admits requests when device memory
  * and batch slots free up and runs admitted requests together (continuous

@@ -110,6 +110,9 @@ SIGNATURES = {
     "dses_vote_static": (_i32, [_i32, _vp, _vp, _i64, _vp, _i64, _vp, _i64, _P(dses_params), _vp]),
     "dses_exhaustive_search": (_i32, [_vp, _P(dses_problem), _vp, _i64, _P(dses_result)]),
     "dses_refine_translation": (_i32, [_vp, _vp, _vp, _i64, _i32, _vp, _vp, _f32, _i32, _vp, _P(ctypes.c_uint32)]),
+    "dses_shard_range": (_i32, [_i64, _i32, _i32, _P(_i64), _P(_i64)]),
+    "dses_register_shard": (_i32, [_vp, _P(dses_problem), _i32, _i32, _P(dses_result)]),
+    "dses_combine_results": (_i32, [_P(dses_result), _i32, _P(dses_result)]),
     "dses_last_error": (ctypes.c_char_p, [_vp]),
     "dses_status_string": (ctypes.c_char_p, [_i32]),
 }
@@ -271,6 +274,25 @@ def dses_exhaustive_search(ctx, problem: dses_problem, n_entries: int = 0):
     return st, r, cost
 
 
+def dses_shard_range(n_rot: int, rank: int, world: int):
+    b, e = ctypes.c_int64(), ctypes.c_int64()
+    st = load().dses_shard_range(n_rot, rank, world, ctypes.byref(b), ctypes.byref(e))
+    return st, b.value, e.value
+
+
+def dses_register_shard(ctx, problem: dses_problem, rank: int, world: int):
+    out = dses_result()
+    st = load().dses_register_shard(ctx, ctypes.byref(problem), rank, world, ctypes.byref(out))
+    return st, out
+
+
+def dses_combine_results(parts):
+    arr = (dses_result * len(parts))(*parts)
+    out = dses_result()
+    st = load().dses_combine_results(arr, len(parts), ctypes.byref(out))
+    return st, out
+
+
 def dses_last_error(ctx) -> str:
     return load().dses_last_error(ctx).decode()
 
@@ -395,6 +417,11 @@ class Context:
         self.check(st, allow=(DSES_OK, DSES_ERR_NO_CANDIDATE))
         return r
 
+    def register_shard(self, pb: dses_problem, rank: int, world: int) -> dses_result:
+        st, r = dses_register_shard(self.h, pb, rank, world)
+        self.check(st, allow=(DSES_OK, DSES_ERR_NO_CANDIDATE))
+        return r
+
     def register_batch(self, pbs) -> list:
         st, rs = dses_register_batch(self.h, pbs)
         self.check(st, allow=(DSES_OK, DSES_ERR_NO_CANDIDATE))
@@ -434,6 +461,21 @@ class Context:
         st, tr, n = dses_refine_translation(self.h, target, X, len(X), 0, R, t, epsilon, iterations)
         self.check(st)
         return tr, n
+
+
+def shard_range(n_rot: int, rank: int, world: int) -> tuple[int, int]:
+    st, b, e = dses_shard_range(n_rot, rank, world)
+    if st != DSES_OK:
+        raise DsesError(st, f"bad shard {rank} of {world} over {n_rot} rotations")
+    return b, e
+
+
+def combine_results(parts) -> dses_result:
+    """The whole registration's result from its shards' results (dses_combine_results)."""
+    st, r = dses_combine_results(list(parts))
+    if st not in (DSES_OK, DSES_ERR_NO_CANDIDATE):
+        raise DsesError(st, "shard results cannot be combined (a shard failed)")
+    return r
 
 
 def result_dict(r: dses_result) -> dict:

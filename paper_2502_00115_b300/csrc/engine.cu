@@ -21,6 +21,7 @@
 #include <cmath>
 #include <condition_variable>
 #include <cstring>
+#include <limits>
 #include <deque>
 #include <map>
 #include <memory>
@@ -1722,39 +1723,126 @@ dses_status dses_poll(dses_ctx* c, uint64_t ticket, dses_result* out) {
   return r->status;
 }
 
+// Rotation count of a HOPF or EULER_BOX grid and, when out_R is set, its FP32
+// rotations copied to host memory (the values every pass over the grid uses).
+static int64_t build_grid_host(dses_ctx* c, const dses_rotation_grid* grid, float* out_R, int64_t capacity) {
+  int64_t n = 0;
+  if (grid->kind == DSES_GRID_HOPF) {
+    if (grid->hopf_n < 1 || grid->hopf_n > 48) invalid("hopf_n must be in [1, 48]");
+    n = 72LL * grid->hopf_n * grid->hopf_n * grid->hopf_n;
+  } else if (grid->kind == DSES_GRID_EULER_BOX) {
+    if (grid->K < 0 || grid->K > 100 || !(grid->delta_r > 0)) invalid("bad Euler box");
+    n = (int64_t)(2 * grid->K + 1) * (2 * grid->K + 1) * (2 * grid->K + 1);
+  } else {
+    invalid("only HOPF and EULER_BOX grids are built on the device");
+  }
+  if (!out_R) return n;
+  if (n > capacity) invalid("capacity is smaller than the grid");
+  if (grid->kind == DSES_GRID_HOPF) {
+    const float* p = hopf_grid(c, grid->hopf_n);
+    CK(cudaMemcpyAsync(out_R, p, 36 * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
+  } else {
+    DevMem m;
+    m.alloc(align256(36 * (size_t)n) + 256, c->stream);
+    double* R0 = (double*)((char*)m.p + align256(36 * (size_t)n));
+    CK(cudaMemcpyAsync(R0, grid->R0, 72, cudaMemcpyHostToDevice, c->stream));
+    CK(launch_euler_box_single(R0, grid->K, grid->delta_r, (float*)m.p, c->stream));
+    CK(cudaMemcpyAsync(out_R, m.p, 36 * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
+    m.release();
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return n;
+}
+
 dses_status dses_rotation_grid_build(dses_ctx* c, const dses_rotation_grid* grid, float* out_R, int64_t capacity,
                                      int64_t* count) {
   if (!c || !grid || !count) return DSES_ERR_INVALID_ARG;
   std::lock_guard<std::recursive_mutex> g(c->mu);
   return guard(c, [&] {
     set_device(c);
-    int64_t n = 0;
-    if (grid->kind == DSES_GRID_HOPF) {
-      if (grid->hopf_n < 1 || grid->hopf_n > 48) invalid("hopf_n must be in [1, 48]");
-      n = 72LL * grid->hopf_n * grid->hopf_n * grid->hopf_n;
-    } else if (grid->kind == DSES_GRID_EULER_BOX) {
-      if (grid->K < 0 || grid->K > 100 || !(grid->delta_r > 0)) invalid("bad Euler box");
-      n = (int64_t)(2 * grid->K + 1) * (2 * grid->K + 1) * (2 * grid->K + 1);
-    } else {
-      invalid("only HOPF and EULER_BOX grids are built on the device");
-    }
-    *count = n;
-    if (!out_R) return;
-    if (n > capacity) invalid("capacity is smaller than the grid");
-    if (grid->kind == DSES_GRID_HOPF) {
-      const float* p = hopf_grid(c, grid->hopf_n);
-      CK(cudaMemcpyAsync(out_R, p, 36 * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
-    } else {
-      DevMem m;
-      m.alloc(align256(36 * (size_t)n) + 256, c->stream);
-      double* R0 = (double*)((char*)m.p + align256(36 * (size_t)n));
-      CK(cudaMemcpyAsync(R0, grid->R0, 72, cudaMemcpyHostToDevice, c->stream));
-      CK(launch_euler_box_single(R0, grid->K, grid->delta_r, (float*)m.p, c->stream));
-      CK(cudaMemcpyAsync(out_R, m.p, 36 * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
-      m.release();
-    }
-    CK(cudaStreamSynchronize(c->stream));
+    *count = build_grid_host(c, grid, nullptr, 0);
+    if (out_R) build_grid_host(c, grid, out_R, capacity);
   });
+}
+
+dses_status dses_shard_range(int64_t n_rot, int32_t rank, int32_t world, int64_t* begin, int64_t* end) {
+  if (!begin || !end || n_rot < 0 || world < 1 || rank < 0 || rank >= world) return DSES_ERR_INVALID_ARG;
+  *begin = n_rot * rank / world;
+  *end = n_rot * (rank + 1) / world;
+  return DSES_OK;
+}
+
+dses_status dses_register_shard(dses_ctx* c, const dses_problem* problem, int32_t rank, int32_t world,
+                                dses_result* out) {
+  if (!c || !problem || !out) return DSES_ERR_INVALID_ARG;
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  dses_status st = DSES_OK;
+  const dses_status gs = guard(c, [&] {
+    set_device(c);
+    if (world < 1 || rank < 0 || rank >= world) invalid("shard rank must be in [0, world)");
+    const dses_params& P = problem->params;
+    if (P.q_milli != 0 || P.top_k != 0 || P.refine_top_k != 0)
+      invalid("a shard scores every rotation of its range: q_milli, top_k and refine_top_k must be 0");
+    std::vector<float> R;
+    const float* all = nullptr;
+    int64_t n = 0;
+    if (problem->grid.kind == DSES_GRID_EXPLICIT) {
+      if (!problem->grid.explicit_R || problem->grid.n_explicit < 1)
+        invalid("explicit grid needs explicit_R and n_explicit >= 1");
+      all = problem->grid.explicit_R;
+      n = problem->grid.n_explicit;
+    } else {
+      n = build_grid_host(c, &problem->grid, nullptr, 0);
+      R.resize(9 * (size_t)n);
+      build_grid_host(c, &problem->grid, R.data(), n);
+      all = R.data();
+    }
+    int64_t b = 0, e = 0;
+    dses_shard_range(n, rank, world, &b, &e);
+    if (e == b) {  // more shards than rotations: this one has none
+      std::memset(out, 0, sizeof(*out));
+      out->rot_index = -1;
+      out->cost = std::numeric_limits<float>::quiet_NaN();
+      out->status = DSES_ERR_NO_CANDIDATE;
+      st = DSES_ERR_NO_CANDIDATE;
+      return;
+    }
+    dses_problem part = *problem;
+    part.grid.kind = DSES_GRID_EXPLICIT;
+    part.grid.explicit_R = all + 9 * b;
+    part.grid.n_explicit = e - b;
+    st = dses_register_batch(c, &part, 1, out);
+    if (st != DSES_OK && st != DSES_ERR_NO_CANDIDATE) throw Error{st, dses_last_error(c)};
+    if (out->rot_index >= 0) out->rot_index += b;
+  });
+  return gs != DSES_OK ? gs : st;
+}
+
+dses_status dses_combine_results(const dses_result* parts, int32_t n, dses_result* out) {
+  if (!parts || !out || n < 1) return DSES_ERR_INVALID_ARG;
+  int best = -1;
+  bool voted = false;
+  for (int i = 0; i < n; ++i) {
+    const dses_result& r = parts[i];
+    if (r.status != DSES_OK && r.status != DSES_ERR_NO_CANDIDATE) return DSES_ERR_INVALID_ARG;
+    voted |= r.status == DSES_OK;
+    if (r.rot_index < 0) continue;  // a shard without any candidate
+    uint32_t cb, bb = 0;
+    std::memcpy(&cb, &r.cost, 4);
+    if (best >= 0) std::memcpy(&bb, &parts[best].cost, 4);
+    // the kernels' argmin order: cost bits (cost >= 0), then the rotation index
+    if (best < 0 || cb < bb || (cb == bb && r.rot_index < parts[best].rot_index)) best = i;
+  }
+  if (best < 0) {
+    std::memset(out, 0, sizeof(*out));
+    out->rot_index = -1;
+    out->cost = std::numeric_limits<float>::quiet_NaN();
+    out->status = DSES_ERR_NO_CANDIDATE;
+    return DSES_ERR_NO_CANDIDATE;
+  }
+  *out = parts[best];
+  out->status = voted ? DSES_OK : DSES_ERR_NO_CANDIDATE;
+  return (dses_status)out->status;
 }
 
 dses_status dses_target_distance_grid(dses_ctx* c, const dses_target* T, float* D, float lo[3], float h[3],

@@ -335,9 +335,9 @@ __device__ __forceinline__ uint64_t pack2(float lo, float hi) {
   return ((uint64_t)__float_as_uint(hi) << 32) | (uint64_t)__float_as_uint(lo);
 }
 
-// Staged layout of source i: float4 [2i] holds (c_x, c_x, c_y, c_y), float4
+// Sources [i0, i1) against a lane's Q target pairs (dense packed path). The
+// staged layout of source i: float4 [2i] holds (c_x, c_x, c_y, c_y), float4
 // [2i + 1] holds (c_z, c_z, 0, 0).
-// Sources [i0, i1) against a lane's Q target pairs (dense packed path).
 template <int Q, bool U16, bool CUBE>
 __device__ __forceinline__ void vote_sources_x2(const float4* __restrict__ srcd, int i0, int i1, const uint64_t* yx,
                                                 const uint64_t* yy, const uint64_t* yz, uint64_t inv2, uint64_t mx2,
