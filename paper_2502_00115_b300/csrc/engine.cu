@@ -185,6 +185,11 @@ struct dses_ctx {
   int64_t vote_sparse_jobs = 0;  // problems of the last blocking call on the culled vote
   int64_t vote_paired_jobs = 0;  // ... of which on its paired 64-point-group form
   int64_t graph_count = 0;       // snapshot for the "graphs_cached" option
+  // pinned result slots of submitted requests, handed out and returned under
+  // smu; allocated in chunks and freed only with the context (pinned frees
+  // synchronise the device, which would stall the serving pipeline)
+  std::vector<dses_result*> res_chunks;
+  std::vector<dses_result*> res_free;
   // host staging: blocking calls, the serving worker, and the one in use
   Stage stage, serve_stage[2];  // the serving worker alternates two (two iterations in flight)
   Stage* cur_stage = nullptr;
@@ -1493,8 +1498,7 @@ dses_status dses_destroy(dses_ctx* c) {
   stop_worker(c);
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
-  for (auto& r : c->tickets)
-    if (r.second->host_res) cudaFreeHost(r.second->host_res);
+  for (auto* chunk : c->res_chunks) cudaFreeHost(chunk);
   for (auto* T : c->targets) free_target(T);
   for (auto& h : c->hopf) cudaFree(h.second);
   if (c->pinned_res) cudaFreeHost(c->pinned_res);
@@ -1681,13 +1685,19 @@ dses_status dses_submit(dses_ctx* c, const dses_problem* problem, uint64_t* tick
     resolve(c, &r->prob, r->job);
     plan(c, r->job);
     set_device(c);
-    CK(cudaMallocHost(&r->host_res, sizeof(dses_result)));
     {
       std::lock_guard<std::mutex> lk(c->smu);
-      if ((int64_t)c->queue.size() >= c->opt.serve_queue_cap) {
-        cudaFreeHost(r->host_res);
+      if ((int64_t)c->queue.size() >= c->opt.serve_queue_cap)
         throw Error{DSES_ERR_QUEUE_FULL, "serving queue is full"};
+      if (c->res_free.empty()) {
+        constexpr int kChunk = 256;
+        dses_result* chunk = nullptr;
+        CK(cudaMallocHost((void**)&chunk, sizeof(dses_result) * kChunk));
+        c->res_chunks.push_back(chunk);
+        for (int i = kChunk - 1; i >= 0; --i) c->res_free.push_back(chunk + i);
       }
+      r->host_res = c->res_free.back();
+      c->res_free.pop_back();
       *ticket = c->next_ticket++;
       c->tickets[*ticket] = r;
       r->job.T->inflight++;
@@ -1712,10 +1722,10 @@ dses_status dses_poll(dses_ctx* c, uint64_t ticket, dses_result* out) {
     r = it->second;
     if (r->state.load() != 2) return DSES_NOT_READY;
     c->tickets.erase(it);
+    if (r->host_res) c->res_free.push_back(r->host_res);  // its result is already in r->result
+    r->host_res = nullptr;
   }
   *out = r->result;
-  if (r->host_res) cudaFreeHost(r->host_res);
-  r->host_res = nullptr;
   if (r->status != DSES_OK) {
     std::lock_guard<std::recursive_mutex> g(c->mu);
     c->err = r->err.empty() ? "registration found no candidate" : r->err;
