@@ -95,13 +95,17 @@ def _load():
                 "orc_cost_exact": (d, [pd, i64, pd, i64, pd, pd, P(Params)]),
                 "orc_dist_grid_geometry": (None, [pd, i64, i32, d, pd, pd]),
                 "orc_dist_grid": (None, [pd, i64, i32, d, pd]),
+                "orc_dist_grid_threads": (None, [pd, i64, i32, d, pd, i32]),
                 "orc_grid_lookup": (d, [pd, i32, pd, pd, d, pd]),
                 "orc_cost_grid": (d, [pd, i64, pd, i32, pd, pd, d, pd, pd, P(Params)]),
                 "orc_register": (i32, [pd, i64, pd, i64, pd, i64, P(Params), P(ctypes.c_int32), pi64, pi64, pd,
                                        pi64, pi64, P(Result)]),
                 "orc_register_threads": (i32, [pd, i64, pd, i64, pd, i64, P(Params), i32, P(Result)]),
+                "orc_register_threads_out": (i32, [pd, i64, pd, i64, pd, i64, P(Params), i32, P(ctypes.c_int32),
+                                                   pi64, pi64, pd, pi64, pi64, P(Result)]),
                 "orc_field_create": (ctypes.c_void_p, [pd, i64, i32, d]),
                 "orc_field_free": (None, [ctypes.c_void_p]),
+                "orc_field_create_threads": (ctypes.c_void_p, [pd, i64, i32, d, i32]),
                 "orc_register_field_threads": (i32, [pd, i64, pd, i64, pd, i64, P(Params), ctypes.c_void_p, i32,
                                                      P(Result)]),
                 "orc_eval_rotation": (None, [pd, i64, pd, i64, pd, P(Params), pi32, pi64, pi64, pi64, pi64]),
@@ -284,12 +288,17 @@ class DistGrid:
         return self.D.shape[0]
 
 
-def dist_grid(Y, G: int, cap: float) -> DistGrid:
+def dist_grid(Y, G: int, cap: float, threads: int = 1) -> DistGrid:
+    """The target's truncated distance grid; threads > 1 splits its x-planes
+    over host threads (the same per-voxel arithmetic)."""
     Y = _f64(Y)
     lo, h = np.zeros(3), np.zeros(3)
     _load().orc_dist_grid_geometry(_pd(Y), len(Y), G, cap, _pd(lo), _pd(h))
     D = np.zeros((G, G, G))
-    _load().orc_dist_grid(_pd(Y), len(Y), G, cap, _pd(D))
+    if threads > 1:
+        _load().orc_dist_grid_threads(_pd(Y), len(Y), G, cap, _pd(D), int(threads))
+    else:
+        _load().orc_dist_grid(_pd(Y), len(Y), G, cap, _pd(D))
     return DistGrid(D=D, lo=lo, h=h, cap=cap)
 
 
@@ -326,8 +335,9 @@ def _result(res: Result, **extra) -> Registration:
                         t=np.array(res.t[:]), votes=res.votes, inliers=res.inliers, cost=res.cost, **extra)
 
 
-def register(X, Y, rotations, P: Params) -> Registration:
-    """Algorithm 2 over an explicit FP64 rotation list, single-threaded, with per-rotation outputs."""
+def register(X, Y, rotations, P: Params, threads: int = 1) -> Registration:
+    """Algorithm 2 over an explicit FP64 rotation list with per-rotation outputs;
+    threads > 1 fans the rotations over host threads (same arithmetic)."""
     X, Y, Rl = _f64(X), _f64(Y), _f64(rotations)
     nR = len(Rl)
     B = (2 * P.refine_K + 1) ** 3 if P.refine_top_k > 0 else 0
@@ -337,12 +347,15 @@ def register(X, Y, rotations, P: Params) -> Registration:
     cost = np.zeros(total)
     nbp, nbm = np.zeros(total, dtype=np.int64), np.zeros(total, dtype=np.int64)
     res = Result()
-    _load().orc_register(_pd(X), len(X), _pd(Y), len(Y), _pd(Rl), nR, ctypes.byref(P),
-                         k.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                         V.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
-                         Mc.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _pd(cost),
-                         nbp.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
-                         nbm.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), ctypes.byref(res))
+    args = (_pd(X), len(X), _pd(Y), len(Y), _pd(Rl), nR, ctypes.byref(P))
+    outs = (k.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), V.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+            Mc.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _pd(cost),
+            nbp.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), nbm.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+            ctypes.byref(res))
+    if threads > 1:
+        _load().orc_register_threads_out(*args, int(threads), *outs)
+    else:
+        _load().orc_register(*args, *outs)
     return _result(res, k=k, V=V, M=Mc, costs=cost, n_boundary_pairs=nbp, n_boundary_points=nbm)
 
 
@@ -358,9 +371,12 @@ def register_threads(X, Y, rotations, P: Params, threads: int) -> Registration:
 class Field:
     """A target's distance field built once (the resident-target setting)."""
 
-    def __init__(self, Y, G: int, cap: float):
+    def __init__(self, Y, G: int, cap: float, threads: int = 1):
         self.Y = _f64(Y)
-        self.h = _load().orc_field_create(_pd(self.Y), len(self.Y), G, cap)
+        if threads > 1:
+            self.h = _load().orc_field_create_threads(_pd(self.Y), len(self.Y), G, cap, int(threads))
+        else:
+            self.h = _load().orc_field_create(_pd(self.Y), len(self.Y), G, cap)
 
     def close(self):
         if self.h:

@@ -478,10 +478,9 @@ void orc_dist_grid_geometry(const double* Y, int64_t M, int G, double cap, doubl
   }
 }
 
-void orc_dist_grid(const double* Y, int64_t M, int G, double cap, double* D) {
-  double lo[3], h[3];
-  orc_dist_grid_geometry(Y, M, G, cap, lo, h);
-  for (int a = 0; a < G; ++a)
+static void dist_grid_planes(const double* Y, int64_t M, int G, double cap, const double* lo, const double* h,
+                             double* D, int a0, int a1) {
+  for (int a = a0; a < a1; ++a)
     for (int b = 0; b < G; ++b)
       for (int c = 0; c < G; ++c) {
         const double px = lo[0] + (a + 0.5) * h[0], py = lo[1] + (b + 0.5) * h[1], pz = lo[2] + (c + 0.5) * h[2];
@@ -492,6 +491,25 @@ void orc_dist_grid(const double* Y, int64_t M, int G, double cap, double* D) {
         }
         D[((int64_t)a * G + b) * G + c] = std::min(cap, std::sqrt(best));
       }
+}
+
+void orc_dist_grid(const double* Y, int64_t M, int G, double cap, double* D) {
+  double lo[3], h[3];
+  orc_dist_grid_geometry(Y, M, G, cap, lo, h);
+  dist_grid_planes(Y, M, G, cap, lo, h, D, 0, G);
+}
+
+// The same grid with its x-planes split over host threads (every voxel is
+// computed as above, by one thread), for targets whose brute-force grid takes
+// minutes on one core.
+void orc_dist_grid_threads(const double* Y, int64_t M, int G, double cap, double* D, int threads) {
+  double lo[3], h[3];
+  orc_dist_grid_geometry(Y, M, G, cap, lo, h);
+  const int T = std::max(1, std::min(threads, G));
+  std::vector<std::thread> pool;
+  for (int w = 0; w < T; ++w)
+    pool.emplace_back([=]() { dist_grid_planes(Y, M, G, cap, lo, h, D, G * w / T, G * (w + 1) / T); });
+  for (auto& th : pool) th.join();
 }
 
 // Trilinear interpolation between voxel centres, clamped at the outermost
@@ -691,6 +709,17 @@ int orc_register_threads(const double* X, int64_t N, const double* Y, int64_t M,
                       res);
 }
 
+// The same threaded computation with the per-rotation outputs of
+// orc_register (each thread writes only the rotations it evaluates); used to
+// write stored expected values at sizes the single-threaded path cannot
+// finish in reasonable time.
+int orc_register_threads_out(const double* X, int64_t N, const double* Y, int64_t M, const double* Rlist,
+                             int64_t nR, const orc_params* P, int threads, int32_t* out_k, int64_t* out_V,
+                             int64_t* out_M, double* out_cost, int64_t* out_nbp, int64_t* out_nbm,
+                             orc_result* res) {
+  return run_register(X, N, Y, M, Rlist, nR, P, threads, out_k, out_V, out_M, out_cost, out_nbp, out_nbm, res);
+}
+
 // Algorithm 1 (pure exhaustive search): every rotation of Rlist against every
 // lattice translation k delta_t of the translation box, with the error
 //   e(R, t) = sum over source points of rho(min_j ||y_j - R x_i - t||)
@@ -754,6 +783,17 @@ int64_t orc_exhaustive(const double* X, int64_t N, const double* Y, int64_t M, c
 void* orc_field_create(const double* Y, int64_t M, int G, double cap) {
   Field* F = new Field();
   build_field(Y, M, G, cap, F);
+  return F;
+}
+
+// The same field with the grid's x-planes split over host threads.
+void* orc_field_create_threads(const double* Y, int64_t M, int G, double cap, int threads) {
+  Field* F = new Field();
+  F->G = G;
+  F->cap = cap;
+  F->D.resize((size_t)G * G * G);
+  orc_dist_grid_threads(Y, M, G, cap, F->D.data(), threads);
+  orc_dist_grid_geometry(Y, M, G, cap, F->lo, F->h);
   return F;
 }
 
