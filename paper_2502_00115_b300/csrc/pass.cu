@@ -31,6 +31,7 @@
 #include <atomic>
 
 #include "kernels.cuh"
+#include "optin.h"
 
 namespace dses {
 
@@ -675,8 +676,9 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
     }
     __syncthreads();
     const PassDesc& d = sd;
-    const int r0 = (item - L.tile_prefix[p]) * L.tile_rot;
-    const int r1 = min(r0 + L.tile_rot, d.n_rot);
+    const int tr = d.tile_rot > 0 ? d.tile_rot : L.tile_rot;
+    const int r0 = (item - L.tile_prefix[p]) * tr;
+    const int r1 = min(r0 + tr, d.n_rot);
 
     for (int r = r0; r < r1; ++r) {
       float R[9];
@@ -1006,12 +1008,15 @@ __global__ void __launch_bounds__(256) count_kernel(PassLaunch L) {
 template <int P, int SPARSE, bool PADDED>
 cudaError_t launch_vote_p(const PassLaunch& L, int grid_ctas, cudaStream_t s) {
   const int smem = pass_smem_bytes(L.hist_bytes, L.src_bytes);
-  static int configured = 0;
-  if (configured < smem) {
-    cudaError_t e =
-        cudaFuncSetAttribute(vote_kernel<P, SPARSE, PADDED>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  // the opt-in is per device: a process may launch this instance on several GPUs
+  static OptIn optin;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (optin.needed(dev, smem)) {
+    e = cudaFuncSetAttribute(vote_kernel<P, SPARSE, PADDED>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    configured = smem;
+    optin.done(dev, smem);
   }
   g_launches.fetch_add(1, std::memory_order_relaxed);
   vote_kernel<P, SPARSE, PADDED><<<grid_ctas, kPassThreads, smem, s>>>(L);
