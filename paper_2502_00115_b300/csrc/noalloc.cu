@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <climits>
 #include <cstring>
 #include <mutex>
 
@@ -41,7 +42,9 @@ constexpr size_t kScratchBytes = kOffAcc + 256;
 static __device__ __align__(256) unsigned char g_vote_scratch[kScratchBytes];
 
 // Host view: the array's device address per device, looked up once with that
-// device current (the host symbol itself is not a device address).
+// device current (the host symbol itself is not a device address). The cache
+// lives as long as the process: a cudaDeviceReset of a device (which drops the
+// context that address belongs to) leaves it stale, as dses.h states.
 std::mutex g_addr_mu;
 void* g_addr[64] = {nullptr};
 
@@ -78,6 +81,8 @@ extern "C" dses_status dses_vote_static(int device, void* cuda_stream, const flo
   if (!src_dev || !tgt_dev || !rot_dev || !params || !kv_dev) return DSES_ERR_INVALID_ARG;
   if (n_src < 1 || n_src > (1 << 24) || n_rot < 1 || n_rot > (1LL << 31) - 1) return DSES_ERR_INVALID_ARG;
   if (n_tgt < 1 || n_tgt > kStaticMaxTargets) return DSES_ERR_INVALID_ARG;  // beyond the static scratch
+  // one bin can collect every pair: its count (and V in kv_dev) must fit an int32
+  if (n_src * n_tgt > INT32_MAX) return DSES_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(kv_dev) & 15u) != 0) return DSES_ERR_INVALID_ARG;
   if (device < 0 || device >= 64) return DSES_ERR_INVALID_ARG;
   const dses_params& P = *params;
