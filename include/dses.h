@@ -48,7 +48,8 @@ typedef enum {
   DSES_ERR_QUEUE_FULL = -4,      /* dses_submit: the request queue is at capacity */
   DSES_ERR_TIMEOUT = -5,         /* a bounded wait ran out */
   DSES_ERR_NO_CANDIDATE = -6,    /* no point pair voted inside the translation box */
-  DSES_ERR_UNKNOWN_TICKET = -7   /* dses_poll: ticket never issued or already collected */
+  DSES_ERR_UNKNOWN_TICKET = -7,  /* dses_poll: ticket never issued or already collected */
+  DSES_ERR_EXCHANGE = -8         /* dses_register_sharded: the all-gather callback failed */
 } dses_status;
 
 /* Robust per-point error rho(d) on the nearest-target distance d (the norm p of
@@ -175,14 +176,15 @@ dses_status dses_shard_range(int64_t n_rot, int32_t rank, int32_t world, int64_t
 
 /* Registers shard `rank` of `world` of the problem's grid (the range of
  * dses_shard_range) on this context's GPU, blocking, with the same rotations
- * (FP32 values) as the whole grid; out->rot_index is the rotation's index in
- * the whole grid. Every rotation of the range is scored, so combining the
- * shards (dses_combine_results) gives dses_register's result only when every
- * rotation is a candidate: q_milli, top_k and refine_top_k must be 0
- * (INVALID_ARG otherwise: a q filter, top-k or second pass across shards
- * needs the global M* or the K best keys first). A shard with no rotations
- * (world above the grid size) returns NO_CANDIDATE with rot_index = -1.
- * Errors as dses_register. */
+ * (FP32 values, the device grid sliced in place) as the whole grid;
+ * out->rot_index is the rotation's index in the whole grid. Every rotation of
+ * the range is scored, so combining the shards (dses_combine_results) gives
+ * dses_register's result only when every rotation is a candidate: q_milli,
+ * top_k and refine_top_k must be 0 (INVALID_ARG otherwise: a q filter, top-k
+ * or second pass across shards needs the global M* or the K best keys first,
+ * which dses_register_sharded exchanges). A shard with no rotations (world
+ * above the grid size) returns NO_CANDIDATE with rot_index = -1. Errors as
+ * dses_register. */
 dses_status dses_register_shard(dses_ctx* ctx, const dses_problem* problem, int32_t rank, int32_t world,
                                 dses_result* out);
 
@@ -194,6 +196,31 @@ dses_status dses_register_shard(dses_ctx* ctx, const dses_problem* problem, int3
  * only: results travel between processes as plain structs (an all-gather).
  * INVALID_ARG for n < 1, a NULL pointer or a part with another error. */
 dses_status dses_combine_results(const dses_result* parts, int32_t n, dses_result* out);
+
+/* All-gather used by dses_register_sharded: every shard passes `bytes` bytes
+ * in `send`; `recv` (world * bytes, provided by the library) receives shard
+ * r's bytes at offset r * bytes. Returns 0 on success, anything else on
+ * failure. Called from the thread that called dses_register_sharded. */
+typedef int32_t (*dses_allgather_fn)(void* user, const void* send, int64_t bytes, void* recv);
+
+/* One registration sharded over `world` processes (one GPU each) by rotation
+ * ranges, with every step of Algorithm 2: shard `rank` runs the ranges
+ * dses_shard_range gives it of the grid and of the second pass, and the
+ * shards meet, through `allgather`, only where Algorithm 2 reduces over all
+ * rotations: the best inlier count M* before the q filter (4 bytes per
+ * shard), the top_k keys (M desc, index asc; 8 top_k bytes), the
+ * refine_top_k best first-pass candidates by (cost, index) that centre the
+ * second pass's Euler boxes (8 refine_top_k bytes), the second pass's own M*
+ * or top_k keys, and the shards' results (one dses_result each). Every shard
+ * receives the combined result, equal to dses_register's on the whole
+ * problem. Every shard must make the call with the same problem and world;
+ * the callback is called the same number of times on every shard, with the
+ * same sizes. A shard that fails before an exchange leaves the others waiting
+ * in their callbacks: give the collective behind it a timeout. Blocking.
+ * Errors: INVALID_ARG (NULL argument, bad rank or world, bad problem),
+ * EXCHANGE (the callback returned non-zero), others as dses_register. */
+dses_status dses_register_sharded(dses_ctx* ctx, const dses_problem* problem, int32_t rank, int32_t world,
+                                  dses_allgather_fn allgather, void* user, dses_result* out);
 
 /* Asynchronous registration: copies the problem (and the source cloud) and
  * queues it for the serving worker, which admits requests when device memory
@@ -213,6 +240,16 @@ dses_status dses_poll(dses_ctx* ctx, uint64_t ticket, dses_result* out);
  * (optional) receives the result. */
 dses_status dses_debug_per_rotation(dses_ctx* ctx, const dses_problem* problem, int32_t* k_star,
                                     uint32_t* votes, uint32_t* inliers, float* cost, dses_result* out);
+
+/* Test hook, batched: the n problems run as dses_register_batch runs them (one
+ * persistent launch over their (problem, rotation-tile) work queue, without
+ * graph replay); problem b's per-rotation intermediates go to k_star[b],
+ * votes[b], inliers[b] and cost[b] (host arrays of that problem's n_rot
+ * entries, as dses_debug_per_rotation writes them) and its result to out[b].
+ * Any of the four pointer arrays, or any entry of one, may be NULL. */
+dses_status dses_debug_per_rotation_batch(dses_ctx* ctx, const dses_problem* problems, int32_t n,
+                                          int32_t* const* k_star, uint32_t* const* votes,
+                                          uint32_t* const* inliers, float* const* cost, dses_result* out);
 
 /* Builds a rotation grid on the device and copies it to out_R (host,
  * capacity x 9 floats). *count receives the grid size; INVALID_ARG if it
@@ -267,7 +304,11 @@ dses_status dses_exhaustive_search(dses_ctx* ctx, const dses_problem* problem, f
  *   "fuse_score"           1 (default) score inside the rotation pass when every
  *                          rotation is a candidate; 0 always score in a second kernel
  *   "tile_rotations"       rotations per work item of the persistent launch (0 auto)
- *   "autotune"             1 time the launch shapes once per problem-size bucket
+ *   "autotune"             1 (default): time the vote's launch shapes once per
+ *                          problem-size bucket (points per thread 1/2/4/8, then
+ *                          rotations per work item 1/2/4/8/16 for that shape) on an
+ *                          even-stride sample of the problem's own rotations; 0:
+ *                          fixed heuristics. Results do not depend on the shape.
  *   "use_graphs"           1 (default) replay repeated batches through CUDA graphs
  *   "serve_max_batch"      requests the serving worker runs together
  *   "serve_queue_cap"      submitted requests waiting for admission
@@ -281,6 +322,12 @@ dses_status dses_exhaustive_search(dses_ctx* ctx, const dses_problem* problem, f
  *                          packed pairs (pays when the window spans many groups)
  *   "record_timing"        1: time every rotation pass with CUDA events on the
  *                          context's stream
+ *   "fail_next_allocs"     test hook: the next this-many registrations (blocking or
+ *                          served) fail at their scratch allocation with
+ *                          DSES_ERR_OOM, as if the device allocator had refused,
+ *                          without touching the device; the context stays usable
+ *   "serve_max_active"     most requests the serving worker has held admitted at
+ *                          once (set to 0 to reset; no other value)
  *   "last_pass_ns"         (read-only) summed duration of the vote kernels of the
  *                          last blocking call, in nanoseconds
  *   "last_count_ns"        (read-only) the same for its inlier-count / score kernels
@@ -290,6 +337,9 @@ dses_status dses_exhaustive_search(dses_ctx* ctx, const dses_problem* problem, f
  *   "last_vote_sparse"     (read-only) how many problems of the last blocking call
  *                          ran the culled (windowed) vote
  *   "last_vote_paired"     (read-only) ... of which its 64-point-group form
+ *   "last_p_mask"          (read-only) points-per-thread shapes the last pipeline run
+ *                          launched its rotation passes with (bit P set for each)
+ *   "last_tile_max"        (read-only) the largest rotations per work item among them
  *   "graphs_cached"        (read-only) captured CUDA graphs held by the context
  *                          (dses_destroy_target drops those that read the target)
  *   "kernel_launches"      (read-only) kernels this library has launched in the
@@ -311,9 +361,13 @@ dses_status dses_get_option(dses_ctx* ctx, const char* key, int64_t* value);
  * Work is queued on cuda_stream (NULL: the legacy default stream); outputs are
  * valid once that stream has reached this point. Scratch lives in one static
  * device array of about 129 KB per GPU (held until exit), so n_tgt is limited to
- * 8192 points (larger: INVALID_ARG). The first call on a device looks up the
- * array's device address with that device made current, then restores the
- * caller's current device; make that first call before any stream capture.
+ * 8192 points (larger: INVALID_ARG), and n_src * n_tgt to 2^31 - 1 (a bin may
+ * collect every pair and V is an int32). The first call on a device looks up
+ * the array's device address with that device made current, keeps it for the
+ * life of the process, then restores the caller's current device; make that
+ * first call before any stream capture. A cudaDeviceReset of that device
+ * invalidates the kept address: do not call this entry point on the device
+ * after resetting it.
  * Calls share the array: calls that overlap on the GPU (other streams, other
  * host threads) race and must be serialised by the caller. Each call clears
  * the counters it needs. Errors: INVALID_ARG, CUDA. */

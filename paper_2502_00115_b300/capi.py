@@ -25,6 +25,7 @@ DSES_ERR_QUEUE_FULL = -4
 DSES_ERR_TIMEOUT = -5
 DSES_ERR_NO_CANDIDATE = -6
 DSES_ERR_UNKNOWN_TICKET = -7
+DSES_ERR_EXCHANGE = -8
 
 DSES_METRIC_INLIER, DSES_METRIC_TRUNC_L1, DSES_METRIC_TRUNC_L2, DSES_METRIC_HUBER, DSES_METRIC_LP = range(5)
 DSES_GRID_HOPF, DSES_GRID_EULER_BOX, DSES_GRID_EXPLICIT = range(3)
@@ -87,6 +88,9 @@ class dses_problem(ctypes.Structure):
     ]
 
 
+# int32_t (*dses_allgather_fn)(void* user, const void* send, int64_t bytes, void* recv)
+ALLGATHER_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p)
+
 _lib = None
 _lock = threading.Lock()
 
@@ -103,6 +107,8 @@ SIGNATURES = {
     "dses_submit": (_i32, [_vp, _P(dses_problem), _P(ctypes.c_uint64)]),
     "dses_poll": (_i32, [_vp, ctypes.c_uint64, _P(dses_result)]),
     "dses_debug_per_rotation": (_i32, [_vp, _P(dses_problem), _vp, _vp, _vp, _vp, _P(dses_result)]),
+    "dses_debug_per_rotation_batch": (_i32, [_vp, _P(dses_problem), _i32, _P(_vp), _P(_vp), _P(_vp), _P(_vp),
+                                             _P(dses_result)]),
     "dses_rotation_grid_build": (_i32, [_vp, _P(dses_rotation_grid), _vp, _i64, _P(_i64)]),
     "dses_target_distance_grid": (_i32, [_vp, _vp, _vp, _vp, _vp, _P(_i32), _P(_f32)]),
     "dses_set_option": (_i32, [_vp, ctypes.c_char_p, _i64]),
@@ -113,6 +119,7 @@ SIGNATURES = {
     "dses_shard_range": (_i32, [_i64, _i32, _i32, _P(_i64), _P(_i64)]),
     "dses_register_shard": (_i32, [_vp, _P(dses_problem), _i32, _i32, _P(dses_result)]),
     "dses_combine_results": (_i32, [_P(dses_result), _i32, _P(dses_result)]),
+    "dses_register_sharded": (_i32, [_vp, _P(dses_problem), _i32, _i32, ALLGATHER_FN, _vp, _P(dses_result)]),
     "dses_last_error": (ctypes.c_char_p, [_vp]),
     "dses_status_string": (ctypes.c_char_p, [_i32]),
 }
@@ -205,6 +212,20 @@ def dses_debug_per_rotation(ctx, problem: dses_problem, n_rot: int):
     return st, k, V, M, C, out
 
 
+def dses_debug_per_rotation_batch(ctx, problems, n_rots):
+    """Per-problem (k*, V, M, cost) arrays of a batched run; n_rots[b] = problem b's rotations."""
+    n = len(problems)
+    arr = (dses_problem * n)(*problems)
+    ks = [np.zeros((m, 3), dtype=np.int32) for m in n_rots]
+    Vs = [np.zeros(m, dtype=np.uint32) for m in n_rots]
+    Ms = [np.zeros(m, dtype=np.uint32) for m in n_rots]
+    Cs = [np.zeros(m, dtype=np.float32) for m in n_rots]
+    ptrs = lambda arrs: (_vp * n)(*[a.ctypes.data for a in arrs])
+    out = (dses_result * n)()
+    st = load().dses_debug_per_rotation_batch(ctx, arr, n, ptrs(ks), ptrs(Vs), ptrs(Ms), ptrs(Cs), out)
+    return st, ks, Vs, Ms, Cs, list(out)
+
+
 def dses_rotation_grid_build(ctx, grid: dses_rotation_grid):
     cnt = ctypes.c_int64()
     st = load().dses_rotation_grid_build(ctx, ctypes.byref(grid), None, 0, ctypes.byref(cnt))
@@ -283,6 +304,33 @@ def dses_shard_range(n_rot: int, rank: int, world: int):
 def dses_register_shard(ctx, problem: dses_problem, rank: int, world: int):
     out = dses_result()
     st = load().dses_register_shard(ctx, ctypes.byref(problem), rank, world, ctypes.byref(out))
+    return st, out
+
+
+def make_allgather(gather_bytes):
+    """A dses_allgather_fn from a Python function gather_bytes(bytes) -> list of
+    bytes (one per shard, in rank order). Keep the returned object alive for as
+    long as the library may call it."""
+
+    def fn(user, send, nbytes, recv):
+        try:
+            mine = ctypes.string_at(send, nbytes)
+            parts = gather_bytes(mine)
+            blob = b"".join(parts)
+            if any(len(q) != nbytes for q in parts):
+                return 1
+            ctypes.memmove(recv, blob, len(blob))
+            return 0
+        except Exception:  # an exception must not cross the C boundary
+            return 1
+
+    return ALLGATHER_FN(fn)
+
+
+def dses_register_sharded(ctx, problem: dses_problem, rank: int, world: int, allgather):
+    """allgather: an ALLGATHER_FN (see make_allgather)."""
+    out = dses_result()
+    st = load().dses_register_sharded(ctx, ctypes.byref(problem), rank, world, allgather, None, ctypes.byref(out))
     return st, out
 
 
@@ -422,6 +470,11 @@ class Context:
         self.check(st, allow=(DSES_OK, DSES_ERR_NO_CANDIDATE))
         return r
 
+    def register_sharded(self, pb: dses_problem, rank: int, world: int, allgather) -> dses_result:
+        st, r = dses_register_sharded(self.h, pb, rank, world, allgather)
+        self.check(st, allow=(DSES_OK, DSES_ERR_NO_CANDIDATE))
+        return r
+
     def register_batch(self, pbs) -> list:
         st, rs = dses_register_batch(self.h, pbs)
         self.check(st, allow=(DSES_OK, DSES_ERR_NO_CANDIDATE))
@@ -429,6 +482,11 @@ class Context:
 
     def debug(self, pb: dses_problem, n_rot: int):
         st, k, V, M, C, r = dses_debug_per_rotation(self.h, pb, n_rot)
+        self.check(st, allow=(DSES_OK, DSES_ERR_NO_CANDIDATE))
+        return k, V, M, C, r
+
+    def debug_batch(self, pbs, n_rots):
+        st, k, V, M, C, r = dses_debug_per_rotation_batch(self.h, pbs, n_rots)
         self.check(st, allow=(DSES_OK, DSES_ERR_NO_CANDIDATE))
         return k, V, M, C, r
 

@@ -32,6 +32,7 @@
 #include <vector>
 
 #include "dses.h"
+#include "exchange.h"
 #include "kernels.cuh"
 
 using namespace dses;
@@ -108,7 +109,7 @@ struct Options {
   int64_t points_per_thread = 0;
   int64_t fuse_score = 1;
   int64_t tile_rotations = 0;
-  int64_t autotune = 0;
+  int64_t autotune = 1;
   int64_t use_graphs = 1;
   int64_t serve_max_batch = 16;
   int64_t serve_queue_cap = 100000;
@@ -117,6 +118,10 @@ struct Options {
   int64_t serve_iter_pairs = 30000000000LL;
   int64_t record_timing = 0;
   int64_t vote_sparse = 0;
+  // test hook: the next this-many registrations (blocking or served) are
+  // refused at their scratch allocation as if the device allocator had
+  // failed (DSES_ERR_OOM), without touching the device
+  int64_t fail_next_allocs = 0;
 };
 
 }  // namespace
@@ -185,6 +190,7 @@ struct dses_ctx {
   int64_t vote_sparse_jobs = 0;  // problems of the last blocking call on the culled vote
   int64_t vote_paired_jobs = 0;  // ... of which on its paired 64-point-group form
   int64_t graph_count = 0;       // snapshot for the "graphs_cached" option
+  int64_t serve_max_active = 0;  // most requests the serving worker held at once (resettable to 0)
   // pinned result slots of submitted requests, handed out and returned under
   // smu; allocated in chunks and freed only with the context (pinned frees
   // synchronise the device, which would stall the serving pipeline)
@@ -203,7 +209,10 @@ struct dses_ctx {
   };
   std::map<std::string, GraphEntry> graphs;
   std::map<std::string, int> graph_seen;
-  std::map<std::string, int> tuned_p;  // autotuner: problem-size bucket -> points per thread
+  // autotuner: problem-size bucket -> (points per thread, rotations per work item)
+  std::map<std::string, std::pair<int, int>> tuned;
+  int64_t last_p_mask = 0;   // points-per-thread shapes of the last blocking call's passes (bit P)
+  int64_t last_tile_max = 0; // largest rotations per work item among them
 };
 
 namespace {
@@ -384,6 +393,7 @@ struct Job {
   int Ep[3] = {0, 0, 0};  // vote layout extents: E padded to odd values
   bool fused = false;
   int sparse = 0;  // culled vote: 0 no, 1 32-point groups, 2 paired 64-point groups
+  int tile = 0;    // rotations per work item picked by the autotuner (0: the launch's default)
   // device scratch
   DevMem mem;
   int4* kv = nullptr;
@@ -644,10 +654,15 @@ size_t job_bytes(const Job& j) {
   return b;
 }
 
-// Allocate scratch, upload inputs, build per-call grids, reset accumulators.
-void stage_setup(dses_ctx* c, Job& j) {
+// Scratch and inputs of a job: carve its device scratch, the target's cell
+// list at its epsilon, and the source cloud on the device.
+void stage_inputs(dses_ctx* c, Job& j) {
   cudaStream_t s = c->stream;
   j.mem.s = s;
+  if (c->opt.fail_next_allocs > 0) {
+    --c->opt.fail_next_allocs;
+    throw Error{DSES_ERR_OOM, "scratch allocation refused (fail_next_allocs test hook)"};
+  }
   carve(j);
   j.cl = cell_list(c, j.T, j.eps);
   if (j.Xown) {
@@ -657,6 +672,23 @@ void stage_setup(dses_ctx* c, Job& j) {
   } else {
     j.X = j.prob->src;
   }
+}
+
+// Zeroed accumulators (M*, max V, candidate counts, votes), an empty argmin
+// key and NaN costs (a rotation that is never scored keeps NaN).
+void stage_reset(dses_ctx* c, Job& j) {
+  cudaStream_t s = c->stream;
+  CK(cudaMemsetAsync(j.acc, 0, 16, s));
+  CK(cudaMemsetAsync(j.n_cand, 0, 8, s));
+  CK(launch_fill_u64(j.best, ~0ull, 1, s));
+  CK(cudaMemsetAsync(j.best + 1, 0, 8, s));
+  if (j.n_total > 0) CK(launch_fill_f32(j.cost, NAN, (size_t)j.n_total, s));
+}
+
+// Allocate scratch, upload inputs, build per-call grids, reset accumulators.
+void stage_setup(dses_ctx* c, Job& j) {
+  cudaStream_t s = c->stream;
+  stage_inputs(c, j);
   const dses_rotation_grid& g = j.prob->grid;
   if (g.kind == DSES_GRID_HOPF) {
     j.rot = hopf_grid(c, g.hopf_n);
@@ -670,11 +702,7 @@ void stage_setup(dses_ctx* c, Job& j) {
                        cudaMemcpyHostToDevice, s));
     j.rot = j.rot_own;
   }
-  CK(cudaMemsetAsync(j.acc, 0, 16, s));
-  CK(cudaMemsetAsync(j.n_cand, 0, 8, s));
-  CK(launch_fill_u64(j.best, ~0ull, 1, s));
-  CK(cudaMemsetAsync(j.best + 1, 0, 8, s));
-  CK(launch_fill_f32(j.cost, NAN, (size_t)j.n_total, s));
+  stage_reset(c, j);
 }
 
 // Vote items per source chunk the sparse path aims for (a few per warp).
@@ -787,13 +815,21 @@ void launch_pass(dses_ctx* c, const std::vector<PassPart>& parts, int P) {
   int hist = 16;
   for (auto& pp : parts) total_rot += pp.r1 - pp.r0;
   const int tile = tile_rotations(c, total_rot);
+  // a tuned tile is kept below the size that leaves fewer than ~32 tiles per
+  // SM in this launch (the launch's tail)
+  const int tile_cap = (int)std::max<int64_t>(1, total_rot / ((int64_t)c->sms * 32));
+  c->last_p_mask |= 1LL << P;
   for (auto& pp : parts) {
     PassDesc d = make_desc(*pp.job, P, pp.second);
     d.rot += 9 * pp.r0;
     d.rot_base += (uint32_t)pp.r0;
     d.n_rot = (int)(pp.r1 - pp.r0);
+    d.tile_rot = c->opt.tile_rotations > 0 ? (int)c->opt.tile_rotations
+                 : pp.job->tile > 0         ? std::min(pp.job->tile, tile_cap)
+                                            : tile;
+    c->last_tile_max = std::max<int64_t>(c->last_tile_max, d.tile_rot);
     descs.push_back(d);
-    prefix.push_back(prefix.back() + (int)((d.n_rot + tile - 1) / tile));
+    prefix.push_back(prefix.back() + (int)((d.n_rot + d.tile_rot - 1) / d.tile_rot));
     rprefix.push_back(rprefix.back() + d.n_rot);
     hist = std::max(hist, pp.job->hist_bytes);
   }
@@ -943,10 +979,56 @@ void stage_finalize(dses_ctx* c, std::vector<Job*>& jobs) {
   m.release();
 }
 
-// Autotuner: points per thread of the vote for a problem-size bucket, chosen
-// once per bucket by timing each candidate on a slice of the problem's own
-// rotations (the trial only rewrites per-rotation values the pass rewrites
-// identically).
+// Autotuner: the vote's launch shape for a problem-size bucket, chosen once
+// per bucket by timing trial launches on an even-stride sample of the
+// problem's own rotations (the trials rewrite only per-rotation values that
+// the pass rewrites identically): first the points per thread (1, 2, 4, 8)
+// with one rotation per work item, then, for that shape, the rotations per
+// work item (1, 2, 4, 8, 16) on a sample holding at least 16 items per SM at
+// the largest. Sets j.tile (capped per launch, see launch_pass) and returns
+// the points per thread.
+float time_vote_trial(dses_ctx* c, Job& j, const float* rot, int64_t n, int P, int tile) {
+  std::vector<PassDesc> d{make_desc(j, P, false)};
+  d[0].rot = rot;
+  d[0].n_rot = (int)n;
+  d[0].tile_rot = tile;
+  set_chunks(d[0], pass_src_bytes(j.hist_bytes, j.N));
+  const int tiles = (int)((n + tile - 1) / tile);
+  std::vector<int> tp{0, tiles}, rp{0, (int)n};
+  DevMem m;
+  m.alloc(4096, c->stream);
+  char* base = (char*)m.p;
+  CK(cudaMemcpyAsync(base, stage_put(c, d.data(), sizeof(PassDesc)), sizeof(PassDesc), cudaMemcpyHostToDevice,
+                     c->stream));
+  CK(cudaMemcpyAsync(base + 1024, stage_put(c, tp.data(), 8), 8, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(base + 2048, stage_put(c, rp.data(), 8), 8, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemsetAsync(base + 3072, 0, 4, c->stream));
+  PassLaunch L;
+  L.probs = (const PassDesc*)base;
+  L.tile_prefix = (const int*)(base + 1024);
+  L.rot_prefix = (const int*)(base + 2048);
+  L.n_probs = 1;
+  L.tile_rot = tile;
+  L.work_counter = (int*)(base + 3072);
+  L.hist_bytes = j.hist_bytes;
+  L.src_bytes = pass_src_bytes(j.hist_bytes, j.N);
+  L.padded = 0;
+  for (int a = 0; a < 3; ++a) L.padded |= j.Ep[a] != j.E[a] ? 1 : 0;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, c->stream));
+  CK(launch_vote(L, P, j.sparse, std::min<int>(c->sms, tiles), c->stream));
+  CK(cudaEventRecord(e1, c->stream));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  m.release();
+  return ms;
+}
+
 int pick_p(dses_ctx* c, Job& j) {
   // the culled vote has no 8-points-per-thread instance: the shape is settled
   // here, before any descriptor is built for it
@@ -956,80 +1038,61 @@ int pick_p(dses_ctx* c, Job& j) {
     return j.sparse && P == 8 ? 4 : P;
   }
   std::vector<Job*> one{&j};
-  if (!c->opt.autotune) return choose_p(c, one);
+  if (!c->opt.autotune || j.n_first < 1) return choose_p(c, one);
   auto lg = [](int64_t v) { int b = 0; while ((1LL << b) < v) ++b; return b; };
   char key[96];
-  snprintf(key, sizeof(key), "m%d n%d b%d s%d u%d l%d", lg(j.T->m), lg(j.N), lg((int64_t)j.E[0] * j.E[1] * j.E[2]),
-           (int)j.sparse, j.u16, j.lanes);
-  auto it = c->tuned_p.find(key);
-  if (it != c->tuned_p.end()) return it->second;
-  if (c->capturing) return choose_p(c, one);
-  const int64_t slice = std::min<int64_t>(j.n_first, (int64_t)c->sms * 16);
-  // the slice samples the whole grid at an even stride (the grid's first
-  // rotations are one corner of SO(3), which can favour another shape)
-  DevMem strided;
-  const float* rot = j.rot;
-  const int64_t stride = j.n_first / slice;
-  if (stride > 1) {
-    strided.alloc(36 * (size_t)slice, c->stream);
-    CK(cudaMemcpy2DAsync(strided.p, 36, j.rot, 36 * (size_t)stride, 36, (size_t)slice, cudaMemcpyDeviceToDevice,
-                         c->stream));
-    rot = (const float*)strided.p;
+  snprintf(key, sizeof(key), "m%d n%d b%d r%d s%d u%d l%d", lg(j.T->m), lg(j.N),
+           lg((int64_t)j.E[0] * j.E[1] * j.E[2]), lg(j.n_first), (int)j.sparse, j.u16, j.lanes);
+  auto it = c->tuned.find(key);
+  if (it != c->tuned.end()) {
+    j.tile = it->second.second;
+    return it->second.first;
   }
+  if (c->capturing) return choose_p(c, one);
+  // an even-stride sample of the grid (its first rotations are one corner of
+  // SO(3), which can favour another shape)
+  auto sample = [&](int64_t want, DevMem& buf) -> std::pair<const float*, int64_t> {
+    const int64_t n = std::min<int64_t>(j.n_first, want);
+    const int64_t stride = j.n_first / n;
+    if (stride <= 1) return {j.rot, n};
+    buf.alloc(36 * (size_t)n, c->stream);
+    CK(cudaMemcpy2DAsync(buf.p, 36, j.rot, 36 * (size_t)stride, 36, (size_t)n, cudaMemcpyDeviceToDevice,
+                         c->stream));
+    return {(const float*)buf.p, n};
+  };
+  DevMem s1, s2;
+  const auto a = sample((int64_t)c->sms * 16, s1);
   float best_ms = 1e30f;
   int best_p = choose_p(c, one);
-  const int cands[4] = {1, 2, 4, 8};
-  for (int P : cands) {
+  for (int P : {1, 2, 4, 8}) {
     if ((j.sparse && P == 8) || (j.sparse == 2 && P == 1)) continue;
-    std::vector<PassDesc> d{make_desc(j, P, false)};
-    d[0].rot = rot;
-    d[0].n_rot = (int)slice;
-    set_chunks(d[0], pass_src_bytes(j.hist_bytes, j.N));
-    const int tile = 1;
-    std::vector<int> tp{0, (int)slice}, rp{0, (int)slice};
-    DevMem m;
-    m.alloc(4096, c->stream);
-    char* base = (char*)m.p;
-    CK(cudaMemcpyAsync(base, stage_put(c, d.data(), sizeof(PassDesc)), sizeof(PassDesc), cudaMemcpyHostToDevice,
-                       c->stream));
-    CK(cudaMemcpyAsync(base + 1024, stage_put(c, tp.data(), 8), 8, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(base + 2048, stage_put(c, rp.data(), 8), 8, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemsetAsync(base + 3072, 0, 4, c->stream));
-    PassLaunch L;
-    L.probs = (const PassDesc*)base;
-    L.tile_prefix = (const int*)(base + 1024);
-    L.rot_prefix = (const int*)(base + 2048);
-    L.n_probs = 1;
-    L.tile_rot = tile;
-    L.work_counter = (int*)(base + 3072);
-    L.hist_bytes = j.hist_bytes;
-    L.src_bytes = pass_src_bytes(j.hist_bytes, j.N);
-    L.padded = 0;
-    for (int a = 0; a < 3; ++a) L.padded |= j.Ep[a] != j.E[a] ? 1 : 0;
-    cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
-    CK(cudaEventRecord(e0, c->stream));
-    CK(launch_vote(L, P, j.sparse, std::min<int>(c->sms, (int)slice), c->stream));
-    CK(cudaEventRecord(e1, c->stream));
-    CK(cudaEventSynchronize(e1));
-    float ms = 0;
-    CK(cudaEventElapsedTime(&ms, e0, e1));
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    m.release();
+    const float ms = time_vote_trial(c, j, a.first, a.second, P, 1);
     if (ms < best_ms) {
       best_ms = ms;
       best_p = P;
     }
   }
-  c->tuned_p[key] = best_p;
+  const auto b = sample((int64_t)c->sms * 16 * 16, s2);
+  int best_tile = 1;
+  best_ms = 1e30f;
+  for (int tile : {1, 2, 4, 8, 16}) {
+    if (tile > 1 && b.second / tile < (int64_t)c->sms * 4) break;  // too few items per SM to tell
+    const float ms = time_vote_trial(c, j, b.first, b.second, best_p, tile);
+    if (ms < best_ms * 0.99f) {  // a larger tile must win by 1%
+      best_ms = ms;
+      best_tile = tile;
+    }
+  }
+  c->tuned[key] = {best_p, best_tile};
+  j.tile = best_tile;
   return best_p;
 }
 
 // The whole pipeline for a set of jobs; results land in each job's device
 // result slot. No host synchronisation inside (except autotuner trials).
 void run_pipeline(dses_ctx* c, std::vector<Job*>& jobs) {
+  c->last_p_mask = 0;
+  c->last_tile_max = 0;
   for (auto* j : jobs) stage_setup(c, *j);
   // one persistent launch per (points-per-thread shape, culled mode): key
   // 4 P + mode (normally one launch)
@@ -1048,6 +1111,186 @@ void run_pipeline(dses_ctx* c, std::vector<Job*>& jobs) {
   for (auto* j : jobs)
     if (j->rtop > 0) stage_candidates(c, *j, true);
   stage_finalize(c, jobs);
+}
+
+void collect_timing(dses_ctx* c);
+
+// ---------------------------------------------------------------------------
+// Rotation sharding of one registration. Algorithm 2 treats every rotation on
+// its own, so shard `rank` of `world` runs the contiguous ranges of the grid
+// and of the second pass that dses_shard_range gives it; the shards meet only
+// where the algorithm reduces over all rotations (exchange.h): M* for the q
+// filter, the top-k keys, the second pass's centres and the final argmin. An
+// exchange is an all-gather of a few bytes per shard through the caller's
+// callback; without one (dses_register_shard) no reduction may cross shards.
+
+struct Exchange {
+  dses_allgather_fn fn = nullptr;
+  void* user = nullptr;
+  int world = 1;
+  template <class T>
+  std::vector<T> all(const T* send, size_t count) {
+    std::vector<T> recv(count * (size_t)world);
+    if (fn(user, send, (int64_t)(sizeof(T) * count), recv.data()) != 0)
+      throw Error{DSES_ERR_EXCHANGE, "the all-gather callback of a sharded registration failed"};
+    return recv;
+  }
+};
+
+// Candidate stage of one pass of a shard: the q filter against the M* of all
+// shards, or the top-k by (M desc, index asc) over all shards; then scoring
+// and the argmin of the shard's own candidates.
+void shard_candidates(dses_ctx* c, Job& j, bool second, const ShardMap& map, Exchange* X) {
+  if (j.fused) return;
+  cudaStream_t s = c->stream;
+  const uint32_t first = second ? (uint32_t)j.n_first : 0;
+  const int n = (int)(second ? j.n_fine : j.n_first);
+  uint32_t* cand = j.cand + first;
+  uint32_t* ncand = j.n_cand + (second ? 1 : 0);
+  uint32_t* acc = j.acc + (second ? 2 : 0);
+  if (j.topk > 0) {
+    const int k = j.topk;
+    std::vector<uint64_t> mine((size_t)k, kPadKey);
+    if (n > 0) {
+      CK(launch_keys_from_M(j.M, first, n, 0, j.keys, s));
+      CK(launch_k_smallest(j.keys, n, nullptr, k, j.ks_scratch, j.ksel, s));
+      CK(cudaMemcpyAsync(mine.data(), j.ksel, 8 * (size_t)k, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (auto& key : mine) key = key_to_global(key, map);
+    }
+    const std::vector<uint64_t> glob = X ? merge_k_smallest(X->all(mine.data(), (size_t)k).data(), X->world, k) : mine;
+    std::vector<uint32_t> slots;
+    for (uint64_t key : glob) {
+      uint32_t l = 0;
+      if (key != kPadKey && map.to_local((uint32_t)(key & 0xffffffffull), &l)) slots.push_back(l);
+    }
+    const uint32_t cnt = (uint32_t)slots.size();
+    if (cnt) CK(cudaMemcpyAsync(cand, slots.data(), 4 * (size_t)cnt, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ncand, &cnt, 4, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+  } else {
+    if (X && j.q > 0) {  // M* over all shards (with q = 0 every rotation passes)
+      uint32_t m = 0;
+      if (n > 0) {
+        CK(cudaMemcpyAsync(&m, acc, 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+      }
+      m = merge_max(X->all(&m, 1).data(), X->world);
+      CK(cudaMemcpyAsync(acc, &m, 4, cudaMemcpyHostToDevice, s));
+      CK(cudaStreamSynchronize(s));
+    }
+    if (n > 0) CK(launch_select_q(j.M, first, n, acc, j.q, cand, ncand, s));
+  }
+  if (n < 1) return;
+  const ScoreDesc sd = make_score(j, second);
+  if (j.metric != DSES_METRIC_INLIER) {
+    if (j.nn == DSES_NN_GRID)
+      CK(launch_score_grid(sd, cand, ncand, n, s));
+    else
+      CK(launch_score_brute(sd, cand, ncand, n, s));
+  }
+  CK(launch_argmin(j.cost, j.M, j.N, j.metric, cand, ncand, n, 0, j.best, s));
+}
+
+// The second pass's Euler boxes (all of them, every shard the same): centred
+// on the refine_top_k best first-pass candidates by (cost, index) over all
+// shards, picked from the whole first-pass grid by global index.
+void shard_refine_grid(dses_ctx* c, Job& j, const ShardMap& map, Exchange* X, const float* rot_full,
+                       float* fine_full) {
+  cudaStream_t s = c->stream;
+  const int k = j.rtop;
+  const int n = (int)j.n_first;
+  std::vector<uint64_t> mine((size_t)k, kPadKey);
+  if (n > 0) {
+    if (j.fused)
+      CK(launch_keys_from_cost(j.cost, nullptr, nullptr, n, 0, j.keys, s));
+    else
+      CK(launch_keys_from_cost(j.cost, j.cand, j.n_cand, n, 0, j.keys, s));
+    CK(launch_k_smallest(j.keys, n, j.fused ? nullptr : j.n_cand, k, j.ks_scratch, j.ksel, s));
+    CK(cudaMemcpyAsync(mine.data(), j.ksel, 8 * (size_t)k, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (auto& key : mine) key = key_to_global(key, map);
+  }
+  const std::vector<uint64_t> glob = X ? merge_k_smallest(X->all(mine.data(), (size_t)k).data(), X->world, k) : mine;
+  CK(cudaMemcpyAsync(j.ksel, glob.data(), 8 * (size_t)k, cudaMemcpyHostToDevice, s));
+  if (j.hopf_n > 0)
+    CK(launch_euler_boxes_hopf(j.hopf_n, j.ksel, k, j.rK, j.rdr, fine_full, s));
+  else
+    CK(launch_euler_boxes_keyed(rot_full, j.ksel, k, j.rK, j.rdr, fine_full, s));
+  CK(cudaStreamSynchronize(s));
+}
+
+// One shard of a registration. Returns the shard's own result (rotation index
+// in the whole registration); with an exchange, every shard receives the
+// combined result of all shards instead.
+dses_status run_sharded(dses_ctx* c, const dses_problem* problem, int rank, int world, Exchange* X,
+                        dses_result* out) {
+  Job j;
+  resolve(c, problem, j);
+  plan(c, j);
+  const int64_t n1 = j.n_first, nf = j.n_fine;
+  ShardMap map;
+  int64_t e1 = 0, e2 = 0;
+  dses_shard_range(n1, rank, world, &map.b1, &e1);
+  dses_shard_range(nf, rank, world, &map.b2, &e2);
+  map.n1 = e1 - map.b1;
+  map.n1_total = n1;
+  map.n2 = e2 - map.b2;
+  cudaStream_t s = c->stream;
+  std::vector<Job*> jobs{&j};
+  c->cur_stage = &c->stage;
+  c->stage.reserve(stage_bytes(jobs));  // sized for the whole grid (an explicit one is uploaded whole)
+  c->stage.used = 0;
+  // the whole first-pass grid on the device: the shard's range is a slice of
+  // it, and the second pass picks its centres from it by global index
+  DevMem full1, fine;
+  const float* rot_full = nullptr;
+  const dses_rotation_grid& g = problem->grid;
+  if (g.kind == DSES_GRID_HOPF) {
+    rot_full = hopf_grid(c, g.hopf_n);
+  } else {
+    full1.alloc(align256(36 * (size_t)n1) + 256, s);
+    if (g.kind == DSES_GRID_EULER_BOX) {
+      double* R0 = (double*)((char*)full1.p + align256(36 * (size_t)n1));
+      CK(cudaMemcpyAsync(R0, stage_put(c, g.R0, 72), 72, cudaMemcpyHostToDevice, s));
+      CK(launch_euler_box_single(R0, g.K, g.delta_r, (float*)full1.p, s));
+    } else {
+      if (!finite3(g.explicit_R, 3 * g.n_explicit)) invalid("explicit rotations have a non-finite entry");
+      CK(cudaMemcpyAsync(full1.p, stage_put(c, g.explicit_R, 36 * (size_t)n1), 36 * (size_t)n1,
+                         cudaMemcpyHostToDevice, s));
+    }
+    rot_full = (const float*)full1.p;
+  }
+  j.n_first = map.n1;
+  j.n_fine = map.n2;
+  j.n_total = j.n_first + j.n_fine;
+  stage_inputs(c, j);
+  j.rot = rot_full + 9 * map.b1;
+  stage_reset(c, j);
+  const int P = pick_p(c, j);
+  if (j.n_first > 0) launch_pass(c, {{&j, false, 0, j.n_first}}, P);
+  shard_candidates(c, j, false, map, X);
+  if (j.rtop > 0) {
+    fine.alloc(36 * (size_t)nf + 256, s);
+    shard_refine_grid(c, j, map, X, rot_full, (float*)fine.p);
+    j.rot_fine = (float*)fine.p + 9 * map.b2;
+    if (j.n_fine > 0) launch_pass(c, {{&j, true, 0, j.n_fine}}, P);
+    shard_candidates(c, j, true, map, X);
+  }
+  stage_finalize(c, jobs);
+  dses_result r;
+  CK(cudaMemcpyAsync(&r, j.res, sizeof(r), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  collect_timing(c);
+  if (r.rot_index >= 0) r.rot_index = map.to_global((uint32_t)r.rot_index);
+  if (!X) {
+    *out = r;
+    return (dses_status)r.status;
+  }
+  const std::vector<dses_result> parts = X->all(&r, 1);
+  const dses_status st = dses_combine_results(parts.data(), world, out);
+  if (st != DSES_OK && st != DSES_ERR_NO_CANDIDATE) throw Error{DSES_ERR_EXCHANGE, "a shard's result was an error"};
+  return st;
 }
 
 // ---------------------------------------------------------------------------
@@ -1148,7 +1391,8 @@ void worker_loop(dses_ctx* c) {
       }
     }
     if (schedulable()) {
-      std::lock_guard<std::recursive_mutex> g(c->mu);
+      std::lock_guard<std::recursive_mutex> g(c->mu);  // taken after smu is released (submit nests smu in mu)
+      c->serve_max_active = std::max<int64_t>(c->serve_max_active, (int64_t)active.size());
       Flight f;
       bool launched = false;
       {
@@ -1668,6 +1912,55 @@ dses_status dses_debug_per_rotation(dses_ctx* c, const dses_problem* problem, in
   return gs != DSES_OK ? gs : st;
 }
 
+dses_status dses_debug_per_rotation_batch(dses_ctx* c, const dses_problem* problems, int32_t n,
+                                          int32_t* const* k_star, uint32_t* const* votes, uint32_t* const* inliers,
+                                          float* const* cost, dses_result* out) {
+  if (!c) return DSES_ERR_INVALID_ARG;
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  dses_status st = DSES_OK;
+  dses_status gs = guard(c, [&] {
+    if (!problems || !out || n < 1) invalid("batch needs problems, out and n >= 1");
+    set_device(c);
+    std::vector<std::unique_ptr<Job>> owned;
+    std::vector<Job*> jobs;
+    for (int i = 0; i < n; ++i) {
+      owned.emplace_back(new Job());
+      resolve(c, &problems[i], *owned.back());
+      plan(c, *owned.back());
+      jobs.push_back(owned.back().get());
+    }
+    c->cur_stage = &c->stage;
+    c->stage.reserve(stage_bytes(jobs));
+    c->stage.used = 0;
+    run_pipeline(c, jobs);  // the batch's persistent launches, as dses_register_batch runs them
+    std::vector<std::vector<int4>> kv(jobs.size());
+    std::vector<std::vector<uint32_t>> M(jobs.size());
+    std::vector<std::vector<float>> C(jobs.size());
+    for (size_t b = 0; b < jobs.size(); ++b) {
+      const size_t m = (size_t)jobs[b]->n_total;
+      kv[b].resize(m);
+      M[b].resize(m);
+      C[b].resize(m);
+      CK(cudaMemcpyAsync(kv[b].data(), jobs[b]->kv, 16 * m, cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaMemcpyAsync(M[b].data(), jobs[b]->M, 4 * m, cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaMemcpyAsync(C[b].data(), jobs[b]->cost, 4 * m, cudaMemcpyDeviceToHost, c->stream));
+    }
+    st = finish_results(c, jobs, out);
+    for (size_t b = 0; b < jobs.size(); ++b)
+      for (size_t i = 0; i < kv[b].size(); ++i) {
+        if (k_star && k_star[b]) {
+          k_star[b][3 * i] = kv[b][i].x;
+          k_star[b][3 * i + 1] = kv[b][i].y;
+          k_star[b][3 * i + 2] = kv[b][i].z;
+        }
+        if (votes && votes[b]) votes[b][i] = (uint32_t)kv[b][i].w;
+        if (inliers && inliers[b]) inliers[b][i] = M[b][i];
+        if (cost && cost[b]) cost[b][i] = C[b][i];
+      }
+  });
+  return gs != DSES_OK ? gs : st;
+}
+
 dses_status dses_submit(dses_ctx* c, const dses_problem* problem, uint64_t* ticket) {
   if (!c || !problem || !ticket) return DSES_ERR_INVALID_ARG;
   std::lock_guard<std::recursive_mutex> g(c->mu);
@@ -1792,38 +2085,26 @@ dses_status dses_register_shard(dses_ctx* c, const dses_problem* problem, int32_
     if (world < 1 || rank < 0 || rank >= world) invalid("shard rank must be in [0, world)");
     const dses_params& P = problem->params;
     if (P.q_milli != 0 || P.top_k != 0 || P.refine_top_k != 0)
-      invalid("a shard scores every rotation of its range: q_milli, top_k and refine_top_k must be 0");
-    std::vector<float> R;
-    const float* all = nullptr;
-    int64_t n = 0;
-    if (problem->grid.kind == DSES_GRID_EXPLICIT) {
-      if (!problem->grid.explicit_R || problem->grid.n_explicit < 1)
-        invalid("explicit grid needs explicit_R and n_explicit >= 1");
-      all = problem->grid.explicit_R;
-      n = problem->grid.n_explicit;
-    } else {
-      n = build_grid_host(c, &problem->grid, nullptr, 0);
-      R.resize(9 * (size_t)n);
-      build_grid_host(c, &problem->grid, R.data(), n);
-      all = R.data();
-    }
-    int64_t b = 0, e = 0;
-    dses_shard_range(n, rank, world, &b, &e);
-    if (e == b) {  // more shards than rotations: this one has none
-      std::memset(out, 0, sizeof(*out));
-      out->rot_index = -1;
-      out->cost = std::numeric_limits<float>::quiet_NaN();
-      out->status = DSES_ERR_NO_CANDIDATE;
-      st = DSES_ERR_NO_CANDIDATE;
-      return;
-    }
-    dses_problem part = *problem;
-    part.grid.kind = DSES_GRID_EXPLICIT;
-    part.grid.explicit_R = all + 9 * b;
-    part.grid.n_explicit = e - b;
-    st = dses_register_batch(c, &part, 1, out);
-    if (st != DSES_OK && st != DSES_ERR_NO_CANDIDATE) throw Error{st, dses_last_error(c)};
-    if (out->rot_index >= 0) out->rot_index += b;
+      invalid("a shard without an exchange scores every rotation of its range: q_milli, top_k and refine_top_k "
+              "must be 0 (dses_register_sharded exchanges what they need)");
+    st = run_sharded(c, problem, rank, world, nullptr, out);
+  });
+  return gs != DSES_OK ? gs : st;
+}
+
+dses_status dses_register_sharded(dses_ctx* c, const dses_problem* problem, int32_t rank, int32_t world,
+                                  dses_allgather_fn allgather, void* user, dses_result* out) {
+  if (!c || !problem || !out || !allgather) return DSES_ERR_INVALID_ARG;
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  dses_status st = DSES_OK;
+  const dses_status gs = guard(c, [&] {
+    set_device(c);
+    if (world < 1 || rank < 0 || rank >= world) invalid("shard rank must be in [0, world)");
+    Exchange X;
+    X.fn = allgather;
+    X.user = user;
+    X.world = world;
+    st = run_sharded(c, problem, rank, world, &X, out);
   });
   return gs != DSES_OK ? gs : st;
 }
@@ -2048,12 +2329,16 @@ static int64_t* option_slot(dses_ctx* c, const char* key) {
   if (k == "serve_iter_pairs") return &o.serve_iter_pairs;
   if (k == "record_timing") return &o.record_timing;
   if (k == "vote_sparse") return &o.vote_sparse;
+  if (k == "fail_next_allocs") return &o.fail_next_allocs;
+  if (k == "serve_max_active") return &c->serve_max_active;
   if (k == "last_pass_ns") return &c->pass_ns;
   if (k == "last_pass_launches") return &c->pass_launches;
   if (k == "last_count_ns") return &c->count_ns;
   if (k == "last_votes_total") return &c->votes_total;
   if (k == "last_vote_sparse") return &c->vote_sparse_jobs;
   if (k == "last_vote_paired") return &c->vote_paired_jobs;
+  if (k == "last_p_mask") return &c->last_p_mask;
+  if (k == "last_tile_max") return &c->last_tile_max;
   if (k == "graphs_cached") {
     c->graph_count = (int64_t)c->graphs.size();
     return &c->graph_count;
@@ -2081,9 +2366,12 @@ dses_status dses_set_option(dses_ctx* c, const char* key, int64_t value) {
       ok = value == 0 || value == 1;
     else if (k == "last_pass_ns" || k == "last_pass_launches" || k == "kernel_launches" || k == "last_count_ns" ||
              k == "last_votes_total" || k == "last_vote_sparse" || k == "last_vote_paired" ||
+             k == "last_p_mask" || k == "last_tile_max" ||
              k == "graphs_cached")
       ok = false;  // read-only
     else if (k == "tile_rotations") ok = value >= 0 && value <= 4096;
+    else if (k == "fail_next_allocs") ok = value >= 0;
+    else if (k == "serve_max_active") ok = value == 0;  // reset only
     else ok = value >= 1;
     if (!ok) invalid("option value out of range for " + k);
     *slot = value;
@@ -2113,6 +2401,7 @@ const char* dses_status_string(dses_status s) {
     case DSES_ERR_TIMEOUT: return "DSES_ERR_TIMEOUT";
     case DSES_ERR_NO_CANDIDATE: return "DSES_ERR_NO_CANDIDATE";
     case DSES_ERR_UNKNOWN_TICKET: return "DSES_ERR_UNKNOWN_TICKET";
+    case DSES_ERR_EXCHANGE: return "DSES_ERR_EXCHANGE";
   }
   return "unknown status";
 }

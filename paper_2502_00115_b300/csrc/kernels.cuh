@@ -51,6 +51,7 @@ struct PassDesc {
   const float* rot;      // rotations of this pass, 9 floats each (row-major)
   int N, M;
   int n_rot;             // rotations in this pass
+  int tile_rot;          // rotations per work item of this problem (0: the launch's tile_rot)
   uint32_t rot_base;     // global rotation index of rot[0]
   // translation lattice (Lemma 1 discretised): k = floor((y - R x)/delta + 1/2)
   float inv_delta, delta;

@@ -88,3 +88,189 @@ def test_shards_refuse_filters_and_second_passes(ctx):
         assert st == capi.DSES_ERR_INVALID_ARG
     ctx.register(pb)  # the context stays usable
     ctx.destroy_target(t)
+
+
+# ---------------------------------------------------------------------------
+# dses_register_sharded: filters and the second pass across shards. The
+# shards run as host threads of one process, one context each, all on device
+# 0; they meet only in the all-gather callback (a host barrier), so no kernel
+# of one shard waits on another's.
+
+
+class ThreadGather:
+    """An all-gather among `world` host threads (the exchange of
+    dses_register_sharded), with a bounded wait."""
+
+    def __init__(self, world):
+        import threading
+
+        self.world = world
+        self.barrier = threading.Barrier(world, timeout=120)
+        self.slots = [None] * world
+        self.calls = [0] * world
+
+    def callback(self, rank):
+        def gather(mine):
+            self.calls[rank] += 1
+            self.slots[rank] = mine
+            self.barrier.wait()
+            out = list(self.slots)
+            self.barrier.wait()
+            return out
+
+        return capi.make_allgather(gather)
+
+
+def run_sharded_threads(problem_for_rank, world):
+    """problem_for_rank(ctx) -> dses_problem (each rank builds its own target in
+    its own context); returns every rank's combined result and exchange count."""
+    import threading
+
+    g = ThreadGather(world)
+    out, errs = [None] * world, []
+
+    def work(rank):
+        try:
+            with capi.Context(0) as c:
+                pb = problem_for_rank(c)
+                cb = g.callback(rank)
+                out[rank] = c.register_sharded(pb, rank, world, cb)
+        except Exception as e:  # reported by the main thread
+            errs.append(e)
+            g.barrier.abort()
+
+    ths = [threading.Thread(target=work, args=(r,)) for r in range(world)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join(timeout=300)
+    assert not errs, errs
+    assert all(r is not None for r in out)
+    assert len(set(g.calls)) == 1  # every shard made the same exchanges
+    return out, g.calls[0]
+
+
+FILTERS = [dict(q_milli=900), dict(top_k=10), dict(refine_top_k=4, refine_K=1, refine_delta_r=math.radians(2.0)),
+           dict(q_milli=600, refine_top_k=3, refine_K=1, refine_delta_r=math.radians(1.5)),
+           dict(top_k=6, refine_top_k=2, refine_K=2, refine_delta_r=math.radians(1.0), nn_mode="brute")]
+
+
+@pytest.mark.parametrize("world", [2, 3])
+@pytest.mark.parametrize("over", FILTERS, ids=["q900", "top10", "refine4", "q600_refine3", "top6_refine2_brute"])
+def test_sharded_filters_and_second_pass_equal_whole(ctx, world, over):
+    import oracle
+
+    p = synth.tiny_problem(1, hopf_n=3)
+    pr = capi.make_params(metric="trunc_l1", epsilon=p.epsilon, tau=p.tau, t_half=p.t_half, **over)
+    tw = ctx.create_target(p.Y, grid_cap=2 * p.tau)
+    whole = ctx.register(ctx.problem(tw, p.X, capi.hopf_grid(3), pr))
+    ctx.destroy_target(tw)
+    parts, n_x = run_sharded_threads(
+        lambda c: c.problem(c.create_target(p.Y, grid_cap=2 * p.tau), p.X, capi.hopf_grid(3), pr), world)
+    for r in parts:
+        same(r, whole)
+    # the exchanges: M* / top-k per pass, second-pass centres, results
+    assert n_x >= 2 if ("q_milli" in over or "top_k" in over or "refine_top_k" in over) else n_x == 1
+    # and the oracle's registration of the same problem
+    f32 = lambda v: float(np.float32(v))
+    P = oracle.make_params(metric="trunc_l1", epsilon=f32(p.epsilon), tau=f32(p.tau), t_half=[f32(v) for v in p.t_half],
+                           q_milli=over.get("q_milli", 0), top_k=over.get("top_k", 0),
+                           nn_mode=over.get("nn_mode", "grid"), grid_cap=f32(2 * p.tau),
+                           refine_top_k=over.get("refine_top_k", 0), refine_K=over.get("refine_K", 0),
+                           refine_delta_r=over.get("refine_delta_r", 0.0))
+    ref = oracle.register(p.X, p.Y, oracle.hopf_grid(3), P)
+    if whole.rot_index != ref.rot_index:  # a near-tie of the oracle's own costs only
+        assert abs(ref.costs[whole.rot_index] - ref.costs[ref.rot_index]) <= 1e-4 * abs(ref.costs[ref.rot_index]) + 1e-6
+    else:
+        assert whole.inliers == ref.inliers and whole.votes == ref.votes
+
+
+def test_sharded_euler_explicit_grids_and_empty_shards(ctx):
+    p = synth.tiny_problem(3)
+    over = dict(q_milli=800, refine_top_k=2, refine_K=1, refine_delta_r=math.radians(1.0))
+    pr = capi.make_params(metric="trunc_l1", epsilon=p.epsilon, tau=p.tau, t_half=(0.5, 0.5, 0.5), **over)
+    tw = ctx.create_target(p.Y, grid_cap=2 * p.tau)
+    box = capi.euler_box_grid(p.R_true, 1, math.radians(4.0))  # 27 rotations: some of 4 shards get 6
+    whole = ctx.register(ctx.problem(tw, p.X, box, pr))
+    parts, _ = run_sharded_threads(
+        lambda c: c.problem(c.create_target(p.Y, grid_cap=2 * p.tau), p.X, box, pr), 4)
+    for r in parts:
+        same(r, whole)
+    R = ctx.rotation_grid(capi.hopf_grid(1))[:5]  # 5 rotations over 7 shards: two without any
+    g, keep = capi.explicit_grid(R)
+    whole = ctx.register(ctx.problem(tw, p.X, g, pr))
+    parts, _ = run_sharded_threads(
+        lambda c: c.problem(c.create_target(p.Y, grid_cap=2 * p.tau), p.X, g, pr), 7)
+    for r in parts:
+        same(r, whole)
+    ctx.destroy_target(tw)
+
+
+def test_sharded_culled_robot_like_with_second_pass(ctx):
+    p = synth.robot_like_problem(0, hopf_n=2)
+    pr = capi.make_params(metric=p.metric, epsilon=p.epsilon, tau=p.tau, huber_h=p.huber_h, t_half=p.t_half,
+                          refine_top_k=p.refine_top_k, refine_K=p.refine_K, refine_delta_r=p.refine_delta_r)
+    tw = ctx.create_target(p.Y, grid_cap=p.grid_cap)
+    whole = ctx.register(ctx.problem(tw, p.X, capi.hopf_grid(2), pr))
+    ctx.destroy_target(tw)
+    parts, _ = run_sharded_threads(
+        lambda c: c.problem(c.create_target(p.Y, grid_cap=p.grid_cap), p.X, capi.hopf_grid(2), pr), 2)
+    for r in parts:
+        same(r, whole)
+
+
+def test_sharded_exchange_failure_is_reported(ctx):
+    p = synth.tiny_problem(0, hopf_n=1)
+    t = ctx.create_target(p.Y, grid_cap=2 * p.tau)
+    pb = ctx.problem(t, p.X, capi.hopf_grid(1), capi.make_params(epsilon=p.epsilon, tau=p.tau, q_milli=900))
+    bad = capi.make_allgather(lambda mine: [mine, mine[:-1]])  # a short part: the callback reports failure
+    st, _ = capi.dses_register_sharded(ctx.h, pb, 0, 2, bad)
+    assert st == capi.DSES_ERR_EXCHANGE
+    ctx.register(pb)  # the context stays usable
+    ctx.destroy_target(t)
+
+
+def test_two_contexts_in_two_threads_match_the_oracle():
+    # two contexts on device 0 driven concurrently from two host threads (the
+    # vote kernel's shared-memory opt-in and every cache are per context or
+    # per device); each thread's results equal the oracle's
+    import threading
+
+    import oracle
+
+    f32 = lambda v: float(np.float32(v))
+    probs = [synth.tiny_problem(s, hopf_n=2) for s in (11, 12, 13, 14)]
+    refs = []
+    for p in probs:
+        P = oracle.make_params(metric="trunc_l1", epsilon=f32(p.epsilon), tau=f32(p.tau),
+                               t_half=[f32(v) for v in p.t_half], grid_cap=f32(2 * p.tau))
+        refs.append(oracle.register(p.X, p.Y, oracle.hopf_grid(2), P))
+    got, errs = {}, []
+
+    def work(k):
+        try:
+            with capi.Context(0) as c:
+                for rep in range(3):
+                    for i in range(k, len(probs), 2):
+                        p = probs[i]
+                        t = c.create_target(p.Y, grid_cap=2 * p.tau)
+                        pr = capi.make_params(metric="trunc_l1", epsilon=p.epsilon, tau=p.tau, t_half=p.t_half)
+                        got[(i, rep)] = capi.result_dict(c.register(c.problem(t, p.X, capi.hopf_grid(2), pr)))
+                        c.destroy_target(t)
+        except Exception as e:
+            errs.append(e)
+
+    ths = [threading.Thread(target=work, args=(k,)) for k in (0, 1)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join(timeout=300)
+    assert not errs, errs
+    for (i, rep), r in got.items():
+        ref = refs[i]
+        if r["rot_index"] != ref.rot_index:
+            assert abs(ref.costs[r["rot_index"]] - ref.costs[ref.rot_index]) <= 1e-4 * ref.costs[ref.rot_index] + 1e-6
+        else:
+            assert r["inliers"] == ref.inliers and r["votes"] == ref.votes
+        assert abs(r["cost"] - ref.costs[r["rot_index"]]) <= 1e-4 * abs(ref.costs[r["rot_index"]]) + 1e-6 * 128
+    assert len(got) == 3 * len(probs)
