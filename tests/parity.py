@@ -110,3 +110,21 @@ def best_matches(gpu_best: int, ref, costs_oracle_at=None) -> bool:
         return False
     a, b = costs_oracle_at(gpu_best), costs_oracle_at(ref.rot_index)
     return cost_close(a, b, 1)
+
+
+def result_matches_oracle(res: dict, ref, n_src: int) -> None:
+    """A registration's result against the oracle's registration of the same
+    problem: the best index equal (then V and M equal, unless that rotation has
+    boundary pairs or points, and t* equal unless it has boundary pairs), or a
+    near-tie of the oracle's costs; the cost within the cost tolerance of the
+    oracle's cost at the returned rotation."""
+    r = int(res["rot_index"])
+    assert res["status"] == 0 == ref.status, (res["status"], ref.status)
+    if r == ref.rot_index:
+        nbp, nbm = int(ref.n_boundary_pairs[r]), int(ref.n_boundary_points[r])
+        assert res["votes"] == ref.votes or nbp > 0, (res["votes"], ref.votes)
+        assert res["inliers"] == ref.inliers or nbm > 0 or nbp > 0, (res["inliers"], ref.inliers)
+        assert np.allclose(res["t"], ref.t, atol=1e-6) or nbp > 0, (res["t"], ref.t)
+    else:
+        assert cost_close(ref.costs[r], ref.costs[ref.rot_index], 1), (r, ref.rot_index)
+    assert cost_close(res["cost"], ref.costs[r], n_src), (res["cost"], ref.costs[r])

@@ -12,7 +12,7 @@ import pytest
 
 import oracle
 from paper_2502_00115_b300 import build, capi, synth
-from parity import Report, check_rotations, cost_close
+from parity import Report, check_rotations, cost_close, result_matches_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -413,37 +413,6 @@ def test_modelnet_full_size_sampled_rotations(ctx):
     ctx.destroy_target(t)
 
 
-def test_robot_like_full_size_sampled_rotations(ctx):
-    # 2,359,296 coarse rotations + Euler boxes around the best 32 (the culled
-    # vote path); sampled first-pass rotations against the oracle, second-pass
-    # consistency, and pose quality
-    p = synth.robot_like_problem(0)
-    t = ctx.create_target(p.Y, grid_cap=p.grid_cap)
-    gp = gpu_params(p, nn_mode="grid", huber_h=p.huber_h)
-    pb = ctx.problem(t, p.X, capi.hopf_grid(p.hopf_n), gp)
-    n1 = 72 * p.hopf_n**3
-    n = p.n_rotations
-    k, V, M, C, r = ctx.debug(pb, n)
-    assert r.status == 0
-    assert ctx.get_option("last_vote_paired") == 1  # the window spans many 64-point groups
-    P = oracle_params(p, gp, p.grid_cap)
-    rng = np.random.default_rng(1)
-    idx = sorted(set(rng.choice(n1, size=8, replace=False).tolist()) | {int(np.argmax(V[:n1]))})
-    Rs = np.stack([oracle.hopf_rotation(p.hopf_n, i) for i in idx])
-    rep = check_rotations(p.X, p.Y, Rs, P, k, V, M, None, idx)
-    print("parity:", rep.summary())
-    assert rep.ok(), rep.summary()
-    # each second-pass box is centred on one of the best first-pass candidates
-    B = (2 * p.refine_K + 1) ** 3
-    best_first = np.lexsort((np.arange(n1), C[:n1]))[: p.refine_top_k]
-    for c, rc in enumerate(best_first):
-        assert V[n1 + c * B + B // 2] == V[rc] and M[n1 + c * B + B // 2] == M[rc]
-    assert r.cost <= C[:n1].min() + 1e-7
-    ang = np.degrees(np.arccos(np.clip((np.trace(np.array(r.R[:]).reshape(3, 3).T @ p.R_true) - 1) / 2, -1, 1)))
-    assert ang < 3.0, ang
-    ctx.destroy_target(t)
-
-
 def test_culled_modes_agree_on_robot_like(ctx):
     # the paired 64-point-group culling (auto here), the 32-point culling and
     # the dense vote give bit-identical per-rotation (k*, V, M)
@@ -468,6 +437,15 @@ def test_culled_modes_agree_on_robot_like(ctx):
 # batching, special cases, invariances
 
 
+def oracle_ref(p, gp, cap):
+    """The oracle's registration of problem p with the GPU's FP32 parameters
+    (threaded over rotations: the same arithmetic as its single-threaded path)."""
+    import os
+
+    return oracle.register(p.X, p.Y, oracle.hopf_grid(p.hopf_n), oracle_params(p, gp, cap),
+                           threads=os.cpu_count() or 1)
+
+
 def test_batch_equals_solo(ctx):
     probs = [synth.tiny_problem(s, hopf_n=2 + (s % 2)) for s in range(3)]
     probs.append(synth.modelnet_like_problem(9, m=517, keep=0.55, hopf_n=2))
@@ -479,6 +457,8 @@ def test_batch_equals_solo(ctx):
     for a, b in zip(solo, batch):
         assert a["rot_index"] == b["rot_index"] and a["inliers"] == b["inliers"] and a["votes"] == b["votes"]
         assert np.array_equal(a["t"], b["t"]) and a["cost"] == b["cost"] and a["status"] == b["status"] == 0
+    for p, pb, b in zip(probs, pbs, batch):  # and each against the oracle
+        result_matches_oracle(b, oracle_ref(p, pb.params, 2 * p.tau), len(p.X))
     for t in targets:
         ctx.destroy_target(t)
 
@@ -494,13 +474,22 @@ def test_graph_replayed_batches_equal_solo(ctx):
     X1 = [p.X for p in probs]
     rng = np.random.default_rng(5)
     X2 = [(p.X + rng.normal(scale=0.01, size=p.X.shape)).astype(np.float32) for p in probs]
-    for X in (X1, X1, X2, X2):
+    import copy
+
+    refs = {}
+    for tag, X in (("X1", X1), ("X2", X2)):
+        for i, (p, x) in enumerate(zip(probs, X)):
+            q = copy.copy(p)
+            q.X = x
+            refs[(tag, i)] = oracle_ref(q, gpu_params(p, nn_mode="grid"), 2 * p.tau)
+    for tag, X in (("X1", X1), ("X1", X1), ("X2", X2), ("X2", X2)):
         pbs = mk(X)
         batch = [capi.result_dict(r) for r in ctx.register_batch(pbs)]
         solo = [capi.result_dict(ctx.register(pb)) for pb in pbs]
-        for a, b in zip(solo, batch):
+        for i, (a, b) in enumerate(zip(solo, batch)):
             assert a["rot_index"] == b["rot_index"] and a["inliers"] == b["inliers"] and a["votes"] == b["votes"]
             assert np.array_equal(a["t"], b["t"]) and a["cost"] == b["cost"]
+            result_matches_oracle(b, refs[(tag, i)], len(X[i]))
     for t in targets:
         ctx.destroy_target(t)
 
@@ -733,10 +722,11 @@ def test_serving_staggered_arrivals_with_second_pass_equal_solo(ctx):
         assert len(out) == len(tickets)
     finally:
         ctx.set_option("serve_iter_pairs", 30_000_000_000)
-    for tk, a in zip(tickets, solo):
+    for tk, a, p, pb in zip(tickets, solo, probs, pbs):
         b = out[tk]
         assert a["rot_index"] == b["rot_index"] and a["inliers"] == b["inliers"] and a["votes"] == b["votes"]
         assert np.array_equal(a["t"], b["t"]) and a["cost"] == b["cost"]
+        result_matches_oracle(b, oracle_ref(p, pb.params, 2 * p.tau), len(p.X))
     for t in targets:
         ctx.destroy_target(t)
 
@@ -767,9 +757,10 @@ def test_serving_results_equal_solo(ctx):
         assert capi.dses_poll(ctx.h, tickets[0])[0] == capi.DSES_ERR_UNKNOWN_TICKET
     finally:
         ctx.set_option("serve_tile_rotations", 1 << 30)
-    for tk, a in zip(tickets, solo):
+    for tk, a, p, pb in zip(tickets, solo, probs, pbs):
         b = out[tk]
         assert a["rot_index"] == b["rot_index"] and a["inliers"] == b["inliers"] and a["votes"] == b["votes"]
         assert np.array_equal(a["t"], b["t"]) and a["cost"] == b["cost"]
+        result_matches_oracle(b, oracle_ref(p, pb.params, 2 * p.tau), len(p.X))
     for t in targets:
         ctx.destroy_target(t)
