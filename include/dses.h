@@ -322,6 +322,11 @@ dses_status dses_exhaustive_search(dses_ctx* ctx, const dses_problem* problem, f
  *                          packed pairs (pays when the window spans many groups)
  *   "record_timing"        1: time every rotation pass with CUDA events on the
  *                          context's stream
+ *   "target_order"         the vote's order of a target's points, fixed at
+ *                          dses_create_target: 0 (default) recursive bisection
+ *                          along the longest side of the bounding box, cut at
+ *                          multiples of 64 points (compact culling groups); 1
+ *                          Morton order. Results do not depend on it.
  *   "fail_next_allocs"     test hook: the next this-many registrations (blocking or
  *                          served) fail at their scratch allocation with
  *                          DSES_ERR_OOM, as if the device allocator had refused,

@@ -26,7 +26,7 @@ constexpr int kPassThreads = 1024;
 // Source points staged per chunk in shared memory (a float4 each; the packed
 // vote stages two, so half as many per chunk): 32 KB of staging.
 constexpr int kSrcChunk = 2048;
-// Target points per bounding-box group of the Morton-ordered targets.
+// Target points per bounding-box group of the vote-ordered targets.
 constexpr int kGroup = 32;
 // Largest dynamic shared memory a CTA may request on sm_103a (227 KB).
 constexpr int kMaxSmem = 232448;
@@ -41,8 +41,8 @@ struct PassDesc {
   // inputs (device)
   const float* X;        // N x 3 source points
   const float4* Y;       // M target points (cell-sorted; .w unused), inlier count
-  const float4* Yv;      // M target points in Morton order (vote)
-  const float4* gbox;    // per group of kGroup Morton-consecutive targets: min, max
+  const float4* Yv;      // M target points in the vote's order (compact runs)
+  const float4* gbox;    // per group of kGroup consecutive targets of Yv: min, max
   int n_groups;
   // culled paths: keep windows widen by this many lattice units (1e-3 plus
   // 2^-20 of the largest lattice coordinate of the target and the box: far

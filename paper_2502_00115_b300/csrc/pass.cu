@@ -412,13 +412,13 @@ __device__ __forceinline__ void vote_centred_x2(const PassDesc& d, const float4*
 }
 
 // Sparse centred path, for translation boxes small against the target: the
-// P x 32 targets of an item are P groups of 32 Morton-consecutive points with
-// known bounding boxes. For each block of 32 sources the lanes test (source,
-// group) pairs against the source's translation window, widened by a margin
-// of d.cull_margin lattice units (far above the FP32 roundings of w, the
-// staged offsets and the thresholds, so no pair that could vote is dropped);
-// only surviving (source, group) pairs are voted, one group at a time over the
-// set bits of its ballot.
+// P x 32 targets of an item are P groups of 32 consecutive points (in the
+// vote's target order) with known bounding boxes. For each block of 32
+// sources the lanes test (source, group) pairs against the source's
+// translation window, widened by a margin of d.cull_margin lattice units (far
+// above the FP32 roundings of w, the staged offsets and the thresholds, so no
+// pair that could vote is dropped); only surviving (source, group) pairs are
+// voted, one group at a time over the set bits of its ballot.
 
 template <int P, bool U16, bool CUBE>
 __device__ __forceinline__ void vote_centred_sparse(const PassDesc& d, const float4* __restrict__ srcc, int nsrc,
@@ -499,7 +499,7 @@ __device__ __forceinline__ void vote_centred_sparse(const PassDesc& d, const flo
 }
 
 // Paired culled path, for windows that span many target groups (large
-// targets: the robot-like problem): groups of 64 Morton-consecutive targets
+// targets: the robot-like problem): groups of 64 consecutive targets
 // (d.gbox / d.n_groups hold the 64-point boxes in this mode), a lane holding
 // two of each of its item's P / 2 groups (points 64 g + lane and 64 g + 32 +
 // lane) as a packed FP32 pair; one ballot per (32 sources, group), and each
