@@ -78,6 +78,7 @@ def parse():
     ap.add_argument("--duration", type=float, default=60.0, help="serving: arrival window (s)")
     ap.add_argument("--queue-cap", type=int, default=64, help="serving: requests waiting before arrivals are refused")
     ap.add_argument("--seq-sample", type=int, default=400, help="serving: admitted requests re-run as blocking calls")
+    ap.add_argument("--serve-iter-pairs", type=float, default=0, help="serving: pair votes per iteration (0: library default)")
     ap.add_argument("--split", choices=["problems", "rotations"], default="problems",
                     help="robot_like / modelnet_like under torchrun: one problem per rank (weak scaling) or one "
                          "problem's rotations sharded over the ranks (strong scaling)")
@@ -508,6 +509,8 @@ def serving(args, ws, rank, local):
     wl = synth.serving_workload(args.seed, rate=args.rate, duration=args.duration)
     ctx = capi.Context(local)
     ctx.set_option("serve_queue_cap", args.queue_cap)
+    if args.serve_iter_pairs:
+        ctx.set_option("serve_iter_pairs", int(args.serve_iter_pairs))
     tmap = {}
     for i, Y in enumerate(wl.targets):
         tmap[i] = ctx.create_target(Y, grid_cap=0.1)
@@ -523,7 +526,8 @@ def serving(args, ws, rank, local):
     # per-epsilon cell list and per-delta bounds (built on a target's first use)
     for pb in first_of_target.values():
         ctx.register(pb)
-    ctx.set_option("serve_max_active", 0)
+    for key in ("serve_max_active", "serve_busy_ns", "serve_iterations"):
+        ctx.set_option(key, 0)
     pending = {}
     lat, admitted = [], []
     rejected = 0
@@ -550,6 +554,8 @@ def serving(args, ws, rank, local):
         time.sleep(0.0005)
     wall = time.perf_counter() - t0
     max_active = ctx.get_option("serve_max_active")
+    busy_s = ctx.get_option("serve_busy_ns") / 1e9
+    iterations = ctx.get_option("serve_iterations")
     # the same requests as sequential single-problem launches (blocking
     # dses_register one after another): measured service times of the
     # admitted requests (at most --seq-sample of them), and the latencies of a
@@ -567,11 +573,13 @@ def serving(args, ws, rank, local):
     print(json.dumps({
         "workload": "serving", "metric": METRIC, "value": units / wall, "unit": UNIT,
         "offered_rate": args.rate, "arrival_window_s": args.duration, "requests_offered": len(reqs),
+        "serve_iter_pairs": args.serve_iter_pairs or "library default",
         "admitted": len(admitted), "rejected_queue_full": rejected, "queue_cap": args.queue_cap,
         "registrations_per_s": len(lat) / wall, "max_requests_in_flight": max_active,
         "latency_ms": {"p50": 1000 * float(np.percentile(lat, 50)), "p99": 1000 * float(np.percentile(lat, 99)),
                        "max": 1000 * max(lat)},
-        "wall_s": wall,
+        "wall_s": wall, "device_busy_s": busy_s, "iterations": iterations,
+        "device_ms_per_registration": 1000 * busy_s / max(1, len(lat)),
         "sequential": {"registrations_per_s": 1.0 / statistics.mean(svc), "service_ms_mean": 1000 * statistics.mean(svc),
                        "service_sample": len(svc), "fcfs_rejected": seq_rej,
                        "fcfs_latency_ms": {"p50": 1000 * float(np.percentile(seq_lat, 50)),

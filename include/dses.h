@@ -333,6 +333,10 @@ dses_status dses_exhaustive_search(dses_ctx* ctx, const dses_problem* problem, f
  *                          without touching the device; the context stays usable
  *   "serve_max_active"     most requests the serving worker has held admitted at
  *                          once (set to 0 to reset; no other value)
+ *   "serve_busy_ns"        summed device time of the serving worker's iterations, from
+ *                          events at each iteration's first and last queued work
+ *                          (set to 0 to reset)
+ *   "serve_iterations"     serving iterations retired (set to 0 to reset)
  *   "last_pass_ns"         (read-only) summed duration of the vote kernels of the
  *                          last blocking call, in nanoseconds
  *   "last_count_ns"        (read-only) the same for its inlier-count / score kernels

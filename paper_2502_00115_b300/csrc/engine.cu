@@ -194,6 +194,8 @@ struct dses_ctx {
   int64_t vote_paired_jobs = 0;  // ... of which on its paired 64-point-group form
   int64_t graph_count = 0;       // snapshot for the "graphs_cached" option
   int64_t serve_max_active = 0;  // most requests the serving worker held at once (resettable to 0)
+  int64_t serve_busy_ns = 0;     // summed device time of the serving iterations (resettable to 0)
+  int64_t serve_iterations = 0;  // serving iterations retired (resettable to 0)
   // pinned result slots of submitted requests, handed out and returned under
   // smu; allocated in chunks and freed only with the context (pinned frees
   // synchronise the device, which would stall the serving pipeline)
@@ -1376,6 +1378,7 @@ void worker_loop(dses_ctx* c) {
   // so a stage is refilled only after the iteration that read it has completed.
   struct Flight {
     cudaEvent_t ev = nullptr;
+    cudaEvent_t start = nullptr;  // where the iteration's device work begins
     std::vector<std::shared_ptr<Request>> done;
   };
   std::deque<Flight> flights;
@@ -1393,6 +1396,16 @@ void worker_loop(dses_ctx* c) {
     Flight f = flights.front();
     flights.pop_front();
     const cudaError_t e = cudaEventSynchronize(f.ev);
+    if (e == cudaSuccess && f.start) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, f.start, f.ev) == cudaSuccess) {
+        std::lock_guard<std::recursive_mutex> g(c->mu);
+        c->serve_busy_ns += (int64_t)(ms * 1e6);
+        c->serve_iterations += 1;
+      }
+    }
+    cudaGetLastError();
+    if (f.start) cudaEventDestroy(f.start);
     cudaEventDestroy(f.ev);
     for (auto& r : f.done) {
       if (e != cudaSuccess) {
@@ -1449,6 +1462,15 @@ void worker_loop(dses_ctx* c) {
         }
         c->serve_stage[cur].used = 0;
       }
+      if (cudaEventCreate(&f.start) == cudaSuccess) {
+        if (cudaEventRecord(f.start, c->stream) != cudaSuccess) {
+          cudaEventDestroy(f.start);
+          f.start = nullptr;
+        }
+      } else {
+        f.start = nullptr;
+      }
+      cudaGetLastError();
       // set up newly admitted requests
       for (auto& r : active) {
         if (r->state.load() != 0) continue;
@@ -1505,12 +1527,14 @@ void worker_loop(dses_ctx* c) {
           r->state = 3;  // finishing on the device
           f.done.push_back(r);
         }
-        CK(cudaEventCreateWithFlags(&f.ev, cudaEventDisableTiming));
+        CK(cudaEventCreate(&f.ev));
         CK(cudaEventRecord(f.ev, c->stream));
         launched = true;
       } catch (const Error& e) {
         if (f.ev) cudaEventDestroy(f.ev);
         f.ev = nullptr;
+        if (f.start) cudaEventDestroy(f.start);
+        f.start = nullptr;
         // the stream may hold this iteration's work: let it drain first
         cudaStreamSynchronize(c->stream);
         cudaGetLastError();
@@ -2371,6 +2395,8 @@ static int64_t* option_slot(dses_ctx* c, const char* key) {
   if (k == "fail_next_allocs") return &o.fail_next_allocs;
   if (k == "target_order") return &o.target_order;
   if (k == "serve_max_active") return &c->serve_max_active;
+  if (k == "serve_busy_ns") return &c->serve_busy_ns;
+  if (k == "serve_iterations") return &c->serve_iterations;
   if (k == "last_pass_ns") return &c->pass_ns;
   if (k == "last_pass_launches") return &c->pass_launches;
   if (k == "last_count_ns") return &c->count_ns;
@@ -2412,7 +2438,7 @@ dses_status dses_set_option(dses_ctx* c, const char* key, int64_t value) {
     else if (k == "tile_rotations") ok = value >= 0 && value <= 4096;
     else if (k == "fail_next_allocs") ok = value >= 0;
     else if (k == "target_order") ok = value == 0 || value == 1;
-    else if (k == "serve_max_active") ok = value == 0;  // reset only
+    else if (k == "serve_max_active" || k == "serve_busy_ns" || k == "serve_iterations") ok = value == 0;  // reset only
     else ok = value >= 1;
     if (!ok) invalid("option value out of range for " + k);
     *slot = value;
