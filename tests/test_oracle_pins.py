@@ -415,6 +415,41 @@ def test_q_filter_keeps_equality():
     assert np.array_equal(np.isfinite(reg.costs), keep) and reg.rot_index == r_true
 
 
+def test_selection_on_planted_inlier_counts():
+    # Candidate selection against counts fixed by construction, not by the
+    # oracle's own arithmetic: X = Y holds 3 points on the z axis and 7 points
+    # off it; a rotation about z by 180 or 90 degrees leaves only the axis
+    # points on targets (the others land far from every target and outside the
+    # +-delta translation box), the identity leaves all 10. Grid [Rz180, I,
+    # Rz90, I, Rz180] therefore has M = [3, 10, 3, 10, 3], M* = 10, and:
+    # q = 0.3 keeps every rotation (1000 * 3 == 300 * 10: the filter is >=);
+    # q = 0.301 keeps the two identities; top-3 by (M desc, index asc) is
+    # {1, 3, 0}; the best (inlier metric, cost N - M) is rotation 1.
+    delta = 0.05
+    axis = np.array([[0.0, 0.0, -0.4], [0.0, 0.0, 0.1], [0.0, 0.0, 0.45]])
+    off = np.array([[0.7, 0.1, 0.0], [0.3, 0.9, 0.2], [-0.2, 0.6, -0.3], [0.5, -0.8, 0.4],
+                    [0.9, 0.4, -0.6], [0.15, -0.35, 0.7], [-0.55, -0.2, 0.25]])
+    Y = np.vstack([axis, off])
+    X = Y.copy()
+    Rz = lambda deg: Rotation.from_euler("z", deg, degrees=True).as_matrix()
+    grid = np.stack([Rz(180), np.eye(3), Rz(90), np.eye(3), Rz(180)])
+    # the construction: rotated off-axis points are far from every target
+    for R in (Rz(180), Rz(90)):
+        d = np.linalg.norm((off @ R.T)[:, None, :] - Y[None, :, :], axis=2)
+        assert d.min() > 4 * delta
+    want_M = [3, 10, 3, 10, 3]
+    base = dict(metric="inlier", epsilon=delta, t_half=(delta, delta, delta), nn_mode="brute")
+    for q, kept in ((0, [0, 1, 2, 3, 4]), (300, [0, 1, 2, 3, 4]), (301, [1, 3]), (1000, [1, 3])):
+        reg = oracle.register(X, Y, grid, oracle.make_params(q_milli=q, **base))
+        assert reg.M.tolist() == want_M and reg.V.tolist() == want_M
+        assert np.flatnonzero(np.isfinite(reg.costs)).tolist() == kept, q
+        assert reg.rot_index == 1 and reg.inliers == 10
+    reg = oracle.register(X, Y, grid, oracle.make_params(top_k=3, **base))
+    assert sorted(np.flatnonzero(np.isfinite(reg.costs)).tolist()) == [0, 1, 3]
+    reg = oracle.register(X, Y, grid, oracle.make_params(top_k=1, **base))
+    assert np.flatnonzero(np.isfinite(reg.costs)).tolist() == [1]
+
+
 # ---------------------------------------------------------------------------
 # sub-voxel translation refinement (mean of the inlier translations)
 
