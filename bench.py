@@ -48,7 +48,7 @@ OPS_PER_ROT_SRC = 15
 # ncu capture of the current kernel on the same problem at N_side 4 (None: no
 # capture of the current kernel): a launch reads its inputs (KB) once, so the
 # figure does not grow with the rotations and is used unscaled.
-VOTE_DRAM_BYTES = {"robot_like": None, "modelnet_like": None}
+VOTE_DRAM_BYTES = {"robot_like": 642560, "modelnet_like": 262912}
 
 
 def parse():
@@ -152,7 +152,7 @@ def gpu_params(capi, p):
 
 def config_dict(name, p):
     n1 = 72 * p.hopf_n**3
-    box = int(round(2 * p.t_half[0] / p.delta_t)) + 1
+    box = math.floor((p.t_center[0] + p.t_half[0]) / p.delta_t) - math.ceil((p.t_center[0] - p.t_half[0]) / p.delta_t) + 1
     c = {"workload": f"{name}_single_problem", "target_points": int(len(p.Y)), "source_points": int(len(p.X)),
          "rotations": int(p.n_rotations), "rotation_grid": f"hopf N_side={p.hopf_n} ({n1})", "metric": p.metric,
          "tau": p.tau, "epsilon": p.epsilon, "delta_t": p.delta_t,
