@@ -315,7 +315,8 @@ dses_status dses_exhaustive_search(dses_ctx* ctx, const dses_problem* problem, f
  *   "serve_mem_budget"     device bytes the serving worker may hold for requests
  *   "serve_tile_rotations" most rotations one request takes per serving iteration
  *   "serve_iter_pairs"     pair votes per serving iteration (requests in arrival
- *                          order fill it; default 3e10, ~20 ms of vote work)
+ *                          order fill it; default 1.5e11, ~100 ms of vote work:
+ *                          about one request of the serving workload)
  *   "vote_sparse"          0 auto, 1 dense vote, 2 cull (source, 32-point target
  *                          group) pairs outside the translation window (pays for
  *                          small boxes), 3 the same with 64-point groups voted as

@@ -40,6 +40,8 @@ constexpr int kHistBudget = kMaxSmem - kSrcChunk * 16 - kPassStaticSmem;
 struct PassDesc {
   // inputs (device)
   const float* X;        // N x 3 source points
+  const int* Xperm;      // culled paths: the order the vote stages the sources in
+                         // (compact runs of 32), or NULL for the input order
   const float4* Y;       // M target points (cell-sorted; .w unused), inlier count
   const float4* Yv;      // M target points in the vote's order (compact runs)
   const float4* gbox;    // per group of kGroup consecutive targets of Yv: min, max
@@ -103,7 +105,9 @@ struct PassLaunch {
   int tile_rot;            // rotations per work item
   int* work_counter;       // device, zeroed before the launch
   int hist_bytes;          // histogram bytes of shared memory (max over problems)
-  int src_bytes;           // source staging bytes (>= kSrcChunk * 16, a multiple of 32)
+  int src_bytes;           // source staging bytes (a multiple of 32)
+  int blk_bytes;           // culled launches: per 32-source block bounds of the staged
+                           // offsets (8 floats each) after the staging; else 0
   int padded;              // 1: some problem's layout is padded (E != Ev): the
                            // instance whose mode scan skips padding bins
 };
@@ -120,6 +124,20 @@ int pass_smem_bytes(int hist_bytes, int src_bytes);
 // hist_bytes: enough for all of them (32 bytes each) when shared memory
 // allows, at least kSrcChunk * 16.
 int pass_src_bytes(int hist_bytes, int n_src);
+// Shared memory of a rotation-pass launch past the histogram: the source
+// staging and, for a culled launch, the bounds of every block of 32 staged
+// sources (32 bytes each, sized for the plain layout's largest chunk), taken
+// from the staging room.
+inline void pass_staging(int hist_bytes, int n_src_max, bool culled, int* src_bytes, int* blk_bytes) {
+  int src = pass_src_bytes(hist_bytes, n_src_max);
+  int blk = 0;
+  if (culled) {
+    blk = ((src / 16 + 31) / 32) * 32;
+    src = (src - blk) & ~31;
+  }
+  *src_bytes = src;
+  *blk_bytes = blk;
+}
 // Equal chunks of the problem's sources that fit src_bytes of staging, plain
 // and packed (d.chunk).
 inline void set_chunks(PassDesc& d, int src_bytes) {

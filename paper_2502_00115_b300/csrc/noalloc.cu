@@ -177,6 +177,7 @@ extern "C" dses_status dses_vote_static(int device, void* cuda_stream, const flo
     L.work_counter = reinterpret_cast<int*>(base + kOffCounter);
     L.hist_bytes = hist_bytes;
     L.src_bytes = kSrcChunk * 16;
+    L.blk_bytes = 0;
     L.padded = 0;
     if (launch_vote(L, ppt, 0, std::max(1, std::min(sms, tiles)), s) != cudaSuccess) {
       cudaGetLastError();

@@ -411,6 +411,34 @@ __device__ __forceinline__ void vote_centred_x2(const PassDesc& d, const float4*
   }
 }
 
+// The union of an item's G group windows (thr holds 8 floats per group:
+// lo_x, hi_x, lo_y, hi_y, lo_z, hi_z), written after them at thr + 8 G.
+template <int G>
+__device__ __forceinline__ void item_union(float* thr) {
+  float u[6] = {INFINITY, -INFINITY, INFINITY, -INFINITY, INFINITY, -INFINITY};
+#pragma unroll
+  for (int g = 0; g < G; ++g)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      u[2 * a] = fminf(u[2 * a], thr[8 * g + 2 * a]);
+      u[2 * a + 1] = fmaxf(u[2 * a + 1], thr[8 * g + 2 * a + 1]);
+    }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) thr[8 * G + k] = u[k];
+}
+
+// A block of 32 staged sources whose offset bounds (lo/hi per axis, the
+// layout of item_union) miss the item's union window on some axis: none of
+// its sources keeps any of the item's groups (the per-source test compares
+// the same values), so the block is skipped whole.
+__device__ __forceinline__ bool block_misses(const float* __restrict__ b, const float* __restrict__ u) {
+  const float4 b0 = *reinterpret_cast<const float4*>(b);
+  const float2 b1 = *reinterpret_cast<const float2*>(b + 4);
+  const float4 u0 = *reinterpret_cast<const float4*>(u);
+  const float2 u1 = *reinterpret_cast<const float2*>(u + 4);
+  return b0.y < u0.x || b0.x > u0.y || b0.w < u0.z || b0.z > u0.w || b1.y < u1.x || b1.x > u1.y;
+}
+
 // Sparse centred path, for translation boxes small against the target: the
 // P x 32 targets of an item are P groups of 32 consecutive points (in the
 // vote's target order) with known bounding boxes. For each block of 32
@@ -423,7 +451,8 @@ __device__ __forceinline__ void vote_centred_x2(const PassDesc& d, const float4*
 template <int P, bool U16, bool CUBE>
 __device__ __forceinline__ void vote_centred_sparse(const PassDesc& d, const float4* __restrict__ srcc, int nsrc,
                                                     unsigned SX, uint32_t hist_base, int* item_ctr, int lane,
-                                                    float* __restrict__ thr, uint32_t sink) {
+                                                    float* __restrict__ thr, uint32_t sink,
+                                                    const float* __restrict__ blkp) {
   const int n_tchunks = d.n_tchunks, n_sgroups = d.n_sgroups;
   const int n_items = n_tchunks * n_sgroups;
   const int spg = (nsrc + n_sgroups - 1) / n_sgroups;
@@ -458,38 +487,51 @@ __device__ __forceinline__ void vote_centred_sparse(const PassDesc& d, const flo
       }
     }
     __syncwarp();
+    if (blkp && lane == 0) item_union<P>(thr);
+    __syncwarp();
     const int i0 = sg * spg, i1 = min(i0 + spg, nsrc);
-    for (int s0 = i0; s0 < i1; s0 += 32) {
-      const int mine = s0 + lane;
-      const bool valid = mine < i1;
-      const float4 cm = srcc[valid ? mine : i0];
-      uint32_t kmask[P];
+    // the aligned blocks of 32 staged sources that meet [i0, i1), 32 at a
+    // time: a lane tests one block's bounds, and only blocks that can keep a
+    // group are walked
+    for (int bb = i0 >> 5; bb < ((i1 + 31) >> 5); bb += 32) {
+      const int myb = bb + lane;
+      bool rel = myb < ((i1 + 31) >> 5);
+      if (blkp && rel) rel = !block_misses(blkp + 8 * myb, thr + 8 * P);
+      uint32_t bmask = __ballot_sync(0xffffffffu, rel);
+      while (bmask) {
+        const int s0 = (bb + __ffs(bmask) - 1) << 5;
+        bmask &= bmask - 1;
+        const int mine = s0 + lane;  // the aligned block may start before i0
+        const bool valid = mine >= i0 && mine < i1;
+        const float4 cm = srcc[valid ? mine : i0];
+        uint32_t kmask[P];
 #pragma unroll
-      for (int p = 0; p < P; ++p) {
-        const float4 ta = *reinterpret_cast<const float4*>(thr + 8 * p);
-        const float2 tb = *reinterpret_cast<const float2*>(thr + 8 * p + 4);
-        const bool keep = valid && cm.x >= ta.x && cm.x <= ta.y && cm.y >= ta.z && cm.y <= ta.w && cm.z >= tb.x &&
-                          cm.z <= tb.y;
-        kmask[p] = __ballot_sync(0xffffffffu, keep);
-      }
+        for (int p = 0; p < P; ++p) {
+          const float4 ta = *reinterpret_cast<const float4*>(thr + 8 * p);
+          const float2 tb = *reinterpret_cast<const float2*>(thr + 8 * p + 4);
+          const bool keep = valid && cm.x >= ta.x && cm.x <= ta.y && cm.y >= ta.z && cm.y <= ta.w && cm.z >= tb.x &&
+                            cm.z <= tb.y;
+          kmask[p] = __ballot_sync(0xffffffffu, keep);
+        }
 #pragma unroll
-      for (int p = 0; p < P; ++p) {
-        uint32_t m = kmask[p];
-        while (m) {
-          const int j = __ffs(m) - 1;
-          m &= m - 1;
-          const float4 c = srcc[s0 + j];
-          const float wx = __fmaf_rn(ty[p][0], inv, c.x);
-          const float wy = __fmaf_rn(ty[p][1], inv, c.y);
-          const float wz = __fmaf_rn(ty[p][2], inv, c.z);
-          const uint32_t bx = __float_as_uint(__fadd_rn(wx, mx));
-          const uint32_t by = __float_as_uint(__fadd_rn(wy, my));
-          const uint32_t bz = __float_as_uint(__fadd_rn(wz, mz));
-          if (U16) {
-            const uint32_t b = bx * Eyz + (by * Ez + bz);
-            red_or_sink<CUBE>(abase16 + ((b >> 1) << 2), 1u + (b & 1u) * 0xffffu, sinkl, wx, wy, wz, hx, hy, hz);
-          } else {
-            red_or_sink<CUBE>(abase32 + bx * EyzU + (by * EzU + bz * unit), 1u, sinkl, wx, wy, wz, hx, hy, hz);
+        for (int p = 0; p < P; ++p) {
+          uint32_t m = kmask[p];
+          while (m) {
+            const int j = __ffs(m) - 1;
+            m &= m - 1;
+            const float4 c = srcc[s0 + j];
+            const float wx = __fmaf_rn(ty[p][0], inv, c.x);
+            const float wy = __fmaf_rn(ty[p][1], inv, c.y);
+            const float wz = __fmaf_rn(ty[p][2], inv, c.z);
+            const uint32_t bx = __float_as_uint(__fadd_rn(wx, mx));
+            const uint32_t by = __float_as_uint(__fadd_rn(wy, my));
+            const uint32_t bz = __float_as_uint(__fadd_rn(wz, mz));
+            if (U16) {
+              const uint32_t b = bx * Eyz + (by * Ez + bz);
+              red_or_sink<CUBE>(abase16 + ((b >> 1) << 2), 1u + (b & 1u) * 0xffffu, sinkl, wx, wy, wz, hx, hy, hz);
+            } else {
+              red_or_sink<CUBE>(abase32 + bx * EyzU + (by * EzU + bz * unit), 1u, sinkl, wx, wy, wz, hx, hy, hz);
+            }
           }
         }
       }
@@ -513,7 +555,8 @@ __device__ __forceinline__ void vote_centred_sparse(const PassDesc& d, const flo
 template <int P, bool U16>
 __device__ __forceinline__ void vote_centred_paired(const PassDesc& d, const float4* __restrict__ srcd, int nsrc,
                                                     unsigned SX, uint32_t hist_base, int* item_ctr, int lane,
-                                                    float* __restrict__ thr, uint32_t sink) {
+                                                    float* __restrict__ thr, uint32_t sink,
+                                                    const float* __restrict__ blkp) {
   static_assert(P == 2 || P == 4, "two targets of each of P / 2 groups per lane");
   constexpr int Q = P / 2;  // 64-point groups per item
   const int n_tchunks = d.n_tchunks, n_sgroups = d.n_sgroups;
@@ -548,6 +591,8 @@ __device__ __forceinline__ void vote_centred_paired(const PassDesc& d, const flo
       }
     }
     __syncwarp();
+    if (blkp && lane == 0) item_union<Q>(thr);
+    __syncwarp();
     // the lane's target pairs, one per group; padding lanes never vote
     uint64_t yx[Q], yy[Q], yz[Q];
 #pragma unroll
@@ -560,31 +605,42 @@ __device__ __forceinline__ void vote_centred_paired(const PassDesc& d, const flo
       yz[q] = pack2(a.z, b.z);
     }
     const int i0 = sg * spg, i1 = min(i0 + spg, nsrc);
-    for (int s0 = i0; s0 < i1; s0 += 32) {
-      const int mine = s0 + lane;
-      const bool valid = mine < i1;
-      const int ms = valid ? mine : i0;
-      const float4 cm = srcd[2 * ms];  // (c_x, c_x, c_y, c_y)
-      const float cmz = srcd[2 * ms + 1].x;
-      uint32_t kmask[Q];
+    // the aligned blocks of 32 staged sources that meet [i0, i1), 32 at a
+    // time: a lane tests one block's bounds, and only blocks that can keep a
+    // group are walked
+    for (int bb = i0 >> 5; bb < ((i1 + 31) >> 5); bb += 32) {
+      const int myb = bb + lane;
+      bool rel = myb < ((i1 + 31) >> 5);
+      if (blkp && rel) rel = !block_misses(blkp + 8 * myb, thr + 8 * Q);
+      uint32_t bmask = __ballot_sync(0xffffffffu, rel);
+      while (bmask) {
+        const int s0 = (bb + __ffs(bmask) - 1) << 5;
+        bmask &= bmask - 1;
+        const int mine = s0 + lane;  // the aligned block may start before i0
+        const bool valid = mine >= i0 && mine < i1;
+        const int ms = valid ? mine : i0;
+        const float4 cm = srcd[2 * ms];  // (c_x, c_x, c_y, c_y)
+        const float cmz = srcd[2 * ms + 1].x;
+        uint32_t kmask[Q];
 #pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        const float4 ta = *reinterpret_cast<const float4*>(thr + 8 * q);
-        const float2 tb = *reinterpret_cast<const float2*>(thr + 8 * q + 4);
-        const bool keep = valid && cm.x >= ta.x && cm.x <= ta.y && cm.z >= ta.z && cm.z <= ta.w && cmz >= tb.x &&
-                          cmz <= tb.y;
-        kmask[q] = __ballot_sync(0xffffffffu, keep);
-      }
+        for (int q = 0; q < Q; ++q) {
+          const float4 ta = *reinterpret_cast<const float4*>(thr + 8 * q);
+          const float2 tb = *reinterpret_cast<const float2*>(thr + 8 * q + 4);
+          const bool keep = valid && cm.x >= ta.x && cm.x <= ta.y && cm.z >= ta.z && cm.z <= ta.w && cmz >= tb.x &&
+                            cmz <= tb.y;
+          kmask[q] = __ballot_sync(0xffffffffu, keep);
+        }
 #pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        uint32_t m = kmask[q];
-        while (m) {
-          const int j = s0 + __ffs(m) - 1;
-          m &= m - 1;
-          const float4 ca = srcd[2 * j];
-          const float2 cb = *reinterpret_cast<const float2*>(srcd + 2 * j + 1);
-          vote_two_pairs<U16, false>(yx[q], yy[q], yz[q], inv2, pack2(ca.x, ca.y), pack2(ca.z, ca.w),
-                                     pack2(cb.x, cb.y), mx2, my2, mz2, Eyz, Ez, abase, hx, hy, hz, adummy, unit);
+        for (int q = 0; q < Q; ++q) {
+          uint32_t m = kmask[q];
+          while (m) {
+            const int j = s0 + __ffs(m) - 1;
+            m &= m - 1;
+            const float4 ca = srcd[2 * j];
+            const float2 cb = *reinterpret_cast<const float2*>(srcd + 2 * j + 1);
+            vote_two_pairs<U16, false>(yx[q], yy[q], yz[q], inv2, pack2(ca.x, ca.y), pack2(ca.z, ca.w),
+                                       pack2(cb.x, cb.y), mx2, my2, mz2, Eyz, Ez, abase, hx, hy, hz, adummy, unit);
+          }
         }
       }
     }
@@ -713,8 +769,8 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
           __syncthreads();  // previous chunk's readers are done
           if (tid == 0) s_vote_item = 0;
           for (int i = c0 + tid; i < c1; i += kPassThreads) {
-            const float x = __ldg(d.X + 3 * (size_t)i), y = __ldg(d.X + 3 * (size_t)i + 1),
-                        z = __ldg(d.X + 3 * (size_t)i + 2);
+            const size_t si = (SPARSE && d.Xperm) ? (size_t)__ldg(d.Xperm + i) : (size_t)i;
+            const float x = __ldg(d.X + 3 * si), y = __ldg(d.X + 3 * si + 1), z = __ldg(d.X + 3 * si + 2);
             const float ux = fmaf(R[0], x, fmaf(R[1], y, R[2] * z));
             const float uy = fmaf(R[3], x, fmaf(R[4], y, R[5] * z));
             const float uz = fmaf(R[6], x, fmaf(R[7], y, R[8] * z));
@@ -728,26 +784,69 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
             }
           }
           __syncthreads();
-          if (SPARSE == 2 && centred && d.sparse) {
+          // culled launches: the bounds of every block of 32 staged offsets,
+          // so a block whose bounds miss an item's groups is skipped whole
+          const float* blkp = nullptr;
+          if (SPARSE && d.sparse && L.blk_bytes) {
+            float* blk = reinterpret_cast<float*>(smem + L.hist_bytes + L.src_bytes);
+            const int n = c1 - c0, nb = (n + 31) >> 5;
+            for (int b = warp; b < nb; b += kPassThreads / 32) {
+              const int i = b * 32 + lane;
+              float lx = INFINITY, ly = INFINITY, lz = INFINITY, hx = -INFINITY, hy = -INFINITY, hz = -INFINITY;
+              if (i < n) {
+                if (packed) {
+                  const float4 a = srcc[2 * i];
+                  lx = hx = a.x;
+                  ly = hy = a.z;
+                  lz = hz = srcc[2 * i + 1].x;
+                } else {
+                  const float4 a = srcc[i];
+                  lx = hx = a.x;
+                  ly = hy = a.y;
+                  lz = hz = a.z;
+                }
+              }
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) {
+                lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
+                ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
+                lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
+                hx = fmaxf(hx, __shfl_xor_sync(0xffffffffu, hx, o));
+                hy = fmaxf(hy, __shfl_xor_sync(0xffffffffu, hy, o));
+                hz = fmaxf(hz, __shfl_xor_sync(0xffffffffu, hz, o));
+              }
+              if (lane == 0) {
+                *reinterpret_cast<float4*>(blk + 8 * b) = make_float4(lx, hx, ly, hy);
+                *reinterpret_cast<float2*>(blk + 8 * b + 4) = make_float2(lz, hz);
+              }
+            }
+            __syncthreads();
+            blkp = blk;
+          }
+          if (SPARSE == 2) {  // launches of this instance hold paired culled problems only (odd layouts)
             constexpr int PS = P >= 4 ? 4 : 2;  // paired instances are built for 2 and 4
             float* thr = s_thr[SPARSE ? warp : 0];
             const uint32_t sink = (uint32_t)__cvta_generic_to_shared(s_sink);
             if (d.hist_u16)
-              vote_centred_paired<PS, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink);
+              vote_centred_paired<PS, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink, blkp);
             else
-              vote_centred_paired<PS, false>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink);
-          } else if (SPARSE == 1 && centred && d.sparse) {
+              vote_centred_paired<PS, false>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink, blkp);
+          } else if (SPARSE == 1) {  // ... and of this one 32-point culled problems only
             const bool cube = SX == (unsigned)d.E[1] && d.E[1] == d.E[2];
             float* thr = s_thr[SPARSE ? warp : 0];
             const uint32_t sink = (uint32_t)__cvta_generic_to_shared(s_sink);
             if (d.hist_u16 && cube)
-              vote_centred_sparse<P, true, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink);
+              vote_centred_sparse<P, true, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink,
+                                                     blkp);
             else if (d.hist_u16)
-              vote_centred_sparse<P, true, false>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink);
+              vote_centred_sparse<P, true, false>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink,
+                                                     blkp);
             else if (cube)
-              vote_centred_sparse<P, false, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink);
+              vote_centred_sparse<P, false, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink,
+                                                     blkp);
             else
-              vote_centred_sparse<P, false, false>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink);
+              vote_centred_sparse<P, false, false>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink,
+                                                     blkp);
           } else if (centred) {
             constexpr int PP = P >= 2 ? P : 2;  // the P = 1 instance never takes the packed path
             if (packed) {
@@ -1007,7 +1106,7 @@ __global__ void __launch_bounds__(256) count_kernel(PassLaunch L) {
 
 template <int P, int SPARSE, bool PADDED>
 cudaError_t launch_vote_p(const PassLaunch& L, int grid_ctas, cudaStream_t s) {
-  const int smem = pass_smem_bytes(L.hist_bytes, L.src_bytes);
+  const int smem = pass_smem_bytes(L.hist_bytes, L.src_bytes) + L.blk_bytes;
   // the opt-in is per device: a process may launch this instance on several GPUs
   static OptIn optin;
   int dev = 0;

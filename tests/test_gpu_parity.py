@@ -721,7 +721,7 @@ def test_serving_staggered_arrivals_with_second_pass_equal_solo(ctx):
             time.sleep(0.002)
         assert len(out) == len(tickets)
     finally:
-        ctx.set_option("serve_iter_pairs", 30_000_000_000)
+        ctx.set_option("serve_iter_pairs", 150_000_000_000)
     for tk, a, p, pb in zip(tickets, solo, probs, pbs):
         b = out[tk]
         assert a["rot_index"] == b["rot_index"] and a["inliers"] == b["inliers"] and a["votes"] == b["votes"]
