@@ -515,16 +515,18 @@ def serving(args, ws, rank, local):
     for i, Y in enumerate(wl.targets):
         tmap[i] = ctx.create_target(Y, grid_cap=0.1)
     reqs = []
-    first_of_target = {}
+    first_of_kind = {}
     for (t_arr, ti, p) in wl.requests:
         pb = ctx.problem(tmap[ti], p.X, capi.hopf_grid(p.hopf_n),
                          capi.make_params(metric=p.metric, epsilon=p.epsilon, delta_t=p.delta_t, tau=p.tau,
                                           t_half=p.t_half))
         reqs.append((t_arr, pb, 72 * p.hopf_n**3 * len(p.X)))
-        first_of_target.setdefault(ti, pb)
-    # warm the path outside both measurements: the grid, and every target's
-    # per-epsilon cell list and per-delta bounds (built on a target's first use)
-    for pb in first_of_target.values():
+        first_of_kind.setdefault((ti, len(p.X).bit_length()), pb)
+    # warm the path outside both measurements: the grid, every target's
+    # per-epsilon cell list and per-delta bounds (built on a target's first
+    # use), and the autotuned launch shape of every (target, source size)
+    # bucket (the serving worker runs no tuning trials)
+    for pb in first_of_kind.values():
         ctx.register(pb)
     for key in ("serve_max_active", "serve_busy_ns", "serve_iterations"):
         ctx.set_option(key, 0)

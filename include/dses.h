@@ -309,6 +309,9 @@ dses_status dses_exhaustive_search(dses_ctx* ctx, const dses_problem* problem, f
  *                          rotations per work item 1/2/4/8/16 for that shape) on an
  *                          even-stride sample of the problem's own rotations; 0:
  *                          fixed heuristics. Results do not depend on the shape.
+ *                          The serving worker never runs trials (they would stall
+ *                          the requests in flight): a bucket first seen there takes
+ *                          the heuristic shape until a blocking call tunes it.
  *   "use_graphs"           1 (default) replay repeated batches through CUDA graphs
  *   "serve_max_batch"      requests the serving worker runs together
  *   "serve_queue_cap"      submitted requests waiting for admission

@@ -648,6 +648,9 @@ int choose_p(dses_ctx* c, const std::vector<Job*>& jobs) {
 
 int gcd(int a, int b) { return b ? gcd(b, a % b) : a; }
 
+// Set on the serving worker's thread (no autotuner trials there).
+thread_local bool t_serving_worker = false;
+
 // Vote items per source chunk the sparse path aims for (a few per warp).
 constexpr int c_sparse_items = 128;
 
@@ -1158,7 +1161,10 @@ int pick_p(dses_ctx* c, Job& j) {
     j.tile = it->second.second;
     return it->second.first;
   }
-  if (c->capturing) return choose_p(c, one);
+  // no trial launches inside a capture, nor in the serving worker (they
+  // synchronise the device and would stall every request in flight): an
+  // untuned bucket takes the heuristic shape there
+  if (c->capturing || t_serving_worker) return choose_p(c, one);
   // an even-stride sample of the grid (its first rotations are one corner of
   // SO(3), which can favour another shape)
   auto sample = [&](int64_t want, DevMem& buf) -> std::pair<const float*, int64_t> {
@@ -1438,6 +1444,7 @@ void fail_request(Request& r, const Error& e) {
 
 void worker_loop(dses_ctx* c) {
   cudaSetDevice(c->device);
+  t_serving_worker = true;
   std::vector<std::shared_ptr<Request>> active;
   size_t mem_used = 0;
   // Iterations in flight (at most two): the host admits requests and builds and
