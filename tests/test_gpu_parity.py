@@ -525,14 +525,23 @@ def test_autotuned_shapes_give_identical_results(ctx):
     p = synth.modelnet_like_problem(6, m=700, keep=0.7, hopf_n=3)
     t = ctx.create_target(p.Y, grid_cap=2 * p.tau)
     pb = ctx.problem(t, p.X, capi.hopf_grid(3), gpu_params(p, nn_mode="grid"))
-    base = ctx.debug(pb, 72 * 27)
-    ctx.set_option("autotune", 1)
+    ctx.set_option("autotune", 0)  # fixed heuristic shapes
     try:
-        tuned = ctx.debug(pb, 72 * 27)
-        tuned2 = ctx.debug(pb, 72 * 27)
+        base = ctx.debug(pb, 72 * 27)
     finally:
-        ctx.set_option("autotune", 0)
-    for other in (tuned, tuned2):
+        ctx.set_option("autotune", 1)  # the default: tuned points per thread and rotations per work item
+    tuned = ctx.debug(pb, 72 * 27)
+    tuned2 = ctx.debug(pb, 72 * 27)
+    assert ctx.get_option("last_p_mask") != 0 and ctx.get_option("last_tile_max") >= 1
+    forced = []
+    for tile in (1, 7, 16):  # rotations per work item forced
+        ctx.set_option("tile_rotations", tile)
+        try:
+            forced.append(ctx.debug(pb, 72 * 27))
+            assert ctx.get_option("last_tile_max") == tile
+        finally:
+            ctx.set_option("tile_rotations", 0)
+    for other in [tuned, tuned2] + forced:
         for a, b in zip(base[:3], other[:3]):
             assert np.array_equal(a, b)
         assert other[4].rot_index == base[4].rot_index
