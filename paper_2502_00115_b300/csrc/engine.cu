@@ -315,7 +315,7 @@ void kd_bisect(const std::vector<float>& xyz, std::vector<int>& idx, int lo, int
   kd_bisect(xyz, idx, cut, hi, g);
 }
 
-void build_morton_groups(dses_ctx* c, dses_target* T) {
+void build_vote_groups(dses_ctx* c, dses_target* T) {
   const int m = T->m;
   std::vector<std::pair<uint64_t, int>> code((size_t)m);
   if (c->opt.target_order == 1) {
@@ -1940,7 +1940,7 @@ dses_status dses_create_target(dses_ctx* c, const float* xyz, int64_t m, int32_t
       T->gh[a] = (float)h;
       T->glo[a] = (float)((double)T->bbmin[a] - grid_cap - h);
     }
-    build_morton_groups(c, T.get());
+    build_vote_groups(c, T.get());
     CK(cudaMalloc(&T->D, sizeof(float) * (size_t)G * G * G));
     CK(cudaMalloc(&T->D4, sizeof(float4) * (size_t)G * G * G));
     CK(launch_dist_grid(T->Y, (int)m, G, T->glo, T->gh, grid_cap, T->D, T->D4, c->stream));
