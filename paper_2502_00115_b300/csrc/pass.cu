@@ -548,11 +548,11 @@ __device__ __forceinline__ void vote_centred_sparse(const PassDesc& d, const flo
 // kept source votes the group's 64 targets in one packed step. Against the
 // 32-point path this halves the iterations per kept target but keeps more
 // (source, group) pairs, so it pays only when the window is large against a
-// group. Sources are staged duplicated as for vote_centred_x2. The box test
-// stays per axis here even for a cube: the three-input max measured 8% slower
-// in this loop (an 11^3 box of 32-bit counters), where the dense and 32-point
-// paths gain 1-3% from it.
-template <int P, bool U16>
+// group. Sources are staged duplicated as for vote_centred_x2. A cubic
+// padded box takes the three-input-max box test (CUBE, an instantiation of
+// its own: with the choice made per step the loop ran 11% slower); on the
+// robot-like 33^3 box it is 4.1% faster than the per-axis test.
+template <int P, bool U16, bool CUBE>
 __device__ __forceinline__ void vote_centred_paired(const PassDesc& d, const float4* __restrict__ srcd, int nsrc,
                                                     unsigned SX, uint32_t hist_base, int* item_ctr, int lane,
                                                     float* __restrict__ thr, uint32_t sink,
@@ -638,8 +638,8 @@ __device__ __forceinline__ void vote_centred_paired(const PassDesc& d, const flo
             m &= m - 1;
             const float4 ca = srcd[2 * j];
             const float2 cb = *reinterpret_cast<const float2*>(srcd + 2 * j + 1);
-            vote_two_pairs<U16, false>(yx[q], yy[q], yz[q], inv2, pack2(ca.x, ca.y), pack2(ca.z, ca.w),
-                                       pack2(cb.x, cb.y), mx2, my2, mz2, Eyz, Ez, abase, hx, hy, hz, adummy, unit);
+            vote_two_pairs<U16, CUBE>(yx[q], yy[q], yz[q], inv2, pack2(ca.x, ca.y), pack2(ca.z, ca.w),
+                                      pack2(cb.x, cb.y), mx2, my2, mz2, Eyz, Ez, abase, hx, hy, hz, adummy, unit);
           }
         }
       }
@@ -827,10 +827,18 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
             constexpr int PS = P >= 4 ? 4 : 2;  // paired instances are built for 2 and 4
             float* thr = s_thr[SPARSE ? warp : 0];
             const uint32_t sink = (uint32_t)__cvta_generic_to_shared(s_sink);
-            if (d.hist_u16)
-              vote_centred_paired<PS, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink, blkp);
+            const bool cube = SX == (unsigned)d.E[1] && d.E[1] == d.E[2];
+            if (d.hist_u16 && cube)
+              vote_centred_paired<PS, true, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink, blkp);
+            else if (d.hist_u16)
+              vote_centred_paired<PS, true, false>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink,
+                                                   blkp);
+            else if (cube)
+              vote_centred_paired<PS, false, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink,
+                                                   blkp);
             else
-              vote_centred_paired<PS, false>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink, blkp);
+              vote_centred_paired<PS, false, false>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink,
+                                                    blkp);
           } else if (SPARSE == 1) {  // ... and of this one 32-point culled problems only
             const bool cube = SX == (unsigned)d.E[1] && d.E[1] == d.E[2];
             float* thr = s_thr[SPARSE ? warp : 0];
