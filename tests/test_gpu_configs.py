@@ -106,9 +106,9 @@ def test_modelnet_like_every_rotation_matches_stored_oracle(ctx):
         m_o, nb = oracle.inliers(p.X, p.Y, R, k[r_] * P.delta_t, P.epsilon)
         return ok, abs(int(M[r_]) - m_o) <= nb
 
-    verdicts = parallel(excuse_vote, bad_vote)
-    assert all(v for v, _ in verdicts), [int(r_) for r_, (v, _) in zip(bad_vote, verdicts) if not v][:10]
-    assert all(m for _, m in verdicts)
+    checks = parallel(excuse_vote, bad_vote)
+    assert all(v for v, _ in checks), [int(r_) for r_, (v, _) in zip(bad_vote, checks) if not v][:10]
+    assert all(m for _, m in checks)
     # M where the translation agrees: equal, or within the boundary points
     dM = np.abs(M.astype(np.int64) - M_o)
     m_bad = vote_same & (dM > nbm)
