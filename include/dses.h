@@ -331,6 +331,11 @@ dses_status dses_exhaustive_search(dses_ctx* ctx, const dses_problem* problem, f
  *                          along the longest side of the bounding box, cut at
  *                          multiples of 64 points (compact culling groups); 1
  *                          Morton order. Results do not depend on it.
+ *   "hist_strides"         1 (default): the vote histogram's row and plane strides
+ *                          are padded past the box extents where that spreads
+ *                          neighbouring lattice bins over more shared-memory banks
+ *                          without costing a histogram slab or a source chunk; 0:
+ *                          compact strides. Results do not depend on it.
  *   "fail_next_allocs"     test hook: the next this-many registrations (blocking or
  *                          served) fail at their scratch allocation with
  *                          DSES_ERR_OOM, as if the device allocator had refused,

@@ -125,6 +125,10 @@ struct Options {
   // the vote's target order, fixed when a target is created: 0 recursive
   // bisection along the longest side (compact groups), 1 Morton
   int64_t target_order = 0;
+  // histogram strides: 1 (default) spread a lattice neighbourhood over the
+  // shared-memory banks where the padding costs no slab and no source chunk;
+  // 0 compact (row and plane strides equal to the extents)
+  int64_t hist_strides = 1;
 };
 
 }  // namespace
@@ -431,6 +435,7 @@ struct Job {
   // plan
   int u16 = 0, lanes = 0, slab_x = 0, n_slabs = 1, hist_bytes = 0;
   int Ep[3] = {0, 0, 0};  // vote layout extents: E padded to odd values
+  int64_t hs[2] = {0, 0};  // vote layout strides in bins: per x-plane, per y-row
   bool fused = false;
   int sparse = 0;  // culled vote: 0 no, 1 32-point groups, 2 paired 64-point groups
   int tile = 0;    // rotations per work item picked by the autotuner (0: the launch's default)
@@ -566,6 +571,88 @@ static void odd_slabs(int64_t Ex, int64_t max_planes, int64_t* sx, int64_t* n, i
   *Exp = Ex + (last % 2 == 0 ? 1 : 0);
 }
 
+// Shared-memory bytes of a histogram slab of sx x-planes at plane stride hs0.
+int layout_bytes(int64_t sx, int64_t hs0, bool u16) {
+  const int64_t bins = sx * hs0;
+  const int64_t hb = u16 ? ((bins + 1) / 2) * 4 : bins * 4;
+  return (int)((hb + 15) & ~15LL);
+}
+
+// How well strides (hs0, hs1) spread a lattice neighbourhood over the 32
+// shared-memory banks: a warp's increments come from a compact patch of
+// targets, so its bins are near each other, and two bins whose word indices
+// differ by a non-zero multiple of 32 share a bank. Returns the squared
+// length of the shortest offset |d|_inf <= 4 that lands in the same bank on a
+// different word (larger is better) and, second, how many offsets of squared
+// length <= 9 do (fewer is better). 16-bit counters: word = bin / 2, so an
+// offset conflicts when its bin difference is within one of a multiple of 64
+// (and at least 2).
+std::pair<int, int> bank_spread(int64_t hs0, int64_t hs1, bool u16) {
+  int shortest = 1 << 30, close = 0;
+  for (int dx = -4; dx <= 4; ++dx)
+    for (int dy = -4; dy <= 4; ++dy)
+      for (int dz = -4; dz <= 4; ++dz) {
+        const int n2 = dx * dx + dy * dy + dz * dz;
+        if (n2 == 0) continue;
+        const int64_t v = dx * hs0 + dy * hs1 + dz;
+        bool same_bank;
+        if (u16) {
+          const int64_t m = ((v % 64) + 64) % 64;
+          same_bank = std::llabs(v) >= 2 && (m <= 1 || m == 63);
+        } else {
+          same_bank = v % 32 == 0;
+        }
+        if (!same_bank) continue;
+        shortest = std::min(shortest, n2);
+        close += n2 <= 9 ? 1 : 0;
+      }
+  return {shortest, close};
+}
+
+bool culled_source_order(const Job& j);
+
+// Source chunks a launch of this job alone stages per rotation with a
+// histogram of hist_bytes (pass_staging and set_chunks of the launch).
+int source_chunks(const Job& j, int hist_bytes) {
+  int src = 0, blk = 0, list = 0;
+  const bool blocks = j.sparse && culled_source_order(j);
+  pass_staging(hist_bytes, j.N, blocks, j.sparse == 2, &src, &blk, &list);
+  const int cap = j.sparse == 2 ? std::max(1, src / kTileBytes) * kTileSources : std::max(1, src / (j.sparse ? 16 : 32));
+  return (j.N + cap - 1) / cap;
+}
+
+// Row and plane strides (in bins) of the vote histogram, padded past the
+// extents where that spreads a lattice neighbourhood over more banks
+// (bank_spread) without costing a slab or a source chunk: the slab keeps its
+// x-planes within the budget and the launch stages the sources in as many
+// chunks as with the compact layout. Padding bins are never voted (a pair
+// inside the box has k_a < E_a) and read as zero by the mode scan.
+void spread_strides(Job& j, int64_t budget) {
+  const bool u16 = j.u16;
+  const int64_t Ey = j.Ep[1], Ez = j.Ep[2], sx = j.slab_x;
+  const int chunks0 = source_chunks(j, j.hist_bytes);
+  auto best = bank_spread(j.hs[0], j.hs[1], u16);
+  int64_t b0 = j.hs[0], b1 = j.hs[1];
+  int bbytes = j.hist_bytes;
+  for (int64_t hs1 = Ez; hs1 < Ez + 8; ++hs1)
+    for (int64_t hs0 = Ey * hs1; hs0 < Ey * hs1 + 32; ++hs0) {
+      const int bytes = layout_bytes(sx, hs0, u16);
+      if (bytes + 8 > budget || source_chunks(j, bytes) > chunks0) continue;
+      const auto sc = bank_spread(hs0, hs1, u16);
+      const bool better = sc.first > best.first || (sc.first == best.first && sc.second < best.second) ||
+                          (sc == best && bytes < bbytes);
+      if (better) {
+        best = sc;
+        b0 = hs0;
+        b1 = hs1;
+        bbytes = bytes;
+      }
+    }
+  j.hs[0] = b0;
+  j.hs[1] = b1;
+  j.hist_bytes = bbytes;
+}
+
 void plan(dses_ctx* c, Job& j) {
   // vote layout: the lattice box padded to odd extents (the centred vote
   // paths need them); the scan of a padded layout skips the padding bins
@@ -593,9 +680,9 @@ void plan(dses_ctx* c, Job& j) {
   j.Ep[0] = (int)Exp;
   j.Ep[1] = (int)Ey;
   j.Ep[2] = (int)Ez;
-  const int64_t bins = sx * Ey * Ez;
-  const int64_t hb = u16 ? ((bins + 1) / 2) * 4 : bins * 4;
-  j.hist_bytes = (int)((hb + 15) & ~15LL);
+  j.hs[0] = Ey * Ez;
+  j.hs[1] = Ez;
+  j.hist_bytes = layout_bytes(sx, j.hs[0], u16);
   j.lanes = 0;
   // One 32-bit copy of every bin per lane (word bin * 32 + lane, so a warp's
   // increments never share a bank), on request only: measured slower than
@@ -634,6 +721,7 @@ void plan(dses_ctx* c, Job& j) {
   for (int a = 0; a < 3; ++a)
     span = std::min(span, (double)j.E[a] * j.delta / std::max(1e-12, (double)j.T->gext2[a]));
   j.sparse = !cull ? 0 : c->opt.vote_sparse == 2 ? 1 : c->opt.vote_sparse == 3 ? 2 : (span >= 0.6 ? 2 : 1);
+  if (c->opt.hist_strides && !j.lanes) spread_strides(j, budget);
 }
 
 int choose_p(dses_ctx* c, const std::vector<Job*>& jobs) {
@@ -817,6 +905,8 @@ PassDesc make_desc(const Job& j, int P, bool second) {
     d.E[a] = j.Ep[a];
     d.Ev[a] = j.E[a];
   }
+  d.hs[0] = (uint32_t)j.hs[0];
+  d.hs[1] = (uint32_t)j.hs[1];
   {
     // the magnitudes the culled paths' FP32 keep tests round at: target
     // coordinates and the box's lattice offsets, in lattice units
@@ -936,8 +1026,10 @@ void launch_pass(dses_ctx* c, const std::vector<PassPart>& parts, int P) {
   bool blocks = true;
   for (auto& pp : parts) max_n = std::max(max_n, pp.job->N);
   for (auto& d : descs) blocks &= block_bounds_pay(d);
-  int src_bytes = 0, blk_bytes = 0;
-  pass_staging(hist, max_n, blocks, &src_bytes, &blk_bytes);
+  bool paired = false;
+  for (auto& pp : parts) paired |= pp.job->sparse == 2;
+  int src_bytes = 0, blk_bytes = 0, list_bytes = 0;
+  pass_staging(hist, max_n, blocks, paired, &src_bytes, &blk_bytes, &list_bytes);
   for (auto& d : descs) set_chunks(d, src_bytes);
   const size_t db = align256(sizeof(PassDesc) * descs.size()), pb = align256(sizeof(int) * prefix.size());
   DevMem m;
@@ -960,6 +1052,7 @@ void launch_pass(dses_ctx* c, const std::vector<PassPart>& parts, int P) {
   L.hist_bytes = hist;
   L.src_bytes = src_bytes;
   L.blk_bytes = blk_bytes;
+  L.list_bytes = list_bytes;
   L.padded = 0;
   for (auto& pp : parts)
     for (int a = 0; a < 3; ++a) L.padded |= pp.job->Ep[a] != pp.job->E[a] ? 1 : 0;
@@ -1102,8 +1195,8 @@ float time_vote_trial(dses_ctx* c, Job& j, const float* rot, int64_t n, int P, i
   d[0].n_rot = (int)n;
   d[0].tile_rot = tile;
   d[0].votes_total = nullptr;  // a trial's votes are not the registration's
-  int src_bytes = 0, blk_bytes = 0;
-  pass_staging(j.hist_bytes, j.N, block_bounds_pay(d[0]), &src_bytes, &blk_bytes);
+  int src_bytes = 0, blk_bytes = 0, list_bytes = 0;
+  pass_staging(j.hist_bytes, j.N, block_bounds_pay(d[0]), j.sparse == 2, &src_bytes, &blk_bytes, &list_bytes);
   set_chunks(d[0], src_bytes);
   const int tiles = (int)((n + tile - 1) / tile);
   std::vector<int> tp{0, tiles}, rp{0, (int)n};
@@ -1125,6 +1218,7 @@ float time_vote_trial(dses_ctx* c, Job& j, const float* rot, int64_t n, int P, i
   L.hist_bytes = j.hist_bytes;
   L.src_bytes = src_bytes;
   L.blk_bytes = blk_bytes;
+  L.list_bytes = list_bytes;
   L.padded = 0;
   for (int a = 0; a < 3; ++a) L.padded |= j.Ep[a] != j.E[a] ? 1 : 0;
   cudaEvent_t e0, e1;
@@ -2470,6 +2564,7 @@ static int64_t* option_slot(dses_ctx* c, const char* key) {
   if (k == "vote_sparse") return &o.vote_sparse;
   if (k == "fail_next_allocs") return &o.fail_next_allocs;
   if (k == "target_order") return &o.target_order;
+  if (k == "hist_strides") return &o.hist_strides;
   if (k == "serve_max_active") return &c->serve_max_active;
   if (k == "serve_busy_ns") return &c->serve_busy_ns;
   if (k == "serve_iterations") return &c->serve_iterations;
@@ -2513,7 +2608,7 @@ dses_status dses_set_option(dses_ctx* c, const char* key, int64_t value) {
       ok = false;  // read-only
     else if (k == "tile_rotations") ok = value >= 0 && value <= 4096;
     else if (k == "fail_next_allocs") ok = value >= 0;
-    else if (k == "target_order") ok = value == 0 || value == 1;
+    else if (k == "target_order" || k == "hist_strides") ok = value == 0 || value == 1;
     else if (k == "serve_max_active" || k == "serve_busy_ns" || k == "serve_iterations") ok = value == 0;  // reset only
     else ok = value >= 1;
     if (!ok) invalid("option value out of range for " + k);

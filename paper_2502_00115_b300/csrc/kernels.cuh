@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 namespace dses {
 
 // Robust per-point error rho(d) of a nearest-target distance d (the norm of
@@ -33,6 +35,17 @@ constexpr int kMaxSmem = 232448;
 // Static shared memory of the pass kernel (descriptor, reductions, per-warp
 // culling thresholds) plus headroom.
 constexpr int kPassStaticSmem = 2048 + 32 * 8 * 8 * 4;
+// Paired culled vote: per warp, three lists of kPairedListCap shared addresses
+// of kept sources' staged offsets (sources kept by the item's first group only,
+// by its second only, by both), flushed at kPairedListFlush entries.
+constexpr int kPairedListCap = 48;
+constexpr int kPairedListFlush = 16;
+constexpr int kPairedListBytes = (kPassThreads / 32) * 3 * kPairedListCap * 4;
+// Tiled staging of the paired culled vote: 8 sources per 192-byte tile, the
+// pairs (c_x, c_x) of its sources at bytes 0-63, (c_y, c_y) at 64-127 and
+// (c_z, c_z) at 128-191.
+constexpr int kTileSources = 8;
+constexpr int kTileBytes = 192;
 // Histogram budget: what is left after the source chunk and static storage.
 constexpr int kHistBudget = kMaxSmem - kSrcChunk * 16 - kPassStaticSmem;
 
@@ -60,12 +73,15 @@ struct PassDesc {
   int lo[3];             // lattice box lower corner
   int E[3];              // histogram layout extent per axis (odd; >= Ev)
   int Ev[3];             // lattice box extent per axis (bins beyond it are padding)
+  uint32_t hs[2];        // layout strides in bins: per x-plane (>= E[1] hs[1]) and per
+                         // y-row (>= E[2]); bin of (kx, ky, kz) = kx hs[0] + ky hs[1] + kz
   int slab_x;            // x-planes per histogram slab
   int n_slabs;
   int hist_u16;          // 1: two 16-bit counters per 32-bit word
   int hist_lanes;        // 1: 32-bit counters, one copy per lane: word bin * 32 + lane
-  int chunk[2];          // sources staged per chunk: [0] plain (16 bytes each), [1]
-                         // packed (32 bytes each); equal chunks that fit the staging
+  int chunk[3];          // sources staged per chunk: [0] plain (16 bytes each), [1]
+                         // packed (32 bytes each), [2] tiled (paired culled vote: 24
+                         // bytes each, whole tiles of 8); equal chunks that fit the staging
   int sparse;            // culled vote: 0 no, 1 32-point groups, 2 paired 64-point
                          // groups (gbox / n_groups hold that mode's group boxes)
   // vote work decomposition per rotation: items = n_tchunks x n_sgroups
@@ -108,6 +124,8 @@ struct PassLaunch {
   int src_bytes;           // source staging bytes (a multiple of 32)
   int blk_bytes;           // culled launches: per 32-source block bounds of the staged
                            // offsets (8 floats each) after the staging; else 0
+  int list_bytes;          // paired culled launches: the warps' lists of kept sources
+                           // (kPairedListBytes) after the block bounds; else 0
   int padded;              // 1: some problem's layout is padded (E != Ev): the
                            // instance whose mode scan skips padding bins
 };
@@ -126,10 +144,14 @@ int pass_smem_bytes(int hist_bytes, int src_bytes);
 int pass_src_bytes(int hist_bytes, int n_src);
 // Shared memory of a rotation-pass launch past the histogram: the source
 // staging and, for a culled launch, the bounds of every block of 32 staged
-// sources (32 bytes each, sized for the plain layout's largest chunk), taken
-// from the staging room.
-inline void pass_staging(int hist_bytes, int n_src_max, bool culled, int* src_bytes, int* blk_bytes) {
+// sources (32 bytes each, sized for the plain layout's largest chunk), and for
+// a paired culled launch the warps' kept-source lists, both taken from the
+// staging room.
+inline void pass_staging(int hist_bytes, int n_src_max, bool culled, bool paired, int* src_bytes, int* blk_bytes,
+                         int* list_bytes) {
   int src = pass_src_bytes(hist_bytes, n_src_max);
+  const int list = paired ? kPairedListBytes : 0;
+  src = (src - list) & ~31;
   int blk = 0;
   if (culled) {
     blk = ((src / 16 + 31) / 32) * 32;
@@ -137,12 +159,13 @@ inline void pass_staging(int hist_bytes, int n_src_max, bool culled, int* src_by
   }
   *src_bytes = src;
   *blk_bytes = blk;
+  *list_bytes = list;
 }
-// Equal chunks of the problem's sources that fit src_bytes of staging, plain
-// and packed (d.chunk).
+// Equal chunks of the problem's sources that fit src_bytes of staging, plain,
+// packed and tiled (d.chunk).
 inline void set_chunks(PassDesc& d, int src_bytes) {
-  for (int k = 0; k < 2; ++k) {
-    const int cap = src_bytes / (k ? 32 : 16);
+  for (int k = 0; k < 3; ++k) {
+    const int cap = k == 2 ? std::max(1, src_bytes / kTileBytes) * kTileSources : src_bytes / (k ? 32 : 16);
     const int n = (d.N + cap - 1) / cap;
     d.chunk[k] = (d.N + n - 1) / n;
   }

@@ -152,6 +152,8 @@ extern "C" dses_status dses_vote_static(int device, void* cuda_stream, const flo
       d.E[a] = E[a];
       d.Ev[a] = E[a];
     }
+    d.hs[0] = (uint32_t)(E[1] * E[2]);
+    d.hs[1] = (uint32_t)E[2];
     d.slab_x = sx;
     d.n_slabs = (E[0] + sx - 1) / sx;
     d.hist_u16 = u16 ? 1 : 0;
@@ -178,6 +180,7 @@ extern "C" dses_status dses_vote_static(int device, void* cuda_stream, const flo
     L.hist_bytes = hist_bytes;
     L.src_bytes = kSrcChunk * 16;
     L.blk_bytes = 0;
+    L.list_bytes = 0;
     L.padded = 0;
     if (launch_vote(L, ppt, 0, std::max(1, std::min(sms, tiles)), s) != cudaSuccess) {
       cudaGetLastError();

@@ -223,16 +223,17 @@ __device__ __forceinline__ void vote_centred(const PassDesc& d, const float4* __
   const int n_tchunks = d.n_tchunks, n_sgroups = d.n_sgroups;
   const int n_items = n_tchunks * n_sgroups;
   const int spg = (nsrc + n_sgroups - 1) / n_sgroups;
-  const unsigned Ey = (unsigned)d.E[1], Ez = (unsigned)d.E[2], Eyz = Ey * Ez;
+  const unsigned Ey = (unsigned)d.E[1], Ez = (unsigned)d.E[2];
+  const uint32_t Sx = d.hs[0], Sy = d.hs[1];  // bins per x-plane and per y-row of the layout
   const float inv = d.inv_delta;
   const float hx = 0.5f * (float)SX, hy = 0.5f * (float)Ey, hz = 0.5f * (float)Ez;
   const float mx = kMagic + (float)((SX - 1) / 2), my = kMagic + (float)((Ey - 1) / 2),
               mz = kMagic + (float)((Ez - 1) / 2);
-  // address = base + unit * (kx Eyz + ky Ez + kz), the kMagicBits offsets folded in
-  const uint32_t bias = kMagicBits * (Eyz + Ez + 1u);
+  // address = base + unit * (kx Sx + ky Sy + kz), the kMagicBits offsets folded in
+  const uint32_t bias = kMagicBits * (Sx + Sy + 1u);
   // 32-bit counters: word stride `unit` bytes (4, or 128 with a copy per lane)
   const uint32_t unit = d.hist_lanes ? 128u : 4u;
-  const uint32_t EyzU = Eyz * unit, EzU = Ez * unit;
+  const uint32_t SxU = Sx * unit, SyU = Sy * unit;
   const uint32_t abase32 = hist_base + (d.hist_lanes ? 4u * (uint32_t)lane : 0u) - unit * bias;
   const uint32_t abase16 = hist_base - 2u * bias;
   const uint32_t sinkl = sink + 4u * (uint32_t)lane;
@@ -253,12 +254,12 @@ __device__ __forceinline__ void vote_centred(const PassDesc& d, const float4* __
         const uint32_t by = __float_as_uint(__fadd_rn(wy, my));
         const uint32_t bz = __float_as_uint(__fadd_rn(wz, mz));
         if (U16) {
-          const uint32_t b = bx * Eyz + (by * Ez + bz);  // bin + bias (bias even)
+          const uint32_t b = bx * Sx + (by * Sy + bz);  // bin + bias (bias even)
           const uint32_t addr = abase16 + ((b >> 1) << 2);
           const uint32_t inc = 1u + (b & 1u) * 0xffffu;
           red_or_sink(addr, inc, sinkl, wx, wy, wz, hx, hy, hz);
         } else {
-          const uint32_t addr = abase32 + bx * EyzU + (by * EzU + bz * unit);
+          const uint32_t addr = abase32 + bx * SxU + (by * SyU + bz * unit);
           red_or_sink(addr, 1u, sinkl, wx, wy, wz, hx, hy, hz);
         }
       }
@@ -315,9 +316,9 @@ __device__ __forceinline__ void vote_centred(const PassDesc& d, const float4* __
 template <bool U16, bool CUBE>
 __device__ __forceinline__ void vote_two_pairs(uint64_t yx, uint64_t yy, uint64_t yz, uint64_t inv2, uint64_t cx2,
                                                uint64_t cy2, uint64_t cz2, uint64_t mx2, uint64_t my2, uint64_t mz2,
-                                               uint32_t Eyz, uint32_t Ez, uint32_t abase, float hx, float hy,
+                                               uint32_t Sx, uint32_t Sy, uint32_t abase, float hx, float hy,
                                                float hz, uint32_t adummy, uint32_t unit) {
-  const uint32_t sy = U16 ? Eyz : Eyz * unit, sz = U16 ? Ez : Ez * unit;
+  const uint32_t sy = U16 ? Sx : Sx * unit, sz = U16 ? Sy : Sy * unit;
 #define DSES_VOTE2_ARGS                                                                                         \
   ::"l"(yx), "l"(yy), "l"(yz), "l"(inv2), "l"(cx2), "l"(cy2), "l"(cz2), "l"(mx2), "l"(my2), "l"(mz2), "r"(sy), \
       "r"(sz), "r"(abase), "f"(hx), "f"(hy), "f"(hz), "r"(adummy), "r"(unit)
@@ -342,7 +343,7 @@ __device__ __forceinline__ uint64_t pack2(float lo, float hi) {
 template <int Q, bool U16, bool CUBE>
 __device__ __forceinline__ void vote_sources_x2(const float4* __restrict__ srcd, int i0, int i1, const uint64_t* yx,
                                                 const uint64_t* yy, const uint64_t* yz, uint64_t inv2, uint64_t mx2,
-                                                uint64_t my2, uint64_t mz2, uint32_t Eyz, uint32_t Ez, uint32_t abase,
+                                                uint64_t my2, uint64_t mz2, uint32_t Sx, uint32_t Sy, uint32_t abase,
                                                 float hx, float hy, float hz, uint32_t adummy, uint32_t unit) {
 #pragma unroll 4
   for (int i = i0; i < i1; ++i) {
@@ -351,7 +352,7 @@ __device__ __forceinline__ void vote_sources_x2(const float4* __restrict__ srcd,
     const uint64_t cx2 = pack2(ca.x, ca.y), cy2 = pack2(ca.z, ca.w), cz2 = pack2(cb.x, cb.y);
 #pragma unroll
     for (int q = 0; q < Q; ++q)
-      vote_two_pairs<U16, CUBE>(yx[q], yy[q], yz[q], inv2, cx2, cy2, cz2, mx2, my2, mz2, Eyz, Ez, abase, hx, hy, hz,
+      vote_two_pairs<U16, CUBE>(yx[q], yy[q], yz[q], inv2, cx2, cy2, cz2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz,
                                 adummy, unit);
   }
 }
@@ -375,14 +376,15 @@ __device__ __forceinline__ void vote_centred_x2(const PassDesc& d, const float4*
   const int n_tchunks = d.n_tchunks, n_sgroups = d.n_sgroups;
   const int n_items = n_tchunks * n_sgroups;
   const int spg = (nsrc + n_sgroups - 1) / n_sgroups;
-  const unsigned Ey = (unsigned)d.E[1], Ez = (unsigned)d.E[2], Eyz = Ey * Ez;
+  const unsigned Ey = (unsigned)d.E[1], Ez = (unsigned)d.E[2];
+  const uint32_t Sx = d.hs[0], Sy = d.hs[1];  // bins per x-plane and per y-row of the layout
   const float inv = d.inv_delta;
   const float hx = 0.5f * (float)SX, hy = 0.5f * (float)Ey, hz = 0.5f * (float)Ez;
   const bool cube = SX == Ey && Ey == Ez;  // one half-width for the three axes
   const float mx = kMagic + (float)((SX - 1) / 2), my = kMagic + (float)((Ey - 1) / 2),
               mz = kMagic + (float)((Ez - 1) / 2);
   const uint64_t inv2 = pack2(inv, inv), mx2 = pack2(mx, mx), my2 = pack2(my, my), mz2 = pack2(mz, mz);
-  const uint32_t bias = kMagicBits * (Eyz + Ez + 1u);
+  const uint32_t bias = kMagicBits * (Sx + Sy + 1u);
   // 32-bit counters: word stride `unit` bytes (4, or 128 with a copy per lane)
   const uint32_t unit = d.hist_lanes ? 128u : 4u;
   const uint32_t abase = U16 ? hist_base - 2u * bias
@@ -403,10 +405,10 @@ __device__ __forceinline__ void vote_centred_x2(const PassDesc& d, const float4*
     }
     const int i0 = sg * spg, i1 = min(i0 + spg, nsrc);
     if (DENSE_INST && cube)
-      vote_sources_x2<P / 2, U16, true>(srcd, i0, i1, yx, yy, yz, inv2, mx2, my2, mz2, Eyz, Ez, abase, hx, hy, hz,
+      vote_sources_x2<P / 2, U16, true>(srcd, i0, i1, yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz,
                                        adummy, unit);
     else
-      vote_sources_x2<P / 2, U16, false>(srcd, i0, i1, yx, yy, yz, inv2, mx2, my2, mz2, Eyz, Ez, abase, hx, hy, hz,
+      vote_sources_x2<P / 2, U16, false>(srcd, i0, i1, yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz,
                                         adummy, unit);
   }
 }
@@ -456,14 +458,15 @@ __device__ __forceinline__ void vote_centred_sparse(const PassDesc& d, const flo
   const int n_tchunks = d.n_tchunks, n_sgroups = d.n_sgroups;
   const int n_items = n_tchunks * n_sgroups;
   const int spg = (nsrc + n_sgroups - 1) / n_sgroups;
-  const unsigned Ey = (unsigned)d.E[1], Ez = (unsigned)d.E[2], Eyz = Ey * Ez;
+  const unsigned Ey = (unsigned)d.E[1], Ez = (unsigned)d.E[2];
+  const uint32_t Sx = d.hs[0], Sy = d.hs[1];  // bins per x-plane and per y-row of the layout
   const float inv = d.inv_delta;
   const float hx = 0.5f * (float)SX, hy = 0.5f * (float)Ey, hz = 0.5f * (float)Ez;
   const float mx = kMagic + (float)((SX - 1) / 2), my = kMagic + (float)((Ey - 1) / 2),
               mz = kMagic + (float)((Ez - 1) / 2);
-  const uint32_t bias = kMagicBits * (Eyz + Ez + 1u);
+  const uint32_t bias = kMagicBits * (Sx + Sy + 1u);
   const uint32_t unit = d.hist_lanes ? 128u : 4u;
-  const uint32_t EyzU = Eyz * unit, EzU = Ez * unit;
+  const uint32_t SxU = Sx * unit, SyU = Sy * unit;
   const uint32_t abase32 = hist_base + (d.hist_lanes ? 4u * (uint32_t)lane : 0u) - unit * bias;
   const uint32_t abase16 = hist_base - 2u * bias;
   const uint32_t sinkl = sink + 4u * (uint32_t)lane;
@@ -527,10 +530,10 @@ __device__ __forceinline__ void vote_centred_sparse(const PassDesc& d, const flo
             const uint32_t by = __float_as_uint(__fadd_rn(wy, my));
             const uint32_t bz = __float_as_uint(__fadd_rn(wz, mz));
             if (U16) {
-              const uint32_t b = bx * Eyz + (by * Ez + bz);
+              const uint32_t b = bx * Sx + (by * Sy + bz);
               red_or_sink<CUBE>(abase16 + ((b >> 1) << 2), 1u + (b & 1u) * 0xffffu, sinkl, wx, wy, wz, hx, hy, hz);
             } else {
-              red_or_sink<CUBE>(abase32 + bx * EyzU + (by * EzU + bz * unit), 1u, sinkl, wx, wy, wz, hx, hy, hz);
+              red_or_sink<CUBE>(abase32 + bx * SxU + (by * SyU + bz * unit), 1u, sinkl, wx, wy, wz, hx, hy, hz);
             }
           }
         }
@@ -540,39 +543,97 @@ __device__ __forceinline__ void vote_centred_sparse(const PassDesc& d, const flo
   }
 }
 
+// One kept source against a lane's target pair of each of G groups: its
+// staged pairs (c_x, c_x), (c_y, c_y), (c_z, c_z) read from the tile layout at
+// shared address a (a + 64, a + 128).
+template <int G, bool U16, bool CUBE>
+__device__ __forceinline__ void vote_staged(uint32_t a, const uint64_t* yx, const uint64_t* yy, const uint64_t* yz,
+                                            uint64_t inv2, uint64_t mx2, uint64_t my2, uint64_t mz2, uint32_t Sx,
+                                            uint32_t Sy, uint32_t abase, float hx, float hy, float hz, uint32_t adummy,
+                                            uint32_t unit) {
+  uint64_t cx2, cy2, cz2;
+  asm("ld.shared.b64 %0, [%3];\n\tld.shared.b64 %1, [%3+64];\n\tld.shared.b64 %2, [%3+128];"
+      : "=l"(cx2), "=l"(cy2), "=l"(cz2)
+      : "r"(a));
+#pragma unroll
+  for (int g = 0; g < G; ++g)
+    vote_two_pairs<U16, CUBE>(yx[g], yy[g], yz[g], inv2, cx2, cy2, cz2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz,
+                              adummy, unit);
+}
+
+// The n kept sources of a list against the lane's target pairs of G groups,
+// four per iteration (the list is 16-byte aligned).
+template <int G, bool U16, bool CUBE>
+__device__ __forceinline__ void vote_list(const uint32_t* __restrict__ lst, int n, const uint64_t* yx,
+                                          const uint64_t* yy, const uint64_t* yz, uint64_t inv2, uint64_t mx2,
+                                          uint64_t my2, uint64_t mz2, uint32_t Sx, uint32_t Sy, uint32_t abase,
+                                          float hx, float hy, float hz, uint32_t adummy, uint32_t unit) {
+  int k = 0;
+#pragma unroll 1
+  for (; k + 4 <= n; k += 4) {
+    const uint4 a = *reinterpret_cast<const uint4*>(lst + k);
+    vote_staged<G, U16, CUBE>(a.x, yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy, unit);
+    vote_staged<G, U16, CUBE>(a.y, yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy, unit);
+    vote_staged<G, U16, CUBE>(a.z, yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy, unit);
+    vote_staged<G, U16, CUBE>(a.w, yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy, unit);
+  }
+#pragma unroll 1
+  for (; k < n; ++k)
+    vote_staged<G, U16, CUBE>(lst[k], yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy, unit);
+}
+
+// Appends the lanes whose flag is set to a warp's list (each at its rank in
+// the ballot); n is the list's length, the same in every lane.
+__device__ __forceinline__ void list_push(uint32_t* __restrict__ lst, int& n, bool flag, uint32_t entry,
+                                          uint32_t lanes_below) {
+  const uint32_t m = __ballot_sync(0xffffffffu, flag);
+  if (flag) lst[n + __popc(m & lanes_below)] = entry;
+  n += __popc(m);
+}
+
 // Paired culled path, for windows that span many target groups (large
 // targets: the robot-like problem): groups of 64 consecutive targets
 // (d.gbox / d.n_groups hold the 64-point boxes in this mode), a lane holding
 // two of each of its item's P / 2 groups (points 64 g + lane and 64 g + 32 +
-// lane) as a packed FP32 pair; one ballot per (32 sources, group), and each
-// kept source votes the group's 64 targets in one packed step. Against the
-// 32-point path this halves the iterations per kept target but keeps more
-// (source, group) pairs, so it pays only when the window is large against a
-// group. Sources are staged duplicated as for vote_centred_x2. A cubic
-// padded box takes the three-input-max box test (CUBE, an instantiation of
-// its own: with the choice made per step the loop ran 11% slower); on the
-// robot-like 33^3 box it is 4.1% faster than the per-axis test.
+// lane) as a packed FP32 pair; each kept source votes a group's 64 targets in
+// one packed step. Against the 32-point path this halves the iterations per
+// kept target but keeps more (source, group) pairs, so it pays only when the
+// window is large against a group. Sources are staged in tiles of 8 (their
+// duplicated offsets, one 8-byte pair per axis: the keep tests of 32
+// consecutive sources read two words per bank, a vote step three uniform
+// 8-byte loads). The kept sources of each 32-source block gather in the warp's
+// lists: a source kept by both of an item's groups is read once and votes
+// both; the lists are voted once one holds kPairedListFlush entries, and at
+// the end of the item. A cubic padded box takes the three-input-max box test
+// (CUBE, an instantiation of its own: with the choice made per step the loop
+// ran 11% slower).
 template <int P, bool U16, bool CUBE>
-__device__ __forceinline__ void vote_centred_paired(const PassDesc& d, const float4* __restrict__ srcd, int nsrc,
+__device__ __forceinline__ void vote_centred_paired(const PassDesc& d, const float* __restrict__ srct, int nsrc,
                                                     unsigned SX, uint32_t hist_base, int* item_ctr, int lane,
                                                     float* __restrict__ thr, uint32_t sink,
-                                                    const float* __restrict__ blkp) {
+                                                    const float* __restrict__ blkp, uint32_t* __restrict__ lst) {
   static_assert(P == 2 || P == 4, "two targets of each of P / 2 groups per lane");
-  constexpr int Q = P / 2;  // 64-point groups per item
+  constexpr int Q = P / 2;            // 64-point groups per item
+  constexpr int NL = Q == 2 ? 3 : 1;  // lists: first group only, second only, both
   const int n_tchunks = d.n_tchunks, n_sgroups = d.n_sgroups;
   const int n_items = n_tchunks * n_sgroups;
   const int spg = (nsrc + n_sgroups - 1) / n_sgroups;
-  const unsigned Ey = (unsigned)d.E[1], Ez = (unsigned)d.E[2], Eyz = Ey * Ez;
+  const unsigned Ey = (unsigned)d.E[1], Ez = (unsigned)d.E[2];
+  const uint32_t Sx = d.hs[0], Sy = d.hs[1];  // bins per x-plane and per y-row of the layout
   const float inv = d.inv_delta;
-  const float hx = 0.5f * (float)SX, hy = 0.5f * (float)Ey, hz = 0.5f * (float)Ez;
-  const float mx = kMagic + (float)((SX - 1) / 2), my = kMagic + (float)((Ey - 1) / 2),
-              mz = kMagic + (float)((Ez - 1) / 2);
-  const uint64_t inv2 = pack2(inv, inv), mx2 = pack2(mx, mx), my2 = pack2(my, my), mz2 = pack2(mz, mz);
-  const uint32_t bias = kMagicBits * (Eyz + Ez + 1u);
+  // a cubic box has one half-width and one rounding constant (fewer live registers)
+  const float hx = 0.5f * (float)SX, hy = CUBE ? hx : 0.5f * (float)Ey, hz = CUBE ? hx : 0.5f * (float)Ez;
+  const float mx = kMagic + (float)((SX - 1) / 2), my = CUBE ? mx : kMagic + (float)((Ey - 1) / 2),
+              mz = CUBE ? mx : kMagic + (float)((Ez - 1) / 2);
+  const uint64_t inv2 = pack2(inv, inv), mx2 = pack2(mx, mx), my2 = CUBE ? mx2 : pack2(my, my),
+                 mz2 = CUBE ? mx2 : pack2(mz, mz);
+  const uint32_t bias = kMagicBits * (Sx + Sy + 1u);
   const uint32_t unit = d.hist_lanes ? 128u : 4u;
   const uint32_t abase = U16 ? hist_base - 2u * bias
                              : hist_base + (d.hist_lanes ? 4u * (uint32_t)lane : 0u) - unit * bias;
   const uint32_t adummy = sink + 4u * (uint32_t)lane;
+  const uint32_t lt = (1u << lane) - 1u;
+  const uint32_t tbase = (uint32_t)__cvta_generic_to_shared(srct);
   for (int it = next_item(item_ctr, lane); it < n_items; it = next_item(item_ctr, lane)) {
     const int tc = it % n_tchunks, sg = it / n_tchunks;
     // keep (source, group) iff s1_a <= c_a <= s2_a on every axis
@@ -605,6 +666,9 @@ __device__ __forceinline__ void vote_centred_paired(const PassDesc& d, const flo
       yz[q] = pack2(a.z, b.z);
     }
     const int i0 = sg * spg, i1 = min(i0 + spg, nsrc);
+    int cnt[NL];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) cnt[l] = 0;
     // the aligned blocks of 32 staged sources that meet [i0, i1), 32 at a
     // time: a lane tests one block's bounds, and only blocks that can keep a
     // group are walked
@@ -619,30 +683,56 @@ __device__ __forceinline__ void vote_centred_paired(const PassDesc& d, const flo
         const int mine = s0 + lane;  // the aligned block may start before i0
         const bool valid = mine >= i0 && mine < i1;
         const int ms = valid ? mine : i0;
-        const float4 cm = srcd[2 * ms];  // (c_x, c_x, c_y, c_y)
-        const float cmz = srcd[2 * ms + 1].x;
-        uint32_t kmask[Q];
+        const int o = (ms / kTileSources) * (kTileBytes / 4) + 2 * (ms % kTileSources);
+        const float cx = srct[o], cy = srct[o + 16], cz = srct[o + 32];
+        bool keep[Q];
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
           const float4 ta = *reinterpret_cast<const float4*>(thr + 8 * q);
           const float2 tb = *reinterpret_cast<const float2*>(thr + 8 * q + 4);
-          const bool keep = valid && cm.x >= ta.x && cm.x <= ta.y && cm.z >= ta.z && cm.z <= ta.w && cmz >= tb.x &&
-                            cmz <= tb.y;
-          kmask[q] = __ballot_sync(0xffffffffu, keep);
+          keep[q] = valid && cx >= ta.x && cx <= ta.y && cy >= ta.z && cy <= ta.w && cz >= tb.x && cz <= tb.y;
         }
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-          uint32_t m = kmask[q];
-          while (m) {
-            const int j = s0 + __ffs(m) - 1;
-            m &= m - 1;
-            const float4 ca = srcd[2 * j];
-            const float2 cb = *reinterpret_cast<const float2*>(srcd + 2 * j + 1);
-            vote_two_pairs<U16, CUBE>(yx[q], yy[q], yz[q], inv2, pack2(ca.x, ca.y), pack2(ca.z, ca.w),
-                                      pack2(cb.x, cb.y), mx2, my2, mz2, Eyz, Ez, abase, hx, hy, hz, adummy, unit);
+        const uint32_t entry = tbase + 4u * (uint32_t)o;
+        if constexpr (Q == 2) {
+          list_push(lst, cnt[0], keep[0] && !keep[1], entry, lt);
+          list_push(lst + kPairedListCap, cnt[1], keep[1] && !keep[0], entry, lt);
+          list_push(lst + 2 * kPairedListCap, cnt[2], keep[0] && keep[1], entry, lt);
+        } else {
+          list_push(lst, cnt[0], keep[0], entry, lt);
+        }
+        __syncwarp();
+        // a list holds at most kPairedListFlush - 1 + 32 entries before its vote
+        if (cnt[0] >= kPairedListFlush) {
+          vote_list<1, U16, CUBE>(lst, cnt[0], yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy,
+                                  unit);
+          cnt[0] = 0;
+          __syncwarp();  // read before the next block rewrites the list
+        }
+        if constexpr (Q == 2) {
+          if (cnt[1] >= kPairedListFlush) {
+            vote_list<1, U16, CUBE>(lst + kPairedListCap, cnt[1], yx + 1, yy + 1, yz + 1, inv2, mx2, my2, mz2, Sx, Sy,
+                                    abase, hx, hy, hz, adummy, unit);
+            cnt[1] = 0;
+            __syncwarp();
+          }
+          if (cnt[2] >= kPairedListFlush) {
+            vote_list<2, U16, CUBE>(lst + 2 * kPairedListCap, cnt[2], yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase,
+                                    hx, hy, hz, adummy, unit);
+            cnt[2] = 0;
+            __syncwarp();
           }
         }
       }
+    }
+    if (cnt[0])
+      vote_list<1, U16, CUBE>(lst, cnt[0], yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy, unit);
+    if constexpr (Q == 2) {
+      if (cnt[1])
+        vote_list<1, U16, CUBE>(lst + kPairedListCap, cnt[1], yx + 1, yy + 1, yz + 1, inv2, mx2, my2, mz2, Sx, Sy,
+                                abase, hx, hy, hz, adummy, unit);
+      if (cnt[2])
+        vote_list<2, U16, CUBE>(lst + 2 * kPairedListCap, cnt[2], yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx,
+                                hy, hz, adummy, unit);
     }
     __syncwarp();
   }
@@ -673,7 +763,7 @@ __device__ __forceinline__ void vote_generic(const PassDesc& d, const float4* __
         const unsigned by = floor_bits(fmaf(ty[p][1], inv, c.y));
         const unsigned bz = floor_bits(fmaf(ty[p][2], inv, c.z));
         if (bx < SX && by < Ey && bz < Ez) {
-          const unsigned bin = (bx * Ey + by) * Ez + bz;
+          const unsigned bin = bx * d.hs[0] + by * d.hs[1] + bz;
           if (U16)
             atomicAdd(&hist[bin >> 1], 1u << ((bin & 1u) << 4));
           else
@@ -763,7 +853,8 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
         // the packed path stages 32 bytes per source; the sources are split
         // into equal chunks that fit the staging region
         const bool packed = P >= 2 && centred && !(SPARSE == 1 && d.sparse);
-        const int chunk = max(1, d.chunk[packed ? 1 : 0]);  // >= 1 whatever the descriptor holds
+        // (the paired culled instances stage tiles of 8 sources)
+        const int chunk = max(1, d.chunk[packed ? (SPARSE == 2 ? 2 : 1) : 0]);  // >= 1 whatever the descriptor holds
         for (int c0 = 0; c0 < d.N; c0 += chunk) {
           const int c1 = min(c0 + chunk, d.N);
           __syncthreads();  // previous chunk's readers are done
@@ -776,7 +867,13 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
             const float uz = fmaf(R[6], x, fmaf(R[7], y, R[8] * z));
             const float cx = fmaf(-ux, d.inv_delta, off0), cy = fmaf(-uy, d.inv_delta, off1),
                         cz = fmaf(-uz, d.inv_delta, off2);
-            if (packed) {
+            if (SPARSE == 2) {
+              float* t = reinterpret_cast<float*>(srcc) + ((i - c0) / kTileSources) * (kTileBytes / 4) +
+                         2 * ((i - c0) % kTileSources);
+              *reinterpret_cast<float2*>(t) = make_float2(cx, cx);
+              *reinterpret_cast<float2*>(t + 16) = make_float2(cy, cy);
+              *reinterpret_cast<float2*>(t + 32) = make_float2(cz, cz);
+            } else if (packed) {
               srcc[2 * (i - c0)] = make_float4(cx, cx, cy, cy);
               srcc[2 * (i - c0) + 1] = make_float4(cz, cz, 0.f, 0.f);
             } else {
@@ -794,7 +891,13 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
               const int i = b * 32 + lane;
               float lx = INFINITY, ly = INFINITY, lz = INFINITY, hx = -INFINITY, hy = -INFINITY, hz = -INFINITY;
               if (i < n) {
-                if (packed) {
+                if (SPARSE == 2) {
+                  const float* t = reinterpret_cast<const float*>(srcc) + (i / kTileSources) * (kTileBytes / 4) +
+                                   2 * (i % kTileSources);
+                  lx = hx = t[0];
+                  ly = hy = t[16];
+                  lz = hz = t[32];
+                } else if (packed) {
                   const float4 a = srcc[2 * i];
                   lx = hx = a.x;
                   ly = hy = a.z;
@@ -828,17 +931,20 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
             float* thr = s_thr[SPARSE ? warp : 0];
             const uint32_t sink = (uint32_t)__cvta_generic_to_shared(s_sink);
             const bool cube = SX == (unsigned)d.E[1] && d.E[1] == d.E[2];
+            uint32_t* lst = reinterpret_cast<uint32_t*>(smem + L.hist_bytes + L.src_bytes + L.blk_bytes) +
+                            warp * 3 * kPairedListCap;
+            const float* srct = reinterpret_cast<const float*>(srcc);
             if (d.hist_u16 && cube)
-              vote_centred_paired<PS, true, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink, blkp);
+              vote_centred_paired<PS, true, true>(d, srct, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink, blkp, lst);
             else if (d.hist_u16)
-              vote_centred_paired<PS, true, false>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink,
-                                                   blkp);
+              vote_centred_paired<PS, true, false>(d, srct, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink,
+                                                   blkp, lst);
             else if (cube)
-              vote_centred_paired<PS, false, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink,
-                                                   blkp);
+              vote_centred_paired<PS, false, true>(d, srct, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink,
+                                                   blkp, lst);
             else
-              vote_centred_paired<PS, false, false>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink,
-                                                    blkp);
+              vote_centred_paired<PS, false, false>(d, srct, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink,
+                                                    blkp, lst);
           } else if (SPARSE == 1) {  // ... and of this one 32-point culled problems only
             const bool cube = SX == (unsigned)d.E[1] && d.E[1] == d.E[2];
             float* thr = s_thr[SPARSE ? warp : 0];
@@ -880,7 +986,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
         }
         __syncthreads();
         // mode of this slab: scan and clear; each thread walks increasing bins
-        const unsigned nbins = SX * Ey * Ez;
+        const unsigned nbins = SX * d.hs[0];  // the slab's bins, stride padding included (never voted)
         unsigned bc = 0, bb = 0, vsum = 0;
         // (only PADDED instances carry the padded scan: the others keep the
         // hot loop's code generation of a kernel without it)
@@ -893,7 +999,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
           const unsigned rows = (unsigned)max(0, min((int)SX, d.Ev[0] - x0)) * Eyv;
           for (unsigned row = warp; row < rows; row += kPassThreads / 32) {
             const unsigned x = row / Eyv;
-            const unsigned base = (x * Ey + (row - x * Eyv)) * Ez;
+            const unsigned base = x * d.hs[0] + (row - x * Eyv) * d.hs[1];
             if (d.hist_lanes) {
               for (unsigned z = 0; z < Ezv; ++z) {
                 const unsigned c = warp_sum_u32(hist[(base + z) * 32u + lane]);
@@ -1014,7 +1120,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
           bb = found ? bb : 0u;
         }
         vtotal += warp_sum_u32(vsum);
-        const unsigned gbin = (unsigned)x0 * Ey * Ez + bb;
+        const unsigned gbin = (unsigned)x0 * d.hs[0] + bb;
         unsigned long long key = ((unsigned long long)bc << 32) | (unsigned long long)(0xffffffffu - gbin);
         key = warp_max_u64(key);
         if (lane == 0) red64[warp] = key;
@@ -1032,9 +1138,9 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
       if (tid == 0) {
         const unsigned V = (unsigned)(best >> 32);
         const unsigned gbin = 0xffffffffu - (unsigned)(best & 0xffffffffull);
-        const int kx = d.lo[0] + (int)(gbin / (Ey * Ez));
-        const int ky = d.lo[1] + (int)((gbin / Ez) % Ey);
-        const int kz = d.lo[2] + (int)(gbin % Ez);
+        const int kx = d.lo[0] + (int)(gbin / d.hs[0]);
+        const int ky = d.lo[1] + (int)((gbin % d.hs[0]) / d.hs[1]);
+        const int kz = d.lo[2] + (int)(gbin % d.hs[0] % d.hs[1]);
         d.kv[d.rot_base + (uint32_t)r - d.out_base] = make_int4(kx, ky, kz, (int)V);
         atomicMax(d.acc + 1, V);
       }
@@ -1114,7 +1220,7 @@ __global__ void __launch_bounds__(256) count_kernel(PassLaunch L) {
 
 template <int P, int SPARSE, bool PADDED>
 cudaError_t launch_vote_p(const PassLaunch& L, int grid_ctas, cudaStream_t s) {
-  const int smem = pass_smem_bytes(L.hist_bytes, L.src_bytes) + L.blk_bytes;
+  const int smem = pass_smem_bytes(L.hist_bytes, L.src_bytes) + L.blk_bytes + L.list_bytes;
   // the opt-in is per device: a process may launch this instance on several GPUs
   static OptIn optin;
   int dev = 0;

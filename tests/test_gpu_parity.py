@@ -167,9 +167,10 @@ def test_histogram_modes_and_launch_shapes_agree(ctx):
                 dict(hist_mode=2, hist_budget_bytes=9000), dict(points_per_thread=1), dict(points_per_thread=2),
                 dict(points_per_thread=8), dict(fuse_score=0), dict(tile_rotations=1), dict(vote_sparse=2),
                 dict(vote_sparse=2, points_per_thread=2), dict(vote_sparse=3), dict(vote_sparse=3, points_per_thread=2),
-                dict(vote_sparse=3, hist_mode=1)]
+                dict(vote_sparse=3, hist_mode=1), dict(hist_strides=0), dict(hist_strides=0, hist_mode=1),
+                dict(hist_strides=0, vote_sparse=3)]
     defaults = {k: ctx.get_option(k) for k in ("hist_mode", "hist_budget_bytes", "points_per_thread", "fuse_score",
-                                               "tile_rotations", "vote_sparse")}
+                                               "tile_rotations", "vote_sparse", "hist_strides")}
     try:
         for v in variants:
             for key, val in v.items():
@@ -415,7 +416,8 @@ def test_modelnet_full_size_sampled_rotations(ctx):
 
 def test_culled_modes_agree_on_robot_like(ctx):
     # the paired 64-point-group culling (auto here), the 32-point culling and
-    # the dense vote give bit-identical per-rotation (k*, V, M)
+    # the dense vote give bit-identical per-rotation (k*, V, M), and so do the
+    # compact and the bank-spreading histogram strides
     p = synth.robot_like_problem(0, hopf_n=2, refine_top_k=0)
     t = ctx.create_target(p.Y, grid_cap=p.grid_cap)
     pb = ctx.problem(t, p.X, capi.hopf_grid(2), gpu_params(p, nn_mode="grid", huber_h=p.huber_h, refine_top_k=0))
@@ -423,6 +425,11 @@ def test_culled_modes_agree_on_robot_like(ctx):
     base = ctx.debug(pb, n)
     assert ctx.get_option("last_vote_paired") == 1
     try:
+        ctx.set_option("hist_strides", 0)
+        k, V, M, C, r = ctx.debug(pb, n)
+        ctx.set_option("hist_strides", 1)
+        assert ctx.get_option("last_vote_paired") == 1
+        assert np.array_equal(k, base[0]) and np.array_equal(V, base[1]) and np.array_equal(M, base[2])
         for mode in (2, 1):
             ctx.set_option("vote_sparse", mode)
             k, V, M, C, r = ctx.debug(pb, n)
