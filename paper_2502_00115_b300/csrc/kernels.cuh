@@ -41,6 +41,9 @@ constexpr int kPassStaticSmem = 2048 + 32 * 8 * 8 * 4;
 constexpr int kPairedListCap = 48;
 constexpr int kPairedListFlush = 16;
 constexpr int kPairedListBytes = (kPassThreads / 32) * 3 * kPairedListCap * 4;
+// Culled vote: a source chunk's items are taken largest first (by their count
+// of 32-source blocks that can keep a group) when there are at most this many.
+constexpr int kItemOrderCap = 512;
 // Tiled staging of the paired culled vote: 8 sources per 192-byte tile, the
 // pairs (c_x, c_x) of its sources at bytes 0-63, (c_y, c_y) at 64-127 and
 // (c_z, c_z) at 128-191.
@@ -126,6 +129,9 @@ struct PassLaunch {
                            // offsets (8 floats each) after the staging; else 0
   int list_bytes;          // paired culled launches: the warps' lists of kept sources
                            // (kPairedListBytes) after the block bounds; else 0
+  int order_bytes;         // culled launches with block bounds: the order in which a
+                           // chunk's vote items are taken (kItemOrderCap words) after
+                           // the lists; else 0
   int padded;              // 1: some problem's layout is padded (E != Ev): the
                            // instance whose mode scan skips padding bins
 };
@@ -145,13 +151,14 @@ int pass_src_bytes(int hist_bytes, int n_src);
 // Shared memory of a rotation-pass launch past the histogram: the source
 // staging and, for a culled launch, the bounds of every block of 32 staged
 // sources (32 bytes each, sized for the plain layout's largest chunk), and for
-// a paired culled launch the warps' kept-source lists, both taken from the
-// staging room.
+// a paired culled launch the warps' kept-source lists, and for a culled launch
+// with block bounds the order of its items, all taken from the staging room.
 inline void pass_staging(int hist_bytes, int n_src_max, bool culled, bool paired, int* src_bytes, int* blk_bytes,
-                         int* list_bytes) {
+                         int* list_bytes, int* order_bytes) {
   int src = pass_src_bytes(hist_bytes, n_src_max);
   const int list = paired ? kPairedListBytes : 0;
-  src = (src - list) & ~31;
+  const int order = culled ? kItemOrderCap * 4 : 0;
+  src = (src - list - order) & ~31;
   int blk = 0;
   if (culled) {
     blk = ((src / 16 + 31) / 32) * 32;
@@ -160,6 +167,7 @@ inline void pass_staging(int hist_bytes, int n_src_max, bool culled, bool paired
   *src_bytes = src;
   *blk_bytes = blk;
   *list_bytes = list;
+  *order_bytes = order;
 }
 // Equal chunks of the problem's sources that fit src_bytes of staging, plain,
 // packed and tiled (d.chunk).

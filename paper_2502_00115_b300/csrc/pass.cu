@@ -413,6 +413,29 @@ __device__ __forceinline__ void vote_centred_x2(const PassDesc& d, const float4*
   }
 }
 
+// Keep windows of an item's G target groups (groups tc G .. tc G + G - 1 of
+// d.gbox): a staged source offset c keeps group g iff t[2a] <= c_a <= t[2a+1]
+// on every axis (8 floats per group at thr + 8 g; a missing group keeps
+// nothing). Lanes 0 .. G - 1 write one group each.
+template <int G>
+__device__ __forceinline__ void item_windows(const PassDesc& d, int tc, int lane, float* thr, float hx, float hy,
+                                             float hz, float inv) {
+  if (lane < G) {
+    const int g = tc * G + lane;
+    float* t = thr + 8 * lane;
+    if (g < d.n_groups) {
+      const float4 lo = __ldg(d.gbox + 2 * g), hi = __ldg(d.gbox + 2 * g + 1);
+      const float m = d.cull_margin;
+      t[0] = -hx - m - hi.x * inv; t[1] = hx + m - lo.x * inv;
+      t[2] = -hy - m - hi.y * inv; t[3] = hy + m - lo.y * inv;
+      t[4] = -hz - m - hi.z * inv; t[5] = hz + m - lo.z * inv;
+    } else {
+      t[0] = t[2] = t[4] = INFINITY;
+      t[1] = t[3] = t[5] = -INFINITY;
+    }
+  }
+}
+
 // The union of an item's G group windows (thr holds 8 floats per group:
 // lo_x, hi_x, lo_y, hi_y, lo_z, hi_z), written after them at thr + 8 G.
 template <int G>
@@ -441,6 +464,29 @@ __device__ __forceinline__ bool block_misses(const float* __restrict__ b, const 
   return b0.y < u0.x || b0.x > u0.y || b0.w < u0.z || b0.z > u0.w || b1.y < u1.x || b1.x > u1.y;
 }
 
+// Blocks of 32 staged sources that can keep one of an item's G groups (the
+// test the culled paths make before walking a block): the work estimate by
+// which a chunk's items are ordered.
+template <int G>
+__device__ __forceinline__ int item_blocks(const PassDesc& d, int it, int nsrc, const float* __restrict__ blkp,
+                                           float* thr, int lane, float hx, float hy, float hz) {
+  const int tc = it % d.n_tchunks, sg = it / d.n_tchunks;
+  item_windows<G>(d, tc, lane, thr, hx, hy, hz, d.inv_delta);
+  __syncwarp();
+  if (lane == 0) item_union<G>(thr);
+  __syncwarp();
+  const int spg = (nsrc + d.n_sgroups - 1) / d.n_sgroups;
+  const int i0 = sg * spg, i1 = min(i0 + spg, nsrc);
+  int n = 0;
+  for (int bb = i0 >> 5; bb < ((i1 + 31) >> 5); bb += 32) {
+    const int myb = bb + lane;
+    const bool rel = myb < ((i1 + 31) >> 5) && !block_misses(blkp + 8 * myb, thr + 8 * G);
+    n += __popc(__ballot_sync(0xffffffffu, rel));
+  }
+  __syncwarp();
+  return n;
+}
+
 // Sparse centred path, for translation boxes small against the target: the
 // P x 32 targets of an item are P groups of 32 consecutive points (in the
 // vote's target order) with known bounding boxes. For each block of 32
@@ -454,7 +500,8 @@ template <int P, bool U16, bool CUBE>
 __device__ __forceinline__ void vote_centred_sparse(const PassDesc& d, const float4* __restrict__ srcc, int nsrc,
                                                     unsigned SX, uint32_t hist_base, int* item_ctr, int lane,
                                                     float* __restrict__ thr, uint32_t sink,
-                                                    const float* __restrict__ blkp) {
+                                                    const float* __restrict__ blkp,
+                                                    const uint32_t* __restrict__ ord) {
   const int n_tchunks = d.n_tchunks, n_sgroups = d.n_sgroups;
   const int n_items = n_tchunks * n_sgroups;
   const int spg = (nsrc + n_sgroups - 1) / n_sgroups;
@@ -470,25 +517,12 @@ __device__ __forceinline__ void vote_centred_sparse(const PassDesc& d, const flo
   const uint32_t abase32 = hist_base + (d.hist_lanes ? 4u * (uint32_t)lane : 0u) - unit * bias;
   const uint32_t abase16 = hist_base - 2u * bias;
   const uint32_t sinkl = sink + 4u * (uint32_t)lane;
-  for (int it = next_item(item_ctr, lane); it < n_items; it = next_item(item_ctr, lane)) {
+  for (int k = next_item(item_ctr, lane); k < n_items; k = next_item(item_ctr, lane)) {
+    const int it = ord ? (int)ord[k] : k;  // largest items first when ordered
     const int tc = it % n_tchunks, sg = it / n_tchunks;
     float ty[P][3];
     load_targets(d.Yv, d.M, tc * P * 32, lane, P, ty);
-    // keep (source, group) iff s1_a <= c_a <= s2_a on every axis
-    if (lane < P) {
-      const int g = tc * P + lane;
-      float* t = thr + 8 * lane;
-      if (g < d.n_groups) {
-        const float4 lo = __ldg(d.gbox + 2 * g), hi = __ldg(d.gbox + 2 * g + 1);
-        const float m = d.cull_margin;
-        t[0] = -hx - m - hi.x * inv; t[1] = hx + m - lo.x * inv;
-        t[2] = -hy - m - hi.y * inv; t[3] = hy + m - lo.y * inv;
-        t[4] = -hz - m - hi.z * inv; t[5] = hz + m - lo.z * inv;
-      } else {
-        t[0] = t[2] = t[4] = INFINITY;
-        t[1] = t[3] = t[5] = -INFINITY;
-      }
-    }
+    item_windows<P>(d, tc, lane, thr, hx, hy, hz, inv);
     __syncwarp();
     if (blkp && lane == 0) item_union<P>(thr);
     __syncwarp();
@@ -611,7 +645,8 @@ template <int P, bool U16, bool CUBE>
 __device__ __forceinline__ void vote_centred_paired(const PassDesc& d, const float* __restrict__ srct, int nsrc,
                                                     unsigned SX, uint32_t hist_base, int* item_ctr, int lane,
                                                     float* __restrict__ thr, uint32_t sink,
-                                                    const float* __restrict__ blkp, uint32_t* __restrict__ lst) {
+                                                    const float* __restrict__ blkp, uint32_t* __restrict__ lst,
+                                                    const uint32_t* __restrict__ ord) {
   static_assert(P == 2 || P == 4, "two targets of each of P / 2 groups per lane");
   constexpr int Q = P / 2;            // 64-point groups per item
   constexpr int NL = Q == 2 ? 3 : 1;  // lists: first group only, second only, both
@@ -634,23 +669,10 @@ __device__ __forceinline__ void vote_centred_paired(const PassDesc& d, const flo
   const uint32_t adummy = sink + 4u * (uint32_t)lane;
   const uint32_t lt = (1u << lane) - 1u;
   const uint32_t tbase = (uint32_t)__cvta_generic_to_shared(srct);
-  for (int it = next_item(item_ctr, lane); it < n_items; it = next_item(item_ctr, lane)) {
+  for (int k = next_item(item_ctr, lane); k < n_items; k = next_item(item_ctr, lane)) {
+    const int it = ord ? (int)ord[k] : k;  // largest items first when ordered
     const int tc = it % n_tchunks, sg = it / n_tchunks;
-    // keep (source, group) iff s1_a <= c_a <= s2_a on every axis
-    if (lane < Q) {
-      const int g = tc * Q + lane;
-      float* t = thr + 8 * lane;
-      if (g < d.n_groups) {
-        const float4 lo = __ldg(d.gbox + 2 * g), hi = __ldg(d.gbox + 2 * g + 1);
-        const float m = d.cull_margin;
-        t[0] = -hx - m - hi.x * inv; t[1] = hx + m - lo.x * inv;
-        t[2] = -hy - m - hi.y * inv; t[3] = hy + m - lo.y * inv;
-        t[4] = -hz - m - hi.z * inv; t[5] = hz + m - lo.z * inv;
-      } else {
-        t[0] = t[2] = t[4] = INFINITY;
-        t[1] = t[3] = t[5] = -INFINITY;
-      }
-    }
+    item_windows<Q>(d, tc, lane, thr, hx, hy, hz, inv);
     __syncwarp();
     if (blkp && lane == 0) item_union<Q>(thr);
     __syncwarp();
@@ -926,6 +948,35 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
             __syncthreads();
             blkp = blk;
           }
+          // culled launches: the chunk's items taken largest first (by their
+          // blocks that can keep a group), so that the warps finish the chunk
+          // together rather than waiting at its barrier for the last large item
+          const uint32_t* ord = nullptr;
+          if (SPARSE && d.sparse && blkp && L.order_bytes) {
+            const int n_items = d.n_tchunks * d.n_sgroups;
+            if (n_items <= L.order_bytes / 4 && n_items <= kPassThreads) {
+              uint32_t* o =
+                  reinterpret_cast<uint32_t*>(smem + L.hist_bytes + L.src_bytes + L.blk_bytes + L.list_bytes);
+              float* thr = s_thr[SPARSE ? warp : 0];
+              const float hx = 0.5f * (float)SX, hy = 0.5f * (float)Ey, hz = 0.5f * (float)Ez;
+              for (int it = warp; it < n_items; it += kPassThreads / 32) {
+                const int nb = SPARSE == 2 ? item_blocks<(P >= 4 ? 2 : 1)>(d, it, c1 - c0, blkp, thr, lane, hx, hy, hz)
+                                           : item_blocks<(P >= 4 ? 4 : P)>(d, it, c1 - c0, blkp, thr, lane, hx, hy, hz);
+                if (lane == 0) o[it] = ((uint32_t)nb << 16) | (uint32_t)it;
+              }
+              __syncthreads();
+              // rank of each item's (count, index) key, descending: a permutation
+              uint32_t key = 0, rank = 0;
+              if (tid < n_items) {
+                key = o[tid];
+                for (int j = 0; j < n_items; ++j) rank += o[j] > key ? 1u : 0u;
+              }
+              __syncthreads();
+              if (tid < n_items) o[rank] = key & 0xffffu;
+              __syncthreads();
+              ord = o;
+            }
+          }
           if (SPARSE == 2) {  // launches of this instance hold paired culled problems only (odd layouts)
             constexpr int PS = P >= 4 ? 4 : 2;  // paired instances are built for 2 and 4
             float* thr = s_thr[SPARSE ? warp : 0];
@@ -935,32 +986,32 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
                             warp * 3 * kPairedListCap;
             const float* srct = reinterpret_cast<const float*>(srcc);
             if (d.hist_u16 && cube)
-              vote_centred_paired<PS, true, true>(d, srct, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink, blkp, lst);
+              vote_centred_paired<PS, true, true>(d, srct, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink, blkp, lst, ord);
             else if (d.hist_u16)
               vote_centred_paired<PS, true, false>(d, srct, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink,
-                                                   blkp, lst);
+                                                   blkp, lst, ord);
             else if (cube)
               vote_centred_paired<PS, false, true>(d, srct, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink,
-                                                   blkp, lst);
+                                                   blkp, lst, ord);
             else
               vote_centred_paired<PS, false, false>(d, srct, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink,
-                                                    blkp, lst);
+                                                    blkp, lst, ord);
           } else if (SPARSE == 1) {  // ... and of this one 32-point culled problems only
             const bool cube = SX == (unsigned)d.E[1] && d.E[1] == d.E[2];
             float* thr = s_thr[SPARSE ? warp : 0];
             const uint32_t sink = (uint32_t)__cvta_generic_to_shared(s_sink);
             if (d.hist_u16 && cube)
               vote_centred_sparse<P, true, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink,
-                                                     blkp);
+                                                     blkp, ord);
             else if (d.hist_u16)
               vote_centred_sparse<P, true, false>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink,
-                                                     blkp);
+                                                     blkp, ord);
             else if (cube)
               vote_centred_sparse<P, false, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink,
-                                                     blkp);
+                                                     blkp, ord);
             else
               vote_centred_sparse<P, false, false>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink,
-                                                     blkp);
+                                                     blkp, ord);
           } else if (centred) {
             constexpr int PP = P >= 2 ? P : 2;  // the P = 1 instance never takes the packed path
             if (packed) {
@@ -1220,7 +1271,7 @@ __global__ void __launch_bounds__(256) count_kernel(PassLaunch L) {
 
 template <int P, int SPARSE, bool PADDED>
 cudaError_t launch_vote_p(const PassLaunch& L, int grid_ctas, cudaStream_t s) {
-  const int smem = pass_smem_bytes(L.hist_bytes, L.src_bytes) + L.blk_bytes + L.list_bytes;
+  const int smem = pass_smem_bytes(L.hist_bytes, L.src_bytes) + L.blk_bytes + L.list_bytes + L.order_bytes;
   // the opt-in is per device: a process may launch this instance on several GPUs
   static OptIn optin;
   int dev = 0;
