@@ -721,6 +721,9 @@ void plan(dses_ctx* c, Job& j) {
   for (int a = 0; a < 3; ++a)
     span = std::min(span, (double)j.E[a] * j.delta / std::max(1e-12, (double)j.T->gext2[a]));
   j.sparse = !cull ? 0 : c->opt.vote_sparse == 2 ? 1 : c->opt.vote_sparse == 3 ? 2 : (span >= 0.6 ? 2 : 1);
+  // the paired form votes into shared counters only: lane-private counters
+  // take the 32-point culled path
+  if (j.lanes && j.sparse == 2) j.sparse = 1;
   if (c->opt.hist_strides && !j.lanes) spread_strides(j, budget);
 }
 

@@ -267,30 +267,55 @@ __device__ __forceinline__ void vote_centred(const PassDesc& d, const float4* __
   }
 }
 
-// The three steps shared by every form: w = y / delta + c (packed FMA), the
-// magic-number rounding of w (packed add) and the lattice index t of both
-// pairs. Box test: |w_a| < h_a on every axis, either per axis (three chained
-// compares) or, when the padded box is a cube, as max(|w_x|, |w_y|, |w_z|) < h
-// (one three-input max and one compare).
-#define DSES_VOTE2_HEAD                                                                          \
+// The three steps shared by every form: w = y / delta + c, the magic-number
+// rounding of w and the lattice index t of both pairs, with the x axis on
+// packed FP32 pairs (fma.rn.f32x2 / add.rn.f32x2) and the y and z axes either
+// packed too (DSES_VOTE2_HEAD_P: fewest instructions) or as scalar FP32 on
+// each half (DSES_VOTE2_HEAD_S: the packed operations issue to the FMA-heavy
+// pipe only, scalar ones to either FMA pipe; the culled vote, whose loop is
+// bound by that pipe, ran 7% faster with them; the dense 16-bit vote, bound
+// by issue, 6% slower). Either form rounds each value once, identically. Box
+// test: |w_a| < h_a on every axis, either per axis (three chained compares) or,
+// when the padded box is a cube, as max(|w_x|, |w_y|, |w_z|) < h (one
+// three-input max and one compare).
+#define DSES_VOTE2_DECL                                                                          \
   "{\n\t.reg .b64 wx, wy, wz, fx, fy, fz;\n\t"                                                   \
   ".reg .b32 bx0, bx1, by0, by1, bz0, bz1, t0, t1, a0, a1, i0, i1, u0, u1, v0, v1, s0, s1;\n\t"  \
-  ".reg .f32 x0, x1, y0, y1, z0, z1;\n\t.reg .pred p0, p1;\n\t"                                  \
+  ".reg .f32 x0, x1, y0, y1, z0, z1;\n\t.reg .pred p0, p1;\n\t"
+#define DSES_VOTE2_HEAD_P                                                                        \
+  DSES_VOTE2_DECL                                                                                \
   "fma.rn.f32x2 wx, %0, %3, %4;\n\tfma.rn.f32x2 wy, %1, %3, %5;\n\tfma.rn.f32x2 wz, %2, %3, %6;\n\t" \
   "add.rn.f32x2 fx, wx, %7;\n\tadd.rn.f32x2 fy, wy, %8;\n\tadd.rn.f32x2 fz, wz, %9;\n\t"         \
   "mov.b64 {bx0, bx1}, fx;\n\tmov.b64 {by0, by1}, fy;\n\tmov.b64 {bz0, bz1}, fz;\n\t"
-// 16-bit counters: word t >> 1, half t & 1 (increment 1 or 65536)
-#define DSES_VOTE2_ADDR16                                                   \
-  "mad.lo.u32 t0, by0, %11, bz0;\n\tmad.lo.u32 t0, bx0, %10, t0;\n\t"      \
-  "mad.lo.u32 t1, by1, %11, bz1;\n\tmad.lo.u32 t1, bx1, %10, t1;\n\t"      \
-  "shr.u32 a0, t0, 1;\n\tshr.u32 a1, t1, 1;\n\t"                           \
-  "mad.lo.u32 a0, a0, 4, %12;\n\tmad.lo.u32 a1, a1, 4, %12;\n\t"           \
-  "and.b32 i0, t0, 1;\n\tand.b32 i1, t1, 1;\n\t"                           \
-  "mad.lo.u32 i0, i0, 65535, 1;\n\tmad.lo.u32 i1, i1, 65535, 1;\n\t"
-// 32-bit counters: strides %10 / %11 already scaled by the word stride %17
-#define DSES_VOTE2_ADDR32                                                                            \
-  "mad.lo.u32 t0, bz0, %17, %12;\n\tmad.lo.u32 t0, by0, %11, t0;\n\tmad.lo.u32 a0, bx0, %10, t0;\n\t" \
-  "mad.lo.u32 t1, bz1, %17, %12;\n\tmad.lo.u32 t1, by1, %11, t1;\n\tmad.lo.u32 a1, bx1, %10, t1;\n\t"
+#define DSES_VOTE2_HEAD_S                                                                        \
+  DSES_VOTE2_DECL                                                                                \
+  ".reg .f32 j0, j1, qy0, qy1, cy0, cy1, my0, my1, wy0, wy1, gy0, gy1;\n\t"                      \
+  ".reg .f32 qz0, qz1, cz0, cz1, mz0, mz1, wz0, wz1, gz0, gz1;\n\t"                              \
+  "fma.rn.f32x2 wx, %0, %3, %4;\n\tadd.rn.f32x2 fx, wx, %7;\n\t"                                 \
+  "mov.b64 {j0, j1}, %3;\n\t"                                                                    \
+  "mov.b64 {qy0, qy1}, %1;\n\tmov.b64 {cy0, cy1}, %5;\n\tmov.b64 {my0, my1}, %8;\n\t"            \
+  "fma.rn.f32 wy0, qy0, j0, cy0;\n\tfma.rn.f32 wy1, qy1, j1, cy1;\n\t"                           \
+  "add.rn.f32 gy0, wy0, my0;\n\tadd.rn.f32 gy1, wy1, my1;\n\t"                                   \
+  "mov.b64 {qz0, qz1}, %2;\n\tmov.b64 {cz0, cz1}, %6;\n\tmov.b64 {mz0, mz1}, %9;\n\t"            \
+  "fma.rn.f32 wz0, qz0, j0, cz0;\n\tfma.rn.f32 wz1, qz1, j1, cz1;\n\t"                           \
+  "add.rn.f32 gz0, wz0, mz0;\n\tadd.rn.f32 gz1, wz1, mz1;\n\t"                                   \
+  "mov.b64 wy, {wy0, wy1};\n\tmov.b64 wz, {wz0, wz1};\n\t"                                       \
+  "mov.b64 {bx0, bx1}, fx;\n\tmov.b32 by0, gy0;\n\tmov.b32 by1, gy1;\n\t"                        \
+  "mov.b32 bz0, gz0;\n\tmov.b32 bz1, gz1;\n\t"
+// 16-bit counters: word t >> 1 (address = base + 4 word), half t & 1: the
+// increment 1 << 16 (t & 1) is a funnel shift by (t << 4) mod 32; the
+// multiplies of the bin index are the only work on the FMA-heavy pipe
+#define DSES_VOTE2_ADDR16                                                                     \
+  "mad.lo.u32 t0, by0, %11, bz0;\n\tmad.lo.u32 t0, bx0, %10, t0;\n\t"                        \
+  "mad.lo.u32 t1, by1, %11, bz1;\n\tmad.lo.u32 t1, bx1, %10, t1;\n\t"                        \
+  "shr.u32 a0, t0, 1;\n\tshr.u32 a1, t1, 1;\n\t"                                             \
+  "shl.b32 a0, a0, 2;\n\tshl.b32 a1, a1, 2;\n\tadd.u32 a0, a0, %12;\n\tadd.u32 a1, a1, %12;\n\t" \
+  "shl.b32 i0, t0, 4;\n\tshl.b32 i1, t1, 4;\n\t"                                             \
+  "shf.l.wrap.b32 i0, 0, 1, i0;\n\tshf.l.wrap.b32 i1, 0, 1, i1;\n\t"
+// 32-bit counters: base + 4 kz + %11 ky + %10 kx (strides %10 / %11 in bytes)
+#define DSES_VOTE2_ADDR32                                                                      \
+  "shl.b32 t0, bz0, 2;\n\tadd.u32 t0, t0, %12;\n\tmad.lo.u32 t0, by0, %11, t0;\n\tmad.lo.u32 a0, bx0, %10, t0;\n\t" \
+  "shl.b32 t1, bz1, 2;\n\tadd.u32 t1, t1, %12;\n\tmad.lo.u32 t1, by1, %11, t1;\n\tmad.lo.u32 a1, bx1, %10, t1;\n\t"
 #define DSES_VOTE2_ABS                                                                      \
   "mov.b64 {u0, u1}, wx;\n\tmov.b64 {v0, v1}, wy;\n\tmov.b64 {s0, s1}, wz;\n\t"             \
   "mov.b32 x0, u0;\n\tmov.b32 x1, u1;\n\tmov.b32 y0, v0;\n\tmov.b32 y1, v1;\n\t"           \
@@ -312,24 +337,33 @@ __device__ __forceinline__ void vote_centred(const PassDesc& d, const float4* __
   "red.shared.add.u32 [a0], 1;\n\tred.shared.add.u32 [a1], 1;\n\t}"
 
 // Two (source, target) pairs as packed FP32 pairs: lattice index, box test and
-// one unconditional shared add per pair.
-template <bool U16, bool CUBE>
+// one unconditional shared add per pair (shared 16- or 32-bit counters; the
+// lane-private layout takes the scalar path). SCALAR: the y and z axes in
+// scalar FP32 (DSES_VOTE2_HEAD_S), else packed (DSES_VOTE2_HEAD_P).
+template <bool U16, bool CUBE, bool SCALAR>
 __device__ __forceinline__ void vote_two_pairs(uint64_t yx, uint64_t yy, uint64_t yz, uint64_t inv2, uint64_t cx2,
                                                uint64_t cy2, uint64_t cz2, uint64_t mx2, uint64_t my2, uint64_t mz2,
                                                uint32_t Sx, uint32_t Sy, uint32_t abase, float hx, float hy,
-                                               float hz, uint32_t adummy, uint32_t unit) {
-  const uint32_t sy = U16 ? Sx : Sx * unit, sz = U16 ? Sy : Sy * unit;
+                                               float hz, uint32_t adummy) {
+  const uint32_t sy = U16 ? Sx : Sx * 4u, sz = U16 ? Sy : Sy * 4u;
 #define DSES_VOTE2_ARGS                                                                                         \
   ::"l"(yx), "l"(yy), "l"(yz), "l"(inv2), "l"(cx2), "l"(cy2), "l"(cz2), "l"(mx2), "l"(my2), "l"(mz2), "r"(sy), \
-      "r"(sz), "r"(abase), "f"(hx), "f"(hy), "f"(hz), "r"(adummy), "r"(unit)
-  if (U16 && CUBE)
-    asm volatile(DSES_VOTE2_HEAD DSES_VOTE2_ADDR16 DSES_VOTE2_ABS DSES_VOTE2_TEST_CUBE DSES_VOTE2_RED16 DSES_VOTE2_ARGS);
-  else if (U16)
-    asm volatile(DSES_VOTE2_HEAD DSES_VOTE2_ADDR16 DSES_VOTE2_ABS DSES_VOTE2_TEST_AXES DSES_VOTE2_RED16 DSES_VOTE2_ARGS);
-  else if (CUBE)
-    asm volatile(DSES_VOTE2_HEAD DSES_VOTE2_ADDR32 DSES_VOTE2_ABS DSES_VOTE2_TEST_CUBE DSES_VOTE2_RED32 DSES_VOTE2_ARGS);
-  else
-    asm volatile(DSES_VOTE2_HEAD DSES_VOTE2_ADDR32 DSES_VOTE2_ABS DSES_VOTE2_TEST_AXES DSES_VOTE2_RED32 DSES_VOTE2_ARGS);
+      "r"(sz), "r"(abase), "f"(hx), "f"(hy), "f"(hz), "r"(adummy)
+#define DSES_VOTE2_FORMS(HEAD)                                                                                   \
+  if (U16 && CUBE)                                                                                               \
+    asm volatile(HEAD DSES_VOTE2_ADDR16 DSES_VOTE2_ABS DSES_VOTE2_TEST_CUBE DSES_VOTE2_RED16 DSES_VOTE2_ARGS);   \
+  else if (U16)                                                                                                  \
+    asm volatile(HEAD DSES_VOTE2_ADDR16 DSES_VOTE2_ABS DSES_VOTE2_TEST_AXES DSES_VOTE2_RED16 DSES_VOTE2_ARGS);   \
+  else if (CUBE)                                                                                                 \
+    asm volatile(HEAD DSES_VOTE2_ADDR32 DSES_VOTE2_ABS DSES_VOTE2_TEST_CUBE DSES_VOTE2_RED32 DSES_VOTE2_ARGS);   \
+  else                                                                                                           \
+    asm volatile(HEAD DSES_VOTE2_ADDR32 DSES_VOTE2_ABS DSES_VOTE2_TEST_AXES DSES_VOTE2_RED32 DSES_VOTE2_ARGS);
+  if (SCALAR) {
+    DSES_VOTE2_FORMS(DSES_VOTE2_HEAD_S)
+  } else {
+    DSES_VOTE2_FORMS(DSES_VOTE2_HEAD_P)
+  }
+#undef DSES_VOTE2_FORMS
 #undef DSES_VOTE2_ARGS
 }
 
@@ -344,7 +378,7 @@ template <int Q, bool U16, bool CUBE>
 __device__ __forceinline__ void vote_sources_x2(const float4* __restrict__ srcd, int i0, int i1, const uint64_t* yx,
                                                 const uint64_t* yy, const uint64_t* yz, uint64_t inv2, uint64_t mx2,
                                                 uint64_t my2, uint64_t mz2, uint32_t Sx, uint32_t Sy, uint32_t abase,
-                                                float hx, float hy, float hz, uint32_t adummy, uint32_t unit) {
+                                                float hx, float hy, float hz, uint32_t adummy) {
 #pragma unroll 4
   for (int i = i0; i < i1; ++i) {
     const float4 ca = srcd[2 * i];
@@ -352,8 +386,8 @@ __device__ __forceinline__ void vote_sources_x2(const float4* __restrict__ srcd,
     const uint64_t cx2 = pack2(ca.x, ca.y), cy2 = pack2(ca.z, ca.w), cz2 = pack2(cb.x, cb.y);
 #pragma unroll
     for (int q = 0; q < Q; ++q)
-      vote_two_pairs<U16, CUBE>(yx[q], yy[q], yz[q], inv2, cx2, cy2, cz2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz,
-                                adummy, unit);
+      vote_two_pairs<U16, CUBE, !U16>(yx[q], yy[q], yz[q], inv2, cx2, cy2, cz2, mx2, my2, mz2, Sx, Sy, abase, hx, hy,
+                                      hz, adummy);
   }
 }
 
@@ -385,10 +419,8 @@ __device__ __forceinline__ void vote_centred_x2(const PassDesc& d, const float4*
               mz = kMagic + (float)((Ez - 1) / 2);
   const uint64_t inv2 = pack2(inv, inv), mx2 = pack2(mx, mx), my2 = pack2(my, my), mz2 = pack2(mz, mz);
   const uint32_t bias = kMagicBits * (Sx + Sy + 1u);
-  // 32-bit counters: word stride `unit` bytes (4, or 128 with a copy per lane)
-  const uint32_t unit = d.hist_lanes ? 128u : 4u;
-  const uint32_t abase = U16 ? hist_base - 2u * bias
-                             : hist_base + (d.hist_lanes ? 4u * (uint32_t)lane : 0u) - unit * bias;
+  // shared counters (the lane-private layout takes the scalar path)
+  const uint32_t abase = U16 ? hist_base - 2u * bias : hist_base - 4u * bias;
   // a pair outside the box adds to this lane's sink word outside the
   // histogram instead (no branch, and the increment needs no select)
   const uint32_t adummy = sink + 4u * (uint32_t)lane;
@@ -406,10 +438,10 @@ __device__ __forceinline__ void vote_centred_x2(const PassDesc& d, const float4*
     const int i0 = sg * spg, i1 = min(i0 + spg, nsrc);
     if (DENSE_INST && cube)
       vote_sources_x2<P / 2, U16, true>(srcd, i0, i1, yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz,
-                                       adummy, unit);
+                                       adummy);
     else
       vote_sources_x2<P / 2, U16, false>(srcd, i0, i1, yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz,
-                                        adummy, unit);
+                                        adummy);
   }
 }
 
@@ -583,16 +615,16 @@ __device__ __forceinline__ void vote_centred_sparse(const PassDesc& d, const flo
 template <int G, bool U16, bool CUBE>
 __device__ __forceinline__ void vote_staged(uint32_t a, const uint64_t* yx, const uint64_t* yy, const uint64_t* yz,
                                             uint64_t inv2, uint64_t mx2, uint64_t my2, uint64_t mz2, uint32_t Sx,
-                                            uint32_t Sy, uint32_t abase, float hx, float hy, float hz, uint32_t adummy,
-                                            uint32_t unit) {
+                                            uint32_t Sy, uint32_t abase, float hx, float hy, float hz,
+                                            uint32_t adummy) {
   uint64_t cx2, cy2, cz2;
   asm("ld.shared.b64 %0, [%3];\n\tld.shared.b64 %1, [%3+64];\n\tld.shared.b64 %2, [%3+128];"
       : "=l"(cx2), "=l"(cy2), "=l"(cz2)
       : "r"(a));
 #pragma unroll
   for (int g = 0; g < G; ++g)
-    vote_two_pairs<U16, CUBE>(yx[g], yy[g], yz[g], inv2, cx2, cy2, cz2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz,
-                              adummy, unit);
+    vote_two_pairs<U16, CUBE, true>(yx[g], yy[g], yz[g], inv2, cx2, cy2, cz2, mx2, my2, mz2, Sx, Sy, abase, hx, hy,
+                                    hz, adummy);
 }
 
 // The n kept sources of a list against the lane's target pairs of G groups,
@@ -601,19 +633,19 @@ template <int G, bool U16, bool CUBE>
 __device__ __forceinline__ void vote_list(const uint32_t* __restrict__ lst, int n, const uint64_t* yx,
                                           const uint64_t* yy, const uint64_t* yz, uint64_t inv2, uint64_t mx2,
                                           uint64_t my2, uint64_t mz2, uint32_t Sx, uint32_t Sy, uint32_t abase,
-                                          float hx, float hy, float hz, uint32_t adummy, uint32_t unit) {
+                                          float hx, float hy, float hz, uint32_t adummy) {
   int k = 0;
 #pragma unroll 1
   for (; k + 4 <= n; k += 4) {
     const uint4 a = *reinterpret_cast<const uint4*>(lst + k);
-    vote_staged<G, U16, CUBE>(a.x, yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy, unit);
-    vote_staged<G, U16, CUBE>(a.y, yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy, unit);
-    vote_staged<G, U16, CUBE>(a.z, yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy, unit);
-    vote_staged<G, U16, CUBE>(a.w, yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy, unit);
+    vote_staged<G, U16, CUBE>(a.x, yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy);
+    vote_staged<G, U16, CUBE>(a.y, yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy);
+    vote_staged<G, U16, CUBE>(a.z, yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy);
+    vote_staged<G, U16, CUBE>(a.w, yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy);
   }
 #pragma unroll 1
   for (; k < n; ++k)
-    vote_staged<G, U16, CUBE>(lst[k], yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy, unit);
+    vote_staged<G, U16, CUBE>(lst[k], yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy);
 }
 
 // Appends the lanes whose flag is set to a warp's list (each at its rank in
@@ -663,9 +695,8 @@ __device__ __forceinline__ void vote_centred_paired(const PassDesc& d, const flo
   const uint64_t inv2 = pack2(inv, inv), mx2 = pack2(mx, mx), my2 = CUBE ? mx2 : pack2(my, my),
                  mz2 = CUBE ? mx2 : pack2(mz, mz);
   const uint32_t bias = kMagicBits * (Sx + Sy + 1u);
-  const uint32_t unit = d.hist_lanes ? 128u : 4u;
-  const uint32_t abase = U16 ? hist_base - 2u * bias
-                             : hist_base + (d.hist_lanes ? 4u * (uint32_t)lane : 0u) - unit * bias;
+  // shared counters (the planner keeps the lane-private layout off this path)
+  const uint32_t abase = U16 ? hist_base - 2u * bias : hist_base - 4u * bias;
   const uint32_t adummy = sink + 4u * (uint32_t)lane;
   const uint32_t lt = (1u << lane) - 1u;
   const uint32_t tbase = (uint32_t)__cvta_generic_to_shared(srct);
@@ -725,21 +756,20 @@ __device__ __forceinline__ void vote_centred_paired(const PassDesc& d, const flo
         __syncwarp();
         // a list holds at most kPairedListFlush - 1 + 32 entries before its vote
         if (cnt[0] >= kPairedListFlush) {
-          vote_list<1, U16, CUBE>(lst, cnt[0], yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy,
-                                  unit);
+          vote_list<1, U16, CUBE>(lst, cnt[0], yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy);
           cnt[0] = 0;
           __syncwarp();  // read before the next block rewrites the list
         }
         if constexpr (Q == 2) {
           if (cnt[1] >= kPairedListFlush) {
             vote_list<1, U16, CUBE>(lst + kPairedListCap, cnt[1], yx + 1, yy + 1, yz + 1, inv2, mx2, my2, mz2, Sx, Sy,
-                                    abase, hx, hy, hz, adummy, unit);
+                                    abase, hx, hy, hz, adummy);
             cnt[1] = 0;
             __syncwarp();
           }
           if (cnt[2] >= kPairedListFlush) {
             vote_list<2, U16, CUBE>(lst + 2 * kPairedListCap, cnt[2], yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase,
-                                    hx, hy, hz, adummy, unit);
+                                    hx, hy, hz, adummy);
             cnt[2] = 0;
             __syncwarp();
           }
@@ -747,14 +777,14 @@ __device__ __forceinline__ void vote_centred_paired(const PassDesc& d, const flo
       }
     }
     if (cnt[0])
-      vote_list<1, U16, CUBE>(lst, cnt[0], yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy, unit);
+      vote_list<1, U16, CUBE>(lst, cnt[0], yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy);
     if constexpr (Q == 2) {
       if (cnt[1])
         vote_list<1, U16, CUBE>(lst + kPairedListCap, cnt[1], yx + 1, yy + 1, yz + 1, inv2, mx2, my2, mz2, Sx, Sy,
-                                abase, hx, hy, hz, adummy, unit);
+                                abase, hx, hy, hz, adummy);
       if (cnt[2])
         vote_list<2, U16, CUBE>(lst + 2 * kPairedListCap, cnt[2], yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx,
-                                hy, hz, adummy, unit);
+                                hy, hz, adummy);
     }
     __syncwarp();
   }
@@ -874,7 +904,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
         }
         // the packed path stages 32 bytes per source; the sources are split
         // into equal chunks that fit the staging region
-        const bool packed = P >= 2 && centred && !(SPARSE == 1 && d.sparse);
+        const bool packed = P >= 2 && centred && !(SPARSE == 1 && d.sparse) && !d.hist_lanes;
         // (the paired culled instances stage tiles of 8 sources)
         const int chunk = max(1, d.chunk[packed ? (SPARSE == 2 ? 2 : 1) : 0]);  // >= 1 whatever the descriptor holds
         for (int c0 = 0; c0 < d.N; c0 += chunk) {
