@@ -468,32 +468,23 @@ __device__ __forceinline__ void item_windows(const PassDesc& d, int tc, int lane
   }
 }
 
-// The union of an item's G group windows (thr holds 8 floats per group:
-// lo_x, hi_x, lo_y, hi_y, lo_z, hi_z), written after them at thr + 8 G.
+// Can a block of 32 staged sources keep one of an item's G groups? b holds
+// the block's offset bounds (lo_x, hi_x, lo_y, hi_y, lo_z, hi_z), thr the
+// groups' windows (8 floats each, same order). A block whose bounds miss every
+// window on some axis holds no source that keeps a group (the per-source test
+// compares the same values), so it is skipped whole.
 template <int G>
-__device__ __forceinline__ void item_union(float* thr) {
-  float u[6] = {INFINITY, -INFINITY, INFINITY, -INFINITY, INFINITY, -INFINITY};
-#pragma unroll
-  for (int g = 0; g < G; ++g)
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      u[2 * a] = fminf(u[2 * a], thr[8 * g + 2 * a]);
-      u[2 * a + 1] = fmaxf(u[2 * a + 1], thr[8 * g + 2 * a + 1]);
-    }
-#pragma unroll
-  for (int k = 0; k < 6; ++k) thr[8 * G + k] = u[k];
-}
-
-// A block of 32 staged sources whose offset bounds (lo/hi per axis, the
-// layout of item_union) miss the item's union window on some axis: none of
-// its sources keeps any of the item's groups (the per-source test compares
-// the same values), so the block is skipped whole.
-__device__ __forceinline__ bool block_misses(const float* __restrict__ b, const float* __restrict__ u) {
+__device__ __forceinline__ bool block_keeps(const float* __restrict__ b, const float* __restrict__ thr) {
   const float4 b0 = *reinterpret_cast<const float4*>(b);
   const float2 b1 = *reinterpret_cast<const float2*>(b + 4);
-  const float4 u0 = *reinterpret_cast<const float4*>(u);
-  const float2 u1 = *reinterpret_cast<const float2*>(u + 4);
-  return b0.y < u0.x || b0.x > u0.y || b0.w < u0.z || b0.z > u0.w || b1.y < u1.x || b1.x > u1.y;
+  bool any = false;
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const float4 u0 = *reinterpret_cast<const float4*>(thr + 8 * g);
+    const float2 u1 = *reinterpret_cast<const float2*>(thr + 8 * g + 4);
+    any |= b0.y >= u0.x && b0.x <= u0.y && b0.w >= u0.z && b0.z <= u0.w && b1.y >= u1.x && b1.x <= u1.y;
+  }
+  return any;
 }
 
 // Blocks of 32 staged sources that can keep one of an item's G groups (the
@@ -505,14 +496,12 @@ __device__ __forceinline__ int item_blocks(const PassDesc& d, int it, int nsrc, 
   const int tc = it % d.n_tchunks, sg = it / d.n_tchunks;
   item_windows<G>(d, tc, lane, thr, hx, hy, hz, d.inv_delta);
   __syncwarp();
-  if (lane == 0) item_union<G>(thr);
-  __syncwarp();
   const int spg = (nsrc + d.n_sgroups - 1) / d.n_sgroups;
   const int i0 = sg * spg, i1 = min(i0 + spg, nsrc);
   int n = 0;
   for (int bb = i0 >> 5; bb < ((i1 + 31) >> 5); bb += 32) {
     const int myb = bb + lane;
-    const bool rel = myb < ((i1 + 31) >> 5) && !block_misses(blkp + 8 * myb, thr + 8 * G);
+    const bool rel = myb < ((i1 + 31) >> 5) && block_keeps<G>(blkp + 8 * myb, thr);
     n += __popc(__ballot_sync(0xffffffffu, rel));
   }
   __syncwarp();
@@ -556,8 +545,6 @@ __device__ __forceinline__ void vote_centred_sparse(const PassDesc& d, const flo
     load_targets(d.Yv, d.M, tc * P * 32, lane, P, ty);
     item_windows<P>(d, tc, lane, thr, hx, hy, hz, inv);
     __syncwarp();
-    if (blkp && lane == 0) item_union<P>(thr);
-    __syncwarp();
     const int i0 = sg * spg, i1 = min(i0 + spg, nsrc);
     // the aligned blocks of 32 staged sources that meet [i0, i1), 32 at a
     // time: a lane tests one block's bounds, and only blocks that can keep a
@@ -565,7 +552,7 @@ __device__ __forceinline__ void vote_centred_sparse(const PassDesc& d, const flo
     for (int bb = i0 >> 5; bb < ((i1 + 31) >> 5); bb += 32) {
       const int myb = bb + lane;
       bool rel = myb < ((i1 + 31) >> 5);
-      if (blkp && rel) rel = !block_misses(blkp + 8 * myb, thr + 8 * P);
+      if (blkp && rel) rel = block_keeps<P>(blkp + 8 * myb, thr);
       uint32_t bmask = __ballot_sync(0xffffffffu, rel);
       while (bmask) {
         const int s0 = (bb + __ffs(bmask) - 1) << 5;
@@ -705,8 +692,6 @@ __device__ __forceinline__ void vote_centred_paired(const PassDesc& d, const flo
     const int tc = it % n_tchunks, sg = it / n_tchunks;
     item_windows<Q>(d, tc, lane, thr, hx, hy, hz, inv);
     __syncwarp();
-    if (blkp && lane == 0) item_union<Q>(thr);
-    __syncwarp();
     // the lane's target pairs, one per group; padding lanes never vote
     uint64_t yx[Q], yy[Q], yz[Q];
 #pragma unroll
@@ -728,7 +713,7 @@ __device__ __forceinline__ void vote_centred_paired(const PassDesc& d, const flo
     for (int bb = i0 >> 5; bb < ((i1 + 31) >> 5); bb += 32) {
       const int myb = bb + lane;
       bool rel = myb < ((i1 + 31) >> 5);
-      if (blkp && rel) rel = !block_misses(blkp + 8 * myb, thr + 8 * Q);
+      if (blkp && rel) rel = block_keeps<Q>(blkp + 8 * myb, thr);
       uint32_t bmask = __ballot_sync(0xffffffffu, rel);
       while (bmask) {
         const int s0 = (bb + __ffs(bmask) - 1) << 5;
