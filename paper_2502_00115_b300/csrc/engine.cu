@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -579,30 +580,19 @@ int layout_bytes(int64_t sx, int64_t hs0, bool u16) {
 }
 
 // How well strides (hs0, hs1) spread a lattice neighbourhood over the 32
-// shared-memory banks: a warp's increments come from a compact patch of
-// targets, so its bins are near each other, and two bins whose word indices
-// differ by a non-zero multiple of 32 share a bank. Returns the squared
-// length of the shortest offset |d|_inf <= 4 that lands in the same bank on a
-// different word (larger is better) and, second, how many offsets of squared
-// length <= 9 do (fewer is better). 16-bit counters: word = bin / 2, so an
-// offset conflicts when its bin difference is within one of a multiple of 64
-// (and at least 2).
-std::pair<int, int> bank_spread(int64_t hs0, int64_t hs1, bool u16) {
+// shared-memory banks (32-bit counters): a warp's increments come from a
+// compact patch of targets, so its bins are near each other, and two bins
+// whose indices differ by a non-zero multiple of 32 share a bank. Returns the
+// squared length of the shortest offset |d|_inf <= 4 that lands in the same
+// bank (larger is better) and, second, how many offsets of squared length
+// <= 9 do (fewer is better).
+std::pair<int, int> bank_spread(int64_t hs0, int64_t hs1) {
   int shortest = 1 << 30, close = 0;
   for (int dx = -4; dx <= 4; ++dx)
     for (int dy = -4; dy <= 4; ++dy)
       for (int dz = -4; dz <= 4; ++dz) {
         const int n2 = dx * dx + dy * dy + dz * dz;
-        if (n2 == 0) continue;
-        const int64_t v = dx * hs0 + dy * hs1 + dz;
-        bool same_bank;
-        if (u16) {
-          const int64_t m = ((v % 64) + 64) % 64;
-          same_bank = std::llabs(v) >= 2 && (m <= 1 || m == 63);
-        } else {
-          same_bank = v % 32 == 0;
-        }
-        if (!same_bank) continue;
+        if (n2 == 0 || (dx * hs0 + dy * hs1 + dz) % 32 != 0) continue;
         shortest = std::min(shortest, n2);
         close += n2 <= 9 ? 1 : 0;
       }
@@ -621,36 +611,61 @@ int source_chunks(const Job& j, int hist_bytes) {
   return (j.N + cap - 1) / cap;
 }
 
-// Row and plane strides (in bins) of the vote histogram, padded past the
-// extents where that spreads a lattice neighbourhood over more banks
+// Row and plane strides (in bins) of the 32-bit vote histogram, padded past
+// the extents where that spreads a lattice neighbourhood over more banks
 // (bank_spread) without costing a slab or a source chunk: the slab keeps its
 // x-planes within the budget and the launch stages the sources in as many
 // chunks as with the compact layout. Padding bins are never voted (a pair
-// inside the box has k_a < E_a) and read as zero by the mode scan.
+// inside the box has k_a < E_a) and read as zero by the mode scan. 16-bit
+// counters keep the compact layout: their conflicts come mostly from the two
+// halves of one word, which padding does not separate. The choice depends on
+// the extents and the byte limit only, and is cached.
 void spread_strides(Job& j, int64_t budget) {
-  const bool u16 = j.u16;
+  if (j.u16) return;
   const int64_t Ey = j.Ep[1], Ez = j.Ep[2], sx = j.slab_x;
+  // the largest histogram that keeps the budget and the source chunks
   const int chunks0 = source_chunks(j, j.hist_bytes);
-  auto best = bank_spread(j.hs[0], j.hs[1], u16);
-  int64_t b0 = j.hs[0], b1 = j.hs[1];
-  int bbytes = j.hist_bytes;
-  for (int64_t hs1 = Ez; hs1 < Ez + 8; ++hs1)
-    for (int64_t hs0 = Ey * hs1; hs0 < Ey * hs1 + 32; ++hs0) {
-      const int bytes = layout_bytes(sx, hs0, u16);
-      if (bytes + 8 > budget || source_chunks(j, bytes) > chunks0) continue;
-      const auto sc = bank_spread(hs0, hs1, u16);
-      const bool better = sc.first > best.first || (sc.first == best.first && sc.second < best.second) ||
-                          (sc == best && bytes < bbytes);
-      if (better) {
-        best = sc;
-        b0 = hs0;
-        b1 = hs1;
-        bbytes = bytes;
-      }
+  int64_t lo = j.hist_bytes, hi = budget - 8;
+  if (hi < lo) return;
+  if (source_chunks(j, (int)hi) > chunks0) {
+    while (hi - lo > 16) {
+      const int64_t mid = (lo + hi) / 2;
+      if (source_chunks(j, (int)mid) > chunks0) hi = mid; else lo = mid;
     }
-  j.hs[0] = b0;
-  j.hs[1] = b1;
-  j.hist_bytes = bbytes;
+    hi = lo;
+  }
+  const int64_t limit = hi;
+  static std::mutex mu;
+  static std::map<std::array<int64_t, 4>, std::pair<int64_t, int64_t>> cache;
+  const std::array<int64_t, 4> key{Ey, Ez, sx, limit};
+  std::pair<int64_t, int64_t> pick;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      pick = it->second;
+    } else {
+      auto best = bank_spread(j.hs[0], j.hs[1]);
+      pick = {j.hs[0], j.hs[1]};
+      int bbytes = j.hist_bytes;
+      for (int64_t hs1 = Ez; hs1 < Ez + 8; ++hs1)
+        for (int64_t hs0 = Ey * hs1; hs0 < Ey * hs1 + 32; ++hs0) {
+          const int bytes = layout_bytes(sx, hs0, false);
+          if (bytes > limit) continue;
+          const auto sc = bank_spread(hs0, hs1);
+          if (sc.first > best.first || (sc.first == best.first && sc.second < best.second) ||
+              (sc == best && bytes < bbytes)) {
+            best = sc;
+            pick = {hs0, hs1};
+            bbytes = bytes;
+          }
+        }
+      cache[key] = pick;
+    }
+  }
+  j.hs[0] = pick.first;
+  j.hs[1] = pick.second;
+  j.hist_bytes = layout_bytes(sx, pick.first, false);
 }
 
 void plan(dses_ctx* c, Job& j) {

@@ -144,25 +144,28 @@ cudaError_t launch_vote(const PassLaunch& L, int points_per_thread, int sparse, 
 // Kernel 2: inlier count M at t* and, on the fused path, grid score + argmin.
 cudaError_t launch_count(const PassLaunch& L, int total_rot, cudaStream_t s);
 int pass_smem_bytes(int hist_bytes, int src_bytes);
-// Staging bytes for sources of up to n_src points next to a histogram of
-// hist_bytes: enough for all of them (32 bytes each) when shared memory
-// allows, at least kSrcChunk * 16.
-int pass_src_bytes(int hist_bytes, int n_src);
 // Shared memory of a rotation-pass launch past the histogram: the source
-// staging and, for a culled launch, the bounds of every block of 32 staged
-// sources (32 bytes each, sized for the plain layout's largest chunk), and for
-// a paired culled launch the warps' kept-source lists, and for a culled launch
-// with block bounds the order of its items, all taken from the staging room.
+// staging (32 bytes per source of the largest problem, as far as shared memory
+// allows), for a culled launch with block bounds the bounds of every block of
+// 32 staged sources (32 bytes each, sized for the plain layout's largest
+// chunk) and the order of its items, and for a paired culled launch the warps'
+// kept-source lists.
 inline void pass_staging(int hist_bytes, int n_src_max, bool culled, bool paired, int* src_bytes, int* blk_bytes,
                          int* list_bytes, int* order_bytes) {
-  int src = pass_src_bytes(hist_bytes, n_src_max);
   const int list = paired ? kPairedListBytes : 0;
   const int order = culled ? kItemOrderCap * 4 : 0;
-  src = (src - list - order) & ~31;
+  // what shared memory leaves for the staging (and the block bounds): at
+  // least kSrcChunk * 16 - list - order, since the histogram keeps to
+  // kHistBudget
+  const int avail = (kMaxSmem - kPassStaticSmem - hist_bytes - list - order) & ~31;
+  int src = (int)std::min<long long>(32LL * n_src_max, avail);
   int blk = 0;
   if (culled) {
     blk = ((src / 16 + 31) / 32) * 32;
-    src = (src - blk) & ~31;
+    if (src + blk > avail) {
+      src = ((avail - 32) / 17 * 16) & ~31;
+      blk = ((src / 16 + 31) / 32) * 32;
+    }
   }
   *src_bytes = src;
   *blk_bytes = blk;

@@ -635,6 +635,11 @@ __device__ __forceinline__ void vote_list(const uint32_t* __restrict__ lst, int 
     vote_staged<G, U16, CUBE>(lst[k], yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy);
 }
 
+// Shared address of staged source i's offsets in the tile layout.
+__device__ __forceinline__ uint32_t tile_entry(uint32_t tbase, int i) {
+  return tbase + (uint32_t)((i / kTileSources) * kTileBytes + 8 * (i % kTileSources));
+}
+
 // Appends the lanes whose flag is set to a warp's list (each at its rank in
 // the ballot); n is the list's length, the same in every lane.
 __device__ __forceinline__ void list_push(uint32_t* __restrict__ lst, int& n, bool flag, uint32_t entry,
@@ -660,7 +665,7 @@ __device__ __forceinline__ void list_push(uint32_t* __restrict__ lst, int& n, bo
 // the end of the item. A cubic padded box takes the three-input-max box test
 // (CUBE, an instantiation of its own: with the choice made per step the loop
 // ran 11% slower).
-template <int P, bool U16, bool CUBE>
+template <int P, bool U16, bool CUBE, bool DIRECT>
 __device__ __forceinline__ void vote_centred_paired(const PassDesc& d, const float* __restrict__ srct, int nsrc,
                                                     unsigned SX, uint32_t hist_base, int* item_ctr, int lane,
                                                     float* __restrict__ thr, uint32_t sink,
@@ -687,6 +692,7 @@ __device__ __forceinline__ void vote_centred_paired(const PassDesc& d, const flo
   const uint32_t adummy = sink + 4u * (uint32_t)lane;
   const uint32_t lt = (1u << lane) - 1u;
   const uint32_t tbase = (uint32_t)__cvta_generic_to_shared(srct);
+
   for (int k = next_item(item_ctr, lane); k < n_items; k = next_item(item_ctr, lane)) {
     const int it = ord ? (int)ord[k] : k;  // largest items first when ordered
     const int tc = it % n_tchunks, sg = it / n_tchunks;
@@ -730,33 +736,58 @@ __device__ __forceinline__ void vote_centred_paired(const PassDesc& d, const flo
           const float2 tb = *reinterpret_cast<const float2*>(thr + 8 * q + 4);
           keep[q] = valid && cx >= ta.x && cx <= ta.y && cy >= ta.z && cy <= ta.w && cz >= tb.x && cz <= tb.y;
         }
-        const uint32_t entry = tbase + 4u * (uint32_t)o;
-        if constexpr (Q == 2) {
-          list_push(lst, cnt[0], keep[0] && !keep[1], entry, lt);
-          list_push(lst + kPairedListCap, cnt[1], keep[1] && !keep[0], entry, lt);
-          list_push(lst + 2 * kPairedListCap, cnt[2], keep[0] && keep[1], entry, lt);
-        } else {
-          list_push(lst, cnt[0], keep[0], entry, lt);
-        }
-        __syncwarp();
-        // a list holds at most kPairedListFlush - 1 + 32 entries before its vote
-        if (cnt[0] >= kPairedListFlush) {
-          vote_list<1, U16, CUBE>(lst, cnt[0], yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy);
-          cnt[0] = 0;
-          __syncwarp();  // read before the next block rewrites the list
-        }
-        if constexpr (Q == 2) {
-          if (cnt[1] >= kPairedListFlush) {
-            vote_list<1, U16, CUBE>(lst + kPairedListCap, cnt[1], yx + 1, yy + 1, yz + 1, inv2, mx2, my2, mz2, Sx, Sy,
-                                    abase, hx, hy, hz, adummy);
-            cnt[1] = 0;
-            __syncwarp();
+        if constexpr (DIRECT) {
+          // few sources per item: vote this block's kept sources at once
+          const uint32_t k0 = __ballot_sync(0xffffffffu, keep[0]);
+          const uint32_t k1 = Q == 2 ? __ballot_sync(0xffffffffu, keep[Q - 1]) : 0u;
+          uint32_t mb = k0 & k1, m0 = k0 & ~k1, m1 = k1 & ~k0;
+          while (mb) {
+            const int jj = s0 + __ffs(mb) - 1;
+            mb &= mb - 1;
+            vote_staged<Q, U16, CUBE>(tile_entry(tbase, jj), yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy,
+                                      hz, adummy);
           }
-          if (cnt[2] >= kPairedListFlush) {
-            vote_list<2, U16, CUBE>(lst + 2 * kPairedListCap, cnt[2], yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase,
-                                    hx, hy, hz, adummy);
-            cnt[2] = 0;
-            __syncwarp();
+          while (m0) {
+            const int jj = s0 + __ffs(m0) - 1;
+            m0 &= m0 - 1;
+            vote_staged<1, U16, CUBE>(tile_entry(tbase, jj), yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy,
+                                      hz, adummy);
+          }
+          while (m1) {
+            const int jj = s0 + __ffs(m1) - 1;
+            m1 &= m1 - 1;
+            vote_staged<1, U16, CUBE>(tile_entry(tbase, jj), yx + Q - 1, yy + Q - 1, yz + Q - 1, inv2, mx2, my2, mz2,
+                                      Sx, Sy, abase, hx, hy, hz, adummy);
+          }
+        } else {
+          const uint32_t entry = tbase + 4u * (uint32_t)o;
+          if constexpr (Q == 2) {
+            list_push(lst, cnt[0], keep[0] && !keep[1], entry, lt);
+            list_push(lst + kPairedListCap, cnt[1], keep[1] && !keep[0], entry, lt);
+            list_push(lst + 2 * kPairedListCap, cnt[2], keep[0] && keep[1], entry, lt);
+          } else {
+            list_push(lst, cnt[0], keep[0], entry, lt);
+          }
+          __syncwarp();
+          // a list holds at most kPairedListFlush - 1 + 32 entries before its vote
+          if (cnt[0] >= kPairedListFlush) {
+            vote_list<1, U16, CUBE>(lst, cnt[0], yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy);
+            cnt[0] = 0;
+            __syncwarp();  // read before the next block rewrites the list
+          }
+          if constexpr (Q == 2) {
+            if (cnt[1] >= kPairedListFlush) {
+              vote_list<1, U16, CUBE>(lst + kPairedListCap, cnt[1], yx + 1, yy + 1, yz + 1, inv2, mx2, my2, mz2, Sx, Sy,
+                                      abase, hx, hy, hz, adummy);
+              cnt[1] = 0;
+              __syncwarp();
+            }
+            if (cnt[2] >= kPairedListFlush) {
+              vote_list<2, U16, CUBE>(lst + 2 * kPairedListCap, cnt[2], yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase,
+                                      hx, hy, hz, adummy);
+              cnt[2] = 0;
+              __syncwarp();
+            }
           }
         }
       }
@@ -1000,17 +1031,22 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
             uint32_t* lst = reinterpret_cast<uint32_t*>(smem + L.hist_bytes + L.src_bytes + L.blk_bytes) +
                             warp * 3 * kPairedListCap;
             const float* srct = reinterpret_cast<const float*>(srcc);
+            // items of a few sources each (below the 256 where block bounds
+            // pay) vote each block's kept sources directly: gathering them in
+            // lists and voting at the end of the item costs more than it saves
+            // there (ModelNet-shaped +-0.2 box: 31%)
+            const bool direct = (c1 - c0 + d.n_sgroups - 1) / d.n_sgroups < 256;
+#define DSES_PAIRED(U, C, D)                                                                                   \
+  vote_centred_paired<PS, U, C, D>(d, srct, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink, blkp, lst, ord)
             if (d.hist_u16 && cube)
-              vote_centred_paired<PS, true, true>(d, srct, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink, blkp, lst, ord);
+              direct ? DSES_PAIRED(true, true, true) : DSES_PAIRED(true, true, false);
             else if (d.hist_u16)
-              vote_centred_paired<PS, true, false>(d, srct, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink,
-                                                   blkp, lst, ord);
+              direct ? DSES_PAIRED(true, false, true) : DSES_PAIRED(true, false, false);
             else if (cube)
-              vote_centred_paired<PS, false, true>(d, srct, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink,
-                                                   blkp, lst, ord);
+              direct ? DSES_PAIRED(false, true, true) : DSES_PAIRED(false, true, false);
             else
-              vote_centred_paired<PS, false, false>(d, srct, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink,
-                                                    blkp, lst, ord);
+              direct ? DSES_PAIRED(false, false, true) : DSES_PAIRED(false, false, false);
+#undef DSES_PAIRED
           } else if (SPARSE == 1) {  // ... and of this one 32-point culled problems only
             const bool cube = SX == (unsigned)d.E[1] && d.E[1] == d.E[2];
             float* thr = s_thr[SPARSE ? warp : 0];
@@ -1333,11 +1369,6 @@ cudaError_t launch_vote_padded(const PassLaunch& L, int points_per_thread, int s
 
 int pass_smem_bytes(int hist_bytes, int src_bytes) { return hist_bytes + src_bytes; }
 
-int pass_src_bytes(int hist_bytes, int n_src) {
-  const int room = (kMaxSmem - kPassStaticSmem - hist_bytes) & ~31;
-  const long long want = 32LL * n_src;
-  return (int)std::max<long long>(kSrcChunk * 16, std::min<long long>(want, room));
-}
 
 cudaError_t launch_vote(const PassLaunch& L, int points_per_thread, int sparse, int grid_ctas, cudaStream_t s) {
   return L.padded ? launch_vote_padded<true>(L, points_per_thread, sparse, grid_ctas, s)
