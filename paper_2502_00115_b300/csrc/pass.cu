@@ -482,7 +482,7 @@ __device__ __forceinline__ bool block_keeps(const float* __restrict__ b, const f
   for (int g = 0; g < G; ++g) {
     const float4 u0 = *reinterpret_cast<const float4*>(thr + 8 * g);
     const float2 u1 = *reinterpret_cast<const float2*>(thr + 8 * g + 4);
-    any |= b0.y >= u0.x && b0.x <= u0.y && b0.w >= u0.z && b0.z <= u0.w && b1.y >= u1.x && b1.x <= u1.y;
+    any |= (b0.y >= u0.x) & (b0.x <= u0.y) & (b0.w >= u0.z) & (b0.z <= u0.w) & (b1.y >= u1.x) & (b1.x <= u1.y);
   }
   return any;
 }
@@ -565,8 +565,8 @@ __device__ __forceinline__ void vote_centred_sparse(const PassDesc& d, const flo
         for (int p = 0; p < P; ++p) {
           const float4 ta = *reinterpret_cast<const float4*>(thr + 8 * p);
           const float2 tb = *reinterpret_cast<const float2*>(thr + 8 * p + 4);
-          const bool keep = valid && cm.x >= ta.x && cm.x <= ta.y && cm.y >= ta.z && cm.y <= ta.w && cm.z >= tb.x &&
-                            cm.z <= tb.y;
+          const bool keep = valid & (cm.x >= ta.x) & (cm.x <= ta.y) & (cm.y >= ta.z) & (cm.y <= ta.w) &
+                            (cm.z >= tb.x) & (cm.z <= tb.y);
           kmask[p] = __ballot_sync(0xffffffffu, keep);
         }
 #pragma unroll
@@ -734,7 +734,8 @@ __device__ __forceinline__ void vote_centred_paired(const PassDesc& d, const flo
         for (int q = 0; q < Q; ++q) {
           const float4 ta = *reinterpret_cast<const float4*>(thr + 8 * q);
           const float2 tb = *reinterpret_cast<const float2*>(thr + 8 * q + 4);
-          keep[q] = valid && cx >= ta.x && cx <= ta.y && cy >= ta.z && cy <= ta.w && cz >= tb.x && cz <= tb.y;
+          // bitwise (no short-circuit branches): one predicate chain per group
+          keep[q] = valid & (cx >= ta.x) & (cx <= ta.y) & (cy >= ta.z) & (cy <= ta.w) & (cz >= tb.x) & (cz <= tb.y);
         }
         if constexpr (DIRECT) {
           // few sources per item: vote this block's kept sources at once
@@ -770,23 +771,27 @@ __device__ __forceinline__ void vote_centred_paired(const PassDesc& d, const flo
           }
           __syncwarp();
           // a list holds at most kPairedListFlush - 1 + 32 entries before its vote
-          if (cnt[0] >= kPairedListFlush) {
-            vote_list<1, U16, CUBE>(lst, cnt[0], yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy);
-            cnt[0] = 0;
-            __syncwarp();  // read before the next block rewrites the list
-          }
-          if constexpr (Q == 2) {
-            if (cnt[1] >= kPairedListFlush) {
-              vote_list<1, U16, CUBE>(lst + kPairedListCap, cnt[1], yx + 1, yy + 1, yz + 1, inv2, mx2, my2, mz2, Sx, Sy,
-                                      abase, hx, hy, hz, adummy);
-              cnt[1] = 0;
-              __syncwarp();
+          bool full = cnt[0] >= kPairedListFlush;
+          if constexpr (Q == 2) full |= (cnt[1] >= kPairedListFlush) | (cnt[2] >= kPairedListFlush);
+          if (full) {
+            if (cnt[0] >= kPairedListFlush) {
+              vote_list<1, U16, CUBE>(lst, cnt[0], yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy);
+              cnt[0] = 0;
+              __syncwarp();  // read before the next block rewrites the list
             }
-            if (cnt[2] >= kPairedListFlush) {
-              vote_list<2, U16, CUBE>(lst + 2 * kPairedListCap, cnt[2], yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase,
-                                      hx, hy, hz, adummy);
-              cnt[2] = 0;
-              __syncwarp();
+            if constexpr (Q == 2) {
+              if (cnt[1] >= kPairedListFlush) {
+                vote_list<1, U16, CUBE>(lst + kPairedListCap, cnt[1], yx + 1, yy + 1, yz + 1, inv2, mx2, my2, mz2, Sx, Sy,
+                                        abase, hx, hy, hz, adummy);
+                cnt[1] = 0;
+                __syncwarp();
+              }
+              if (cnt[2] >= kPairedListFlush) {
+                vote_list<2, U16, CUBE>(lst + 2 * kPairedListCap, cnt[2], yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase,
+                                        hx, hy, hz, adummy);
+                cnt[2] = 0;
+                __syncwarp();
+              }
             }
           }
         }
