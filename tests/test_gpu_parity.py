@@ -440,6 +440,50 @@ def test_culled_modes_agree_on_robot_like(ctx):
     ctx.destroy_target(t)
 
 
+def test_paired_lists_with_16bit_counters_and_unordered_items(ctx):
+    # the paired vote's kept-source lists on the forms the robot-like line
+    # does not take: 16-bit counters (a 41^3 box forced to 16 bits, 300
+    # sources: one item walks them all, so the lists and the item order are
+    # used) and two targets per lane (one list per item) on a 40,000-point
+    # target whose 625 items exceed the items the kernel orders: every
+    # rotation's (k*, V, M) bit-identical to the dense vote
+    p = synth.robot_like_problem(0, hopf_n=2, refine_top_k=0)
+    n = 72 * 8
+    defaults = {k: ctx.get_option(k) for k in ("hist_mode", "points_per_thread", "vote_sparse")}
+    try:
+        t = ctx.create_target(p.Y, grid_cap=p.grid_cap)
+        gp = gpu_params(p, nn_mode="grid", refine_top_k=0, t_half=(0.06, 0.06, 0.06))
+        pb = ctx.problem(t, p.X[:300], capi.hopf_grid(2), gp)
+        ctx.set_option("hist_mode", 2)
+        ctx.set_option("vote_sparse", 3)
+        paired = ctx.debug(pb, n)
+        assert ctx.get_option("last_vote_paired") == 1
+        ctx.set_option("vote_sparse", 1)
+        dense = ctx.debug(pb, n)
+        assert ctx.get_option("last_vote_sparse") == 0
+        for a, b in zip(paired[:3], dense[:3]):
+            assert np.array_equal(a, b)
+        ctx.destroy_target(t)
+        for key, val in defaults.items():
+            ctx.set_option(key, val)
+
+        big = synth.robot_like_problem(1, m=40000, hopf_n=2, refine_top_k=0)
+        t = ctx.create_target(big.Y, grid_cap=big.grid_cap)
+        pb = ctx.problem(t, big.X, capi.hopf_grid(2), gpu_params(big, nn_mode="grid", refine_top_k=0))
+        ctx.set_option("points_per_thread", 2)
+        ctx.set_option("vote_sparse", 3)
+        paired = ctx.debug(pb, n)
+        assert ctx.get_option("last_vote_paired") == 1
+        ctx.set_option("vote_sparse", 1)
+        dense = ctx.debug(pb, n)
+        for a, b in zip(paired[:3], dense[:3]):
+            assert np.array_equal(a, b)
+        ctx.destroy_target(t)
+    finally:
+        for key, val in defaults.items():
+            ctx.set_option(key, val)
+
+
 # ---------------------------------------------------------------------------
 # batching, special cases, invariances
 
