@@ -604,9 +604,9 @@ bool culled_source_order(const Job& j);
 // Source chunks a launch of this job alone stages per rotation with a
 // histogram of hist_bytes (pass_staging and set_chunks of the launch).
 int source_chunks(const Job& j, int hist_bytes) {
-  int src = 0, blk = 0, list = 0, order = 0;
+  int src = 0, blk = 0, list = 0;
   const bool blocks = j.sparse && culled_source_order(j);
-  pass_staging(hist_bytes, j.N, blocks, j.sparse == 2, &src, &blk, &list, &order);
+  pass_staging(hist_bytes, j.N, blocks, j.sparse == 2, &src, &blk, &list);
   const int cap = j.sparse == 2 ? std::max(1, src / kTileBytes) * kTileSources : std::max(1, src / (j.sparse ? 16 : 32));
   return (j.N + cap - 1) / cap;
 }
@@ -1046,8 +1046,8 @@ void launch_pass(dses_ctx* c, const std::vector<PassPart>& parts, int P) {
   for (auto& d : descs) blocks &= block_bounds_pay(d);
   bool paired = false;
   for (auto& pp : parts) paired |= pp.job->sparse == 2;
-  int src_bytes = 0, blk_bytes = 0, list_bytes = 0, order_bytes = 0;
-  pass_staging(hist, max_n, blocks, paired, &src_bytes, &blk_bytes, &list_bytes, &order_bytes);
+  int src_bytes = 0, blk_bytes = 0, list_bytes = 0;
+  pass_staging(hist, max_n, blocks, paired, &src_bytes, &blk_bytes, &list_bytes);
   for (auto& d : descs) set_chunks(d, src_bytes);
   const size_t db = align256(sizeof(PassDesc) * descs.size()), pb = align256(sizeof(int) * prefix.size());
   DevMem m;
@@ -1071,7 +1071,6 @@ void launch_pass(dses_ctx* c, const std::vector<PassPart>& parts, int P) {
   L.src_bytes = src_bytes;
   L.blk_bytes = blk_bytes;
   L.list_bytes = list_bytes;
-  L.order_bytes = order_bytes;
   L.padded = 0;
   for (auto& pp : parts)
     for (int a = 0; a < 3; ++a) L.padded |= pp.job->Ep[a] != pp.job->E[a] ? 1 : 0;
@@ -1214,9 +1213,8 @@ float time_vote_trial(dses_ctx* c, Job& j, const float* rot, int64_t n, int P, i
   d[0].n_rot = (int)n;
   d[0].tile_rot = tile;
   d[0].votes_total = nullptr;  // a trial's votes are not the registration's
-  int src_bytes = 0, blk_bytes = 0, list_bytes = 0, order_bytes = 0;
-  pass_staging(j.hist_bytes, j.N, block_bounds_pay(d[0]), j.sparse == 2, &src_bytes, &blk_bytes, &list_bytes,
-               &order_bytes);
+  int src_bytes = 0, blk_bytes = 0, list_bytes = 0;
+  pass_staging(j.hist_bytes, j.N, block_bounds_pay(d[0]), j.sparse == 2, &src_bytes, &blk_bytes, &list_bytes);
   set_chunks(d[0], src_bytes);
   const int tiles = (int)((n + tile - 1) / tile);
   std::vector<int> tp{0, tiles}, rp{0, (int)n};
@@ -1239,7 +1237,6 @@ float time_vote_trial(dses_ctx* c, Job& j, const float* rot, int64_t n, int P, i
   L.src_bytes = src_bytes;
   L.blk_bytes = blk_bytes;
   L.list_bytes = list_bytes;
-  L.order_bytes = order_bytes;
   L.padded = 0;
   for (int a = 0; a < 3; ++a) L.padded |= j.Ep[a] != j.E[a] ? 1 : 0;
   cudaEvent_t e0, e1;

@@ -41,9 +41,6 @@ constexpr int kPassStaticSmem = 2048 + 32 * 8 * 8 * 4;
 constexpr int kPairedListCap = 48;
 constexpr int kPairedListFlush = 16;
 constexpr int kPairedListBytes = (kPassThreads / 32) * 3 * kPairedListCap * 4;
-// Culled vote: a source chunk's items are taken largest first (by their count
-// of 32-source blocks that can keep a group) when there are at most this many.
-constexpr int kItemOrderCap = 512;
 // Tiled staging of the paired culled vote: 8 sources per 192-byte tile, the
 // pairs (c_x, c_x) of its sources at bytes 0-63, (c_y, c_y) at 64-127 and
 // (c_z, c_z) at 128-191.
@@ -129,9 +126,6 @@ struct PassLaunch {
                            // offsets (8 floats each) after the staging; else 0
   int list_bytes;          // paired culled launches: the warps' lists of kept sources
                            // (kPairedListBytes) after the block bounds; else 0
-  int order_bytes;         // culled launches with block bounds: the order in which a
-                           // chunk's vote items are taken (kItemOrderCap words) after
-                           // the lists; else 0
   int padded;              // 1: some problem's layout is padded (E != Ev): the
                            // instance whose mode scan skips padding bins
 };
@@ -148,16 +142,13 @@ int pass_smem_bytes(int hist_bytes, int src_bytes);
 // staging (32 bytes per source of the largest problem, as far as shared memory
 // allows), for a culled launch with block bounds the bounds of every block of
 // 32 staged sources (32 bytes each, sized for the plain layout's largest
-// chunk) and the order of its items, and for a paired culled launch the warps'
-// kept-source lists.
+// chunk), and for a paired culled launch the warps' kept-source lists.
 inline void pass_staging(int hist_bytes, int n_src_max, bool culled, bool paired, int* src_bytes, int* blk_bytes,
-                         int* list_bytes, int* order_bytes) {
+                         int* list_bytes) {
   const int list = paired ? kPairedListBytes : 0;
-  const int order = culled ? kItemOrderCap * 4 : 0;
   // what shared memory leaves for the staging (and the block bounds): at
-  // least kSrcChunk * 16 - list - order, since the histogram keeps to
-  // kHistBudget
-  const int avail = (kMaxSmem - kPassStaticSmem - hist_bytes - list - order) & ~31;
+  // least kSrcChunk * 16 - list, since the histogram keeps to kHistBudget
+  const int avail = (kMaxSmem - kPassStaticSmem - hist_bytes - list) & ~31;
   int src = (int)std::min<long long>(32LL * n_src_max, avail);
   int blk = 0;
   if (culled) {
@@ -170,7 +161,6 @@ inline void pass_staging(int hist_bytes, int n_src_max, bool culled, bool paired
   *src_bytes = src;
   *blk_bytes = blk;
   *list_bytes = list;
-  *order_bytes = order;
 }
 // Equal chunks of the problem's sources that fit src_bytes of staging, plain,
 // packed and tiled (d.chunk).

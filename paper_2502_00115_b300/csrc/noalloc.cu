@@ -181,7 +181,6 @@ extern "C" dses_status dses_vote_static(int device, void* cuda_stream, const flo
     L.src_bytes = kSrcChunk * 16;
     L.blk_bytes = 0;
     L.list_bytes = 0;
-    L.order_bytes = 0;
     L.padded = 0;
     if (launch_vote(L, ppt, 0, std::max(1, std::min(sms, tiles)), s) != cudaSuccess) {
       cudaGetLastError();

@@ -487,27 +487,6 @@ __device__ __forceinline__ bool block_keeps(const float* __restrict__ b, const f
   return any;
 }
 
-// Blocks of 32 staged sources that can keep one of an item's G groups (the
-// test the culled paths make before walking a block): the work estimate by
-// which a chunk's items are ordered.
-template <int G>
-__device__ __forceinline__ int item_blocks(const PassDesc& d, int it, int nsrc, const float* __restrict__ blkp,
-                                           float* thr, int lane, float hx, float hy, float hz) {
-  const int tc = it % d.n_tchunks, sg = it / d.n_tchunks;
-  item_windows<G>(d, tc, lane, thr, hx, hy, hz, d.inv_delta);
-  __syncwarp();
-  const int spg = (nsrc + d.n_sgroups - 1) / d.n_sgroups;
-  const int i0 = sg * spg, i1 = min(i0 + spg, nsrc);
-  int n = 0;
-  for (int bb = i0 >> 5; bb < ((i1 + 31) >> 5); bb += 32) {
-    const int myb = bb + lane;
-    const bool rel = myb < ((i1 + 31) >> 5) && block_keeps<G>(blkp + 8 * myb, thr);
-    n += __popc(__ballot_sync(0xffffffffu, rel));
-  }
-  __syncwarp();
-  return n;
-}
-
 // Sparse centred path, for translation boxes small against the target: the
 // P x 32 targets of an item are P groups of 32 consecutive points (in the
 // vote's target order) with known bounding boxes. For each block of 32
@@ -521,8 +500,7 @@ template <int P, bool U16, bool CUBE>
 __device__ __forceinline__ void vote_centred_sparse(const PassDesc& d, const float4* __restrict__ srcc, int nsrc,
                                                     unsigned SX, uint32_t hist_base, int* item_ctr, int lane,
                                                     float* __restrict__ thr, uint32_t sink,
-                                                    const float* __restrict__ blkp,
-                                                    const uint32_t* __restrict__ ord) {
+                                                    const float* __restrict__ blkp) {
   const int n_tchunks = d.n_tchunks, n_sgroups = d.n_sgroups;
   const int n_items = n_tchunks * n_sgroups;
   const int spg = (nsrc + n_sgroups - 1) / n_sgroups;
@@ -538,8 +516,7 @@ __device__ __forceinline__ void vote_centred_sparse(const PassDesc& d, const flo
   const uint32_t abase32 = hist_base + (d.hist_lanes ? 4u * (uint32_t)lane : 0u) - unit * bias;
   const uint32_t abase16 = hist_base - 2u * bias;
   const uint32_t sinkl = sink + 4u * (uint32_t)lane;
-  for (int k = next_item(item_ctr, lane); k < n_items; k = next_item(item_ctr, lane)) {
-    const int it = ord ? (int)ord[k] : k;  // largest items first when ordered
+  for (int it = next_item(item_ctr, lane); it < n_items; it = next_item(item_ctr, lane)) {
     const int tc = it % n_tchunks, sg = it / n_tchunks;
     float ty[P][3];
     load_targets(d.Yv, d.M, tc * P * 32, lane, P, ty);
@@ -669,8 +646,7 @@ template <int P, bool U16, bool CUBE, bool DIRECT>
 __device__ __forceinline__ void vote_centred_paired(const PassDesc& d, const float* __restrict__ srct, int nsrc,
                                                     unsigned SX, uint32_t hist_base, int* item_ctr, int lane,
                                                     float* __restrict__ thr, uint32_t sink,
-                                                    const float* __restrict__ blkp, uint32_t* __restrict__ lst,
-                                                    const uint32_t* __restrict__ ord) {
+                                                    const float* __restrict__ blkp, uint32_t* __restrict__ lst) {
   static_assert(P == 2 || P == 4, "two targets of each of P / 2 groups per lane");
   constexpr int Q = P / 2;            // 64-point groups per item
   constexpr int NL = Q == 2 ? 3 : 1;  // lists: first group only, second only, both
@@ -693,8 +669,7 @@ __device__ __forceinline__ void vote_centred_paired(const PassDesc& d, const flo
   const uint32_t lt = (1u << lane) - 1u;
   const uint32_t tbase = (uint32_t)__cvta_generic_to_shared(srct);
 
-  for (int k = next_item(item_ctr, lane); k < n_items; k = next_item(item_ctr, lane)) {
-    const int it = ord ? (int)ord[k] : k;  // largest items first when ordered
+  for (int it = next_item(item_ctr, lane); it < n_items; it = next_item(item_ctr, lane)) {
     const int tc = it % n_tchunks, sg = it / n_tchunks;
     item_windows<Q>(d, tc, lane, thr, hx, hy, hz, inv);
     __syncwarp();
@@ -999,35 +974,6 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
             __syncthreads();
             blkp = blk;
           }
-          // culled launches: the chunk's items taken largest first (by their
-          // blocks that can keep a group), so that the warps finish the chunk
-          // together rather than waiting at its barrier for the last large item
-          const uint32_t* ord = nullptr;
-          if (SPARSE && d.sparse && blkp && L.order_bytes) {
-            const int n_items = d.n_tchunks * d.n_sgroups;
-            if (n_items <= L.order_bytes / 4 && n_items <= kPassThreads) {
-              uint32_t* o =
-                  reinterpret_cast<uint32_t*>(smem + L.hist_bytes + L.src_bytes + L.blk_bytes + L.list_bytes);
-              float* thr = s_thr[SPARSE ? warp : 0];
-              const float hx = 0.5f * (float)SX, hy = 0.5f * (float)Ey, hz = 0.5f * (float)Ez;
-              for (int it = warp; it < n_items; it += kPassThreads / 32) {
-                const int nb = SPARSE == 2 ? item_blocks<(P >= 4 ? 2 : 1)>(d, it, c1 - c0, blkp, thr, lane, hx, hy, hz)
-                                           : item_blocks<(P >= 4 ? 4 : P)>(d, it, c1 - c0, blkp, thr, lane, hx, hy, hz);
-                if (lane == 0) o[it] = ((uint32_t)nb << 16) | (uint32_t)it;
-              }
-              __syncthreads();
-              // rank of each item's (count, index) key, descending: a permutation
-              uint32_t key = 0, rank = 0;
-              if (tid < n_items) {
-                key = o[tid];
-                for (int j = 0; j < n_items; ++j) rank += o[j] > key ? 1u : 0u;
-              }
-              __syncthreads();
-              if (tid < n_items) o[rank] = key & 0xffffu;
-              __syncthreads();
-              ord = o;
-            }
-          }
           if (SPARSE == 2) {  // launches of this instance hold paired culled problems only (odd layouts)
             constexpr int PS = P >= 4 ? 4 : 2;  // paired instances are built for 2 and 4
             float* thr = s_thr[SPARSE ? warp : 0];
@@ -1042,7 +988,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
             // there (ModelNet-shaped +-0.2 box: 31%)
             const bool direct = (c1 - c0 + d.n_sgroups - 1) / d.n_sgroups < 256;
 #define DSES_PAIRED(U, C, D)                                                                                   \
-  vote_centred_paired<PS, U, C, D>(d, srct, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink, blkp, lst, ord)
+  vote_centred_paired<PS, U, C, D>(d, srct, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink, blkp, lst)
             if (d.hist_u16 && cube)
               direct ? DSES_PAIRED(true, true, true) : DSES_PAIRED(true, true, false);
             else if (d.hist_u16)
@@ -1058,16 +1004,16 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
             const uint32_t sink = (uint32_t)__cvta_generic_to_shared(s_sink);
             if (d.hist_u16 && cube)
               vote_centred_sparse<P, true, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink,
-                                                     blkp, ord);
+                                                     blkp);
             else if (d.hist_u16)
               vote_centred_sparse<P, true, false>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink,
-                                                     blkp, ord);
+                                                     blkp);
             else if (cube)
               vote_centred_sparse<P, false, true>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink,
-                                                     blkp, ord);
+                                                     blkp);
             else
               vote_centred_sparse<P, false, false>(d, srcc, c1 - c0, SX, hist_base, &s_vote_item, lane, thr, sink,
-                                                     blkp, ord);
+                                                     blkp);
           } else if (centred) {
             constexpr int PP = P >= 2 ? P : 2;  // the P = 1 instance never takes the packed path
             if (packed) {
@@ -1327,7 +1273,7 @@ __global__ void __launch_bounds__(256) count_kernel(PassLaunch L) {
 
 template <int P, int SPARSE, bool PADDED>
 cudaError_t launch_vote_p(const PassLaunch& L, int grid_ctas, cudaStream_t s) {
-  const int smem = pass_smem_bytes(L.hist_bytes, L.src_bytes) + L.blk_bytes + L.list_bytes + L.order_bytes;
+  const int smem = pass_smem_bytes(L.hist_bytes, L.src_bytes) + L.blk_bytes + L.list_bytes;
   // the opt-in is per device: a process may launch this instance on several GPUs
   static OptIn optin;
   int dev = 0;
