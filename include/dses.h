@@ -297,7 +297,8 @@ dses_status dses_exhaustive_search(dses_ctx* ctx, const dses_problem* problem, f
 /* Tuning and engine options (key = value). Keys:
  *   "hist_mode"            0 auto, 1 force 32-bit counters, 2 force packed 16-bit,
  *                          3 lane-private 32-bit counters (a copy of every bin
- *                          per lane, 128 bytes per bin; never chosen by 0)
+ *                          per lane, 128 bytes per bin; never chosen by 0; they
+ *                          take the scalar dense or the 32-point culled vote)
  *   "hist_budget_bytes"    shared-memory bytes for the vote histogram (slabs below it)
  *   "points_per_thread"    0 auto, or 1, 2, 4, 8 target points held per lane
  *                          (a problem on the culled vote uses 4 for 8)
@@ -323,7 +324,8 @@ dses_status dses_exhaustive_search(dses_ctx* ctx, const dses_problem* problem, f
  *   "vote_sparse"          0 auto, 1 dense vote, 2 cull (source, 32-point target
  *                          group) pairs outside the translation window (pays for
  *                          small boxes), 3 the same with 64-point groups voted as
- *                          packed pairs (pays when the window spans many groups)
+ *                          packed pairs (pays when the window spans many groups;
+ *                          with lane-private counters the 32-point form is used)
  *   "record_timing"        1: time every rotation pass with CUDA events on the
  *                          context's stream
  *   "target_order"         the vote's order of a target's points, fixed at
