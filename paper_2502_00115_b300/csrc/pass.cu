@@ -639,9 +639,10 @@ __device__ __forceinline__ void list_push(uint32_t* __restrict__ lst, int& n, bo
 // 8-byte loads). The kept sources of each 32-source block gather in the warp's
 // lists: a source kept by both of an item's groups is read once and votes
 // both; the lists are voted once one holds kPairedListFlush entries, and at
-// the end of the item. A cubic padded box takes the three-input-max box test
-// (CUBE, an instantiation of its own: with the choice made per step the loop
-// ran 11% slower).
+// the end of the item (DIRECT, for items of a few sources: each block's kept
+// sources are voted at once, without the lists). A cubic padded box takes the
+// three-input-max box test (CUBE, an instantiation of its own: with the
+// choice made per step the loop ran 11% slower).
 template <int P, bool U16, bool CUBE, bool DIRECT>
 __device__ __forceinline__ void vote_centred_paired(const PassDesc& d, const float* __restrict__ srct, int nsrc,
                                                     unsigned SX, uint32_t hist_base, int* item_ctr, int lane,
