@@ -35,6 +35,7 @@
 #include "dses.h"
 #include "exchange.h"
 #include "kernels.cuh"
+#include "strides.h"
 
 using namespace dses;
 
@@ -572,33 +573,6 @@ static void odd_slabs(int64_t Ex, int64_t max_planes, int64_t* sx, int64_t* n, i
   *Exp = Ex + (last % 2 == 0 ? 1 : 0);
 }
 
-// Shared-memory bytes of a histogram slab of sx x-planes at plane stride hs0.
-int layout_bytes(int64_t sx, int64_t hs0, bool u16) {
-  const int64_t bins = sx * hs0;
-  const int64_t hb = u16 ? ((bins + 1) / 2) * 4 : bins * 4;
-  return (int)((hb + 15) & ~15LL);
-}
-
-// How well strides (hs0, hs1) spread a lattice neighbourhood over the 32
-// shared-memory banks (32-bit counters): a warp's increments come from a
-// compact patch of targets, so its bins are near each other, and two bins
-// whose indices differ by a non-zero multiple of 32 share a bank. Returns the
-// squared length of the shortest offset |d|_inf <= 4 that lands in the same
-// bank (larger is better) and, second, how many offsets of squared length
-// <= 9 do (fewer is better).
-std::pair<int, int> bank_spread(int64_t hs0, int64_t hs1) {
-  int shortest = 1 << 30, close = 0;
-  for (int dx = -4; dx <= 4; ++dx)
-    for (int dy = -4; dy <= 4; ++dy)
-      for (int dz = -4; dz <= 4; ++dz) {
-        const int n2 = dx * dx + dy * dy + dz * dz;
-        if (n2 == 0 || (dx * hs0 + dy * hs1 + dz) % 32 != 0) continue;
-        shortest = std::min(shortest, n2);
-        close += n2 <= 9 ? 1 : 0;
-      }
-  return {shortest, close};
-}
-
 bool culled_source_order(const Job& j);
 
 // Source chunks a launch of this job alone stages per rotation with a
@@ -613,13 +587,12 @@ int source_chunks(const Job& j, int hist_bytes) {
 
 // Row and plane strides (in bins) of the 32-bit vote histogram, padded past
 // the extents where that spreads a lattice neighbourhood over more banks
-// (bank_spread) without costing a slab or a source chunk: the slab keeps its
-// x-planes within the budget and the launch stages the sources in as many
-// chunks as with the compact layout. Padding bins are never voted (a pair
-// inside the box has k_a < E_a) and read as zero by the mode scan. 16-bit
-// counters keep the compact layout: their conflicts come mostly from the two
-// halves of one word, which padding does not separate. The choice depends on
-// the extents and the byte limit only, and is cached.
+// (pick_strides, strides.h) without costing a slab or a source chunk: the
+// slab keeps its x-planes within the budget and the launch stages the sources
+// in as many chunks as with the compact layout. 16-bit counters keep the
+// compact layout: their conflicts come mostly from the two halves of one
+// word, which padding does not separate. The choice depends on the extents
+// and the byte limit only, and is cached.
 void spread_strides(Job& j, int64_t budget) {
   if (j.u16) return;
   const int64_t Ey = j.Ep[1], Ez = j.Ep[2], sx = j.slab_x;
@@ -645,21 +618,7 @@ void spread_strides(Job& j, int64_t budget) {
     if (it != cache.end()) {
       pick = it->second;
     } else {
-      auto best = bank_spread(j.hs[0], j.hs[1]);
-      pick = {j.hs[0], j.hs[1]};
-      int bbytes = j.hist_bytes;
-      for (int64_t hs1 = Ez; hs1 < Ez + 8; ++hs1)
-        for (int64_t hs0 = Ey * hs1; hs0 < Ey * hs1 + 32; ++hs0) {
-          const int bytes = layout_bytes(sx, hs0, false);
-          if (bytes > limit) continue;
-          const auto sc = bank_spread(hs0, hs1);
-          if (sc.first > best.first || (sc.first == best.first && sc.second < best.second) ||
-              (sc == best && bytes < bbytes)) {
-            best = sc;
-            pick = {hs0, hs1};
-            bbytes = bytes;
-          }
-        }
+      pick = pick_strides(Ey, Ez, sx, limit);
       cache[key] = pick;
     }
   }
