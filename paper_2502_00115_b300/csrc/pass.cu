@@ -270,11 +270,13 @@ __device__ __forceinline__ void vote_centred(const PassDesc& d, const float4* __
 // The three steps shared by every form: w = y / delta + c, the magic-number
 // rounding of w and the lattice index t of both pairs, with the x axis on
 // packed FP32 pairs (fma.rn.f32x2 / add.rn.f32x2) and the y and z axes either
-// packed too (DSES_VOTE2_HEAD_P: fewest instructions) or as scalar FP32 on
-// each half (DSES_VOTE2_HEAD_S: the packed operations issue to the FMA-heavy
-// pipe only, scalar ones to either FMA pipe; the culled vote, whose loop is
-// bound by that pipe, ran 7% faster with them; the dense 16-bit vote, bound
-// by issue, 6% slower). Either form rounds each value once, identically. Box
+// packed too (DSES_VOTE2_HEAD_P: fewest instructions), or z (DSES_VOTE2_HEAD_Z)
+// or y and z (DSES_VOTE2_HEAD_S) as scalar FP32 on each half: the packed
+// operations issue to the FMA-heavy pipe only, scalar ones to either FMA pipe.
+// Measured: the culled vote's list loop fastest with HEAD_Z (1.4% ahead of
+// HEAD_S, 5% ahead of HEAD_P), its direct form with HEAD_S (2% ahead of
+// HEAD_Z), the dense 16-bit vote with HEAD_P (HEAD_S 6% slower). Every form
+// rounds each value once, identically. Box
 // test: |w_a| < h_a on every axis, either per axis (three chained compares) or,
 // when the padded box is a cube, as max(|w_x|, |w_y|, |w_z|) < h (one
 // three-input max and one compare).
@@ -301,6 +303,18 @@ __device__ __forceinline__ void vote_centred(const PassDesc& d, const float4* __
   "add.rn.f32 gz0, wz0, mz0;\n\tadd.rn.f32 gz1, wz1, mz1;\n\t"                                   \
   "mov.b64 wy, {wy0, wy1};\n\tmov.b64 wz, {wz0, wz1};\n\t"                                       \
   "mov.b64 {bx0, bx1}, fx;\n\tmov.b32 by0, gy0;\n\tmov.b32 by1, gy1;\n\t"                        \
+  "mov.b32 bz0, gz0;\n\tmov.b32 bz1, gz1;\n\t"
+#define DSES_VOTE2_HEAD_Z                                                                        \
+  DSES_VOTE2_DECL                                                                                \
+  ".reg .f32 j0, j1, qz0, qz1, cz0, cz1, mz0, mz1, wz0, wz1, gz0, gz1;\n\t"                      \
+  "fma.rn.f32x2 wx, %0, %3, %4;\n\tfma.rn.f32x2 wy, %1, %3, %5;\n\t"                             \
+  "add.rn.f32x2 fx, wx, %7;\n\tadd.rn.f32x2 fy, wy, %8;\n\t"                                     \
+  "mov.b64 {j0, j1}, %3;\n\t"                                                                    \
+  "mov.b64 {qz0, qz1}, %2;\n\tmov.b64 {cz0, cz1}, %6;\n\tmov.b64 {mz0, mz1}, %9;\n\t"            \
+  "fma.rn.f32 wz0, qz0, j0, cz0;\n\tfma.rn.f32 wz1, qz1, j1, cz1;\n\t"                           \
+  "add.rn.f32 gz0, wz0, mz0;\n\tadd.rn.f32 gz1, wz1, mz1;\n\t"                                   \
+  "mov.b64 wz, {wz0, wz1};\n\t"                                                                  \
+  "mov.b64 {bx0, bx1}, fx;\n\tmov.b64 {by0, by1}, fy;\n\t"                                       \
   "mov.b32 bz0, gz0;\n\tmov.b32 bz1, gz1;\n\t"
 // 16-bit counters: word t >> 1 (address = base + 4 word), half t & 1: the
 // increment 1 << 16 (t & 1) is a funnel shift by (t << 4) mod 32; the
@@ -338,9 +352,10 @@ __device__ __forceinline__ void vote_centred(const PassDesc& d, const float4* __
 
 // Two (source, target) pairs as packed FP32 pairs: lattice index, box test and
 // one unconditional shared add per pair (shared 16- or 32-bit counters; the
-// lane-private layout takes the scalar path). SCALAR: the y and z axes in
-// scalar FP32 (DSES_VOTE2_HEAD_S), else packed (DSES_VOTE2_HEAD_P).
-template <bool U16, bool CUBE, bool SCALAR>
+// lane-private layout takes the scalar path). FORM: 0 every axis packed
+// (DSES_VOTE2_HEAD_P), 1 z scalar (DSES_VOTE2_HEAD_Z), 2 y and z scalar
+// (DSES_VOTE2_HEAD_S).
+template <bool U16, bool CUBE, int FORM>
 __device__ __forceinline__ void vote_two_pairs(uint64_t yx, uint64_t yy, uint64_t yz, uint64_t inv2, uint64_t cx2,
                                                uint64_t cy2, uint64_t cz2, uint64_t mx2, uint64_t my2, uint64_t mz2,
                                                uint32_t Sx, uint32_t Sy, uint32_t abase, float hx, float hy,
@@ -358,8 +373,10 @@ __device__ __forceinline__ void vote_two_pairs(uint64_t yx, uint64_t yy, uint64_
     asm volatile(HEAD DSES_VOTE2_ADDR32 DSES_VOTE2_ABS DSES_VOTE2_TEST_CUBE DSES_VOTE2_RED32 DSES_VOTE2_ARGS);   \
   else                                                                                                           \
     asm volatile(HEAD DSES_VOTE2_ADDR32 DSES_VOTE2_ABS DSES_VOTE2_TEST_AXES DSES_VOTE2_RED32 DSES_VOTE2_ARGS);
-  if (SCALAR) {
+  if (FORM == 2) {
     DSES_VOTE2_FORMS(DSES_VOTE2_HEAD_S)
+  } else if (FORM == 1) {
+    DSES_VOTE2_FORMS(DSES_VOTE2_HEAD_Z)
   } else {
     DSES_VOTE2_FORMS(DSES_VOTE2_HEAD_P)
   }
@@ -386,8 +403,8 @@ __device__ __forceinline__ void vote_sources_x2(const float4* __restrict__ srcd,
     const uint64_t cx2 = pack2(ca.x, ca.y), cy2 = pack2(ca.z, ca.w), cz2 = pack2(cb.x, cb.y);
 #pragma unroll
     for (int q = 0; q < Q; ++q)
-      vote_two_pairs<U16, CUBE, !U16>(yx[q], yy[q], yz[q], inv2, cx2, cy2, cz2, mx2, my2, mz2, Sx, Sy, abase, hx, hy,
-                                      hz, adummy);
+      vote_two_pairs<U16, CUBE, U16 ? 0 : 2>(yx[q], yy[q], yz[q], inv2, cx2, cy2, cz2, mx2, my2, mz2, Sx, Sy, abase,
+                                             hx, hy, hz, adummy);
   }
 }
 
@@ -576,7 +593,7 @@ __device__ __forceinline__ void vote_centred_sparse(const PassDesc& d, const flo
 // One kept source against a lane's target pair of each of G groups: its
 // staged pairs (c_x, c_x), (c_y, c_y), (c_z, c_z) read from the tile layout at
 // shared address a (a + 64, a + 128).
-template <int G, bool U16, bool CUBE>
+template <int G, bool U16, bool CUBE, int FORM>
 __device__ __forceinline__ void vote_staged(uint32_t a, const uint64_t* yx, const uint64_t* yy, const uint64_t* yz,
                                             uint64_t inv2, uint64_t mx2, uint64_t my2, uint64_t mz2, uint32_t Sx,
                                             uint32_t Sy, uint32_t abase, float hx, float hy, float hz,
@@ -587,12 +604,13 @@ __device__ __forceinline__ void vote_staged(uint32_t a, const uint64_t* yx, cons
       : "r"(a));
 #pragma unroll
   for (int g = 0; g < G; ++g)
-    vote_two_pairs<U16, CUBE, true>(yx[g], yy[g], yz[g], inv2, cx2, cy2, cz2, mx2, my2, mz2, Sx, Sy, abase, hx, hy,
+    vote_two_pairs<U16, CUBE, FORM>(yx[g], yy[g], yz[g], inv2, cx2, cy2, cz2, mx2, my2, mz2, Sx, Sy, abase, hx, hy,
                                     hz, adummy);
 }
 
 // The n kept sources of a list against the lane's target pairs of G groups,
-// four per iteration (the list is 16-byte aligned).
+// four per iteration (the list is 16-byte aligned; z coordinates in scalar
+// FP32, DSES_VOTE2_HEAD_Z).
 template <int G, bool U16, bool CUBE>
 __device__ __forceinline__ void vote_list(const uint32_t* __restrict__ lst, int n, const uint64_t* yx,
                                           const uint64_t* yy, const uint64_t* yz, uint64_t inv2, uint64_t mx2,
@@ -602,14 +620,14 @@ __device__ __forceinline__ void vote_list(const uint32_t* __restrict__ lst, int 
 #pragma unroll 1
   for (; k + 4 <= n; k += 4) {
     const uint4 a = *reinterpret_cast<const uint4*>(lst + k);
-    vote_staged<G, U16, CUBE>(a.x, yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy);
-    vote_staged<G, U16, CUBE>(a.y, yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy);
-    vote_staged<G, U16, CUBE>(a.z, yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy);
-    vote_staged<G, U16, CUBE>(a.w, yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy);
+    vote_staged<G, U16, CUBE, 1>(a.x, yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy);
+    vote_staged<G, U16, CUBE, 1>(a.y, yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy);
+    vote_staged<G, U16, CUBE, 1>(a.z, yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy);
+    vote_staged<G, U16, CUBE, 1>(a.w, yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy);
   }
 #pragma unroll 1
   for (; k < n; ++k)
-    vote_staged<G, U16, CUBE>(lst[k], yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy);
+    vote_staged<G, U16, CUBE, 1>(lst[k], yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy, hz, adummy);
 }
 
 // Shared address of staged source i's offsets in the tile layout.
@@ -721,19 +739,19 @@ __device__ __forceinline__ void vote_centred_paired(const PassDesc& d, const flo
           while (mb) {
             const int jj = s0 + __ffs(mb) - 1;
             mb &= mb - 1;
-            vote_staged<Q, U16, CUBE>(tile_entry(tbase, jj), yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy,
+            vote_staged<Q, U16, CUBE, 2>(tile_entry(tbase, jj), yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy,
                                       hz, adummy);
           }
           while (m0) {
             const int jj = s0 + __ffs(m0) - 1;
             m0 &= m0 - 1;
-            vote_staged<1, U16, CUBE>(tile_entry(tbase, jj), yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy,
+            vote_staged<1, U16, CUBE, 2>(tile_entry(tbase, jj), yx, yy, yz, inv2, mx2, my2, mz2, Sx, Sy, abase, hx, hy,
                                       hz, adummy);
           }
           while (m1) {
             const int jj = s0 + __ffs(m1) - 1;
             m1 &= m1 - 1;
-            vote_staged<1, U16, CUBE>(tile_entry(tbase, jj), yx + Q - 1, yy + Q - 1, yz + Q - 1, inv2, mx2, my2, mz2,
+            vote_staged<1, U16, CUBE, 2>(tile_entry(tbase, jj), yx + Q - 1, yy + Q - 1, yz + Q - 1, inv2, mx2, my2, mz2,
                                       Sx, Sy, abase, hx, hy, hz, adummy);
           }
         } else {
