@@ -37,9 +37,14 @@ constexpr int kMaxSmem = 232448;
 constexpr int kPassStaticSmem = 2048 + 32 * 8 * 8 * 4;
 // Paired culled vote: per warp, three lists of kPairedListCap shared addresses
 // of kept sources' staged offsets (sources kept by the item's first group only,
-// by its second only, by both), flushed at kPairedListFlush entries.
-constexpr int kPairedListCap = 48;
-constexpr int kPairedListFlush = 16;
+// by its second only, by both), flushed at kPairedListFlush entries (a block
+// of 32 sources adds at most 32, so the cap is the flush count + 32). Measured
+// on the robot-like vote at N_side 12: flushing at 16 / 24 / 32 / 40 entries
+// ran 393.9 / 392.0 / 390.6 / 390.1 ms (at 8: 397.1 against 394.4 at 16 in
+// another run); 32 keeps at least 8 KB of staging beside a histogram at
+// kHistBudget.
+constexpr int kPairedListFlush = 32;
+constexpr int kPairedListCap = kPairedListFlush + 32;
 constexpr int kPairedListBytes = (kPassThreads / 32) * 3 * kPairedListCap * 4;
 // Tiled staging of the paired culled vote: 8 sources per 192-byte tile, the
 // pairs (c_x, c_x) of its sources at bytes 0-63, (c_y, c_y) at 64-127 and
