@@ -144,17 +144,23 @@ cudaError_t launch_vote(const PassLaunch& L, int points_per_thread, int sparse, 
 cudaError_t launch_count(const PassLaunch& L, int total_rot, cudaStream_t s);
 int pass_smem_bytes(int hist_bytes, int src_bytes);
 // Shared memory of a rotation-pass launch past the histogram: the source
-// staging (32 bytes per source of the largest problem, as far as shared memory
-// allows), for a culled launch with block bounds the bounds of every block of
-// 32 staged sources (32 bytes each, sized for the plain layout's largest
-// chunk), and for a paired culled launch the warps' kept-source lists.
+// staging (32 bytes per source of the largest problem, and for a paired
+// launch at least its whole 192-byte tiles, as far as shared memory allows),
+// for a culled launch with block bounds the bounds of every block of 32
+// staged sources (32 bytes each, sized for the plain layout's largest chunk),
+// and for a paired culled launch the warps' kept-source lists.
 inline void pass_staging(int hist_bytes, int n_src_max, bool culled, bool paired, int* src_bytes, int* blk_bytes,
                          int* list_bytes) {
   const int list = paired ? kPairedListBytes : 0;
   // what shared memory leaves for the staging (and the block bounds): at
   // least kSrcChunk * 16 - list, since the histogram keeps to kHistBudget
   const int avail = (kMaxSmem - kPassStaticSmem - hist_bytes - list) & ~31;
-  int src = (int)std::min<long long>(32LL * n_src_max, avail);
+  // a tile holds 8 sources in 192 bytes, 24 per source, but a partial tile
+  // of r sources still spans 128 + 8 r bytes (its z pairs start at byte
+  // 128): more than 32 per source for 1-5, 9 and 10 sources
+  long long need = 32LL * n_src_max;
+  if (paired) need = std::max<long long>(need, (long long)((n_src_max + kTileSources - 1) / kTileSources) * kTileBytes);
+  int src = (int)std::min<long long>(need, avail);
   int blk = 0;
   if (culled) {
     blk = ((src / 16 + 31) / 32) * 32;

@@ -484,6 +484,29 @@ def test_paired_lists_with_16bit_counters_and_unordered_items(ctx):
             ctx.set_option(key, val)
 
 
+def test_paired_vote_with_a_few_sources(ctx):
+    # 1 to 17 sources on the paired path (forced): a partial tile of the
+    # staged offsets is wider than 32 bytes per source, so the staging must be
+    # sized by tiles; every rotation's (k*, V, M) bit-identical to the dense vote
+    p = synth.robot_like_problem(0, hopf_n=2, refine_top_k=0)
+    n = 72 * 8
+    t = ctx.create_target(p.Y, grid_cap=p.grid_cap)
+    try:
+        for ns in (1, 2, 3, 5, 9, 10, 11, 17):
+            pb = ctx.problem(t, p.X[:ns], capi.hopf_grid(2), gpu_params(p, nn_mode="grid", refine_top_k=0))
+            ctx.set_option("vote_sparse", 3)
+            paired = ctx.debug(pb, n)
+            assert ctx.get_option("last_vote_paired") == 1
+            ctx.set_option("vote_sparse", 1)
+            dense = ctx.debug(pb, n)
+            assert ctx.get_option("last_vote_sparse") == 0
+            for a, b in zip(paired[:3], dense[:3]):
+                assert np.array_equal(a, b), ns
+    finally:
+        ctx.set_option("vote_sparse", 0)
+        ctx.destroy_target(t)
+
+
 # ---------------------------------------------------------------------------
 # batching, special cases, invariances
 
