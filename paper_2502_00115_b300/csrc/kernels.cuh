@@ -51,6 +51,12 @@ constexpr int kPairedListBytes = (kPassThreads / 32) * 3 * kPairedListCap * 4;
 // (c_z, c_z) at 128-191.
 constexpr int kTileSources = 8;
 constexpr int kTileBytes = 192;
+static_assert(kTileBytes == 3 * 8 * kTileSources, "one 8-byte pair per axis and source");
+// the list loop reads four entries as one 16-byte load from a list start,
+// and a block of 32 sources may add 32 entries to a list holding up to
+// kPairedListFlush - 1
+static_assert(kPairedListCap % 4 == 0, "16-byte aligned lists");
+static_assert(kPairedListCap >= kPairedListFlush - 1 + 32, "room for a block's pushes before the flush");
 // Histogram budget: what is left after the source chunk and static storage.
 constexpr int kHistBudget = kMaxSmem - kSrcChunk * 16 - kPassStaticSmem;
 
