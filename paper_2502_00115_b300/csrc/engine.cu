@@ -619,6 +619,9 @@ void spread_strides(Job& j, int64_t budget) {
       pick = it->second;
     } else {
       pick = pick_strides(Ey, Ez, sx, limit);
+      // a process that plans many box shapes keeps at most 4,096 choices
+      // (~0.3 ms of host search each to redo)
+      if (cache.size() >= 4096) cache.clear();
       cache[key] = pick;
     }
   }
