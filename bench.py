@@ -102,11 +102,13 @@ class ClockSampler:
     def __init__(self, device):
         self.device = device
         self.proc = None
-        self.path = tempfile.mktemp(prefix="clocks", suffix=".csv")
+        self.f = None
+        self.path = None
 
     def start(self):
         try:
-            self.f = open(self.path, "w")
+            self.f = tempfile.NamedTemporaryFile("w", prefix="clocks", suffix=".csv", delete=False)
+            self.path = self.f.name
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
@@ -115,6 +117,10 @@ class ClockSampler:
 
     def stop(self):
         if not self.proc:
+            if self.f is not None:
+                self.f.close()
+                os.unlink(self.path)
+                self.f = None
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
         try:
