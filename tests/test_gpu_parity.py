@@ -440,13 +440,13 @@ def test_culled_modes_agree_on_robot_like(ctx):
     ctx.destroy_target(t)
 
 
-def test_paired_lists_with_16bit_counters_and_unordered_items(ctx):
+def test_paired_lists_with_16bit_counters_and_many_items(ctx):
     # the paired vote's kept-source lists on the forms the robot-like line
     # does not take: 16-bit counters (a 41^3 box forced to 16 bits, 300
-    # sources: one item walks them all, so the lists and the item order are
-    # used) and two targets per lane (one list per item) on a 40,000-point
-    # target whose 625 items exceed the items the kernel orders: every
-    # rotation's (k*, V, M) bit-identical to the dense vote
+    # sources: one item walks them all, so the lists are used) and two
+    # targets per lane (one list per item) on a 40,000-point target (625
+    # items per rotation): every rotation's (k*, V, M) bit-identical to the
+    # dense vote
     p = synth.robot_like_problem(0, hopf_n=2, refine_top_k=0)
     n = 72 * 8
     defaults = {k: ctx.get_option(k) for k in ("hist_mode", "points_per_thread", "vote_sparse")}
