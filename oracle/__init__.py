@@ -73,8 +73,12 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            lib = ctypes.CDLL(_LIB)
+            # test hook: DSES_ORACLE_LIB names another build of oracle.cpp (the
+            # mutation test loads copies with a planted mistake)
+            alt = os.environ.get("DSES_ORACLE_LIB")
+            if not alt:
+                build()
+            lib = ctypes.CDLL(alt or _LIB)
             P = ctypes.POINTER
             d, i64, i32 = ctypes.c_double, ctypes.c_int64, ctypes.c_int
             pd, pi64, pi32 = P(d), P(i64), P(i32)

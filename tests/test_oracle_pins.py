@@ -383,17 +383,23 @@ def test_refinement_pass_indices_and_monotonicity():
     p = synth.tiny_problem(1, hopf_n=1)
     grid = oracle.hopf_grid(1)
     P0 = oracle.params_from_problem(p, nn_mode="brute")
-    P1 = oracle.params_from_problem(p, nn_mode="brute", refine_top_k=2, refine_K=1,
+    P1 = oracle.params_from_problem(p, nn_mode="brute", refine_top_k=4, refine_K=1,
                                     refine_delta_r=math.radians(5))
     a = oracle.register(p.X, p.Y, grid, P0)
     b = oracle.register(p.X, p.Y, grid, P1)
-    assert len(b.V) == len(grid) + 2 * 27
+    assert len(b.V) == len(grid) + 4 * 27
     np.testing.assert_array_equal(a.V, b.V[: len(grid)])
     assert b.cost <= a.cost
-    # the centre sample of each local box is its coarse centre
-    order = sorted(np.flatnonzero(np.isfinite(a.costs)), key=lambda r: (a.costs[r], r))[:2]
+    # the centre sample of each local box (zero Euler angles: the centre
+    # rotation itself) has the outputs of the c-th best coarse candidate by
+    # (cost, index); the four candidates differ, so a box around the wrong
+    # candidate shows
+    order = sorted(np.flatnonzero(np.isfinite(a.costs)), key=lambda r: (a.costs[r], r))[:4]
+    outs = [(tuple(a.k[r]), a.V[r], a.M[r], a.costs[r]) for r in order]
+    assert len(set(outs)) == len(outs)
     for c, r in enumerate(order):
-        assert b.V[len(grid) + c * 27 + 13] == a.V[r]
+        f = len(grid) + c * 27 + 13
+        assert (tuple(b.k[f]), b.V[f], b.M[f], b.costs[f]) == outs[c], c
 
 
 def test_inlier_threshold_is_strict():
@@ -403,6 +409,18 @@ def test_inlier_threshold_is_strict():
     Y = np.array([[0.25, 0.0, 0.0], [5.0, 5.0, 5.0]])
     assert oracle.inliers(X[:1], Y, np.eye(3), np.zeros(3), 0.25)[0] == 0
     assert oracle.inliers(X[:1], Y, np.eye(3), np.zeros(3), 0.25 + 2**-20)[0] == 1
+
+
+def test_exhaustive_inlier_threshold_is_strict():
+    # Algorithm 1's count and the inlier metric take the same strict reading:
+    # at the one lattice translation t = 0, the source point lies exactly
+    # epsilon from its target (dyadic values, exact distance)
+    X = np.zeros((1, 3))
+    Y = np.array([[0.25, 0.0, 0.0], [5.0, 5.0, 5.0]])
+    for eps, n_in in ((0.25, 0), (0.25 + 2**-20, 1)):
+        P = oracle.make_params(metric="inlier", epsilon=eps, delta_t=0.25, t_half=(0.0, 0.0, 0.0))
+        cost, cnt, best, _ = oracle.exhaustive(X, Y, np.eye(3)[None], P)
+        assert cnt.shape == (1, 1) and cnt[0, 0] == n_in and cost[0, 0] == 1 - n_in
 
 
 def test_q_filter_keeps_equality():
