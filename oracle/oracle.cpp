@@ -30,7 +30,11 @@
 //
 // Parity status per function (what pins it, see tests/test_oracle_pins.py):
 //   healpix / hopf grid        pinned: HEALPix base layout (N_side = 1), ring
-//                              structure, fiber structure of the Hopf map
+//                              structure, fiber structure of the Hopf map;
+//                              the phase of the fiber samples (the half step
+//                              in psi_k = 2 pi (k + 1/2) / 6n) is a reading
+//                              no external fact fixes: parity unpinned for
+//                              that phase alone
 //   euler box grid             pinned: closed form for single-axis boxes
 //   lattice box                pinned: closed form
 //   vote (mode)                pinned: brute force over every lattice cell
@@ -48,6 +52,8 @@
 //                              the planted pose)
 //   register (Algorithm 2)     pinned: theorem special case, exhaustive
 //                              search (Algorithm 1) on tiny inputs
+// tests/test_oracle_mutations.py plants plausible mistakes in copies of this
+// file and checks that the pins catch every one.
 
 #include <algorithm>
 #include <cmath>
