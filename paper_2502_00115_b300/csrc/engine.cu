@@ -32,6 +32,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "bounds.h"
 #include "dses.h"
 #include "exchange.h"
 #include "kernels.cuh"
@@ -255,38 +256,12 @@ const float* hopf_grid(dses_ctx* c, int n) {
   return p;
 }
 
-// Largest number of target points in any 2x2x2 block of cells of side
-// delta * 1.001: every half-open cube of side delta (and its FP32 image) lies
-// in one such block, so N * capY bounds every vote-histogram counter.
+// Bound on the target points in any cube of side delta (bounds.h), cached per
+// delta: N times it bounds every vote-histogram counter.
 int cap_points_in_cube(dses_target* T, float delta) {
   auto it = T->capY.find(fbits(delta));
   if (it != T->capY.end()) return it->second;
-  const double cs = (double)delta * 1.001;
-  std::unordered_map<uint64_t, int> cnt;
-  cnt.reserve((size_t)T->m * 2);
-  auto key = [](int64_t a, int64_t b, int64_t c) {
-    return ((uint64_t)(a + (1 << 20)) << 42) | ((uint64_t)(b + (1 << 20)) << 21) | (uint64_t)(c + (1 << 20));
-  };
-  std::vector<int64_t> cell((size_t)T->m * 3);
-  for (int j = 0; j < T->m; ++j) {
-    for (int a = 0; a < 3; ++a) cell[3 * j + a] = (int64_t)std::floor((T->host[3 * j + a] - T->bbmin[a]) / cs);
-    cnt[key(cell[3 * j], cell[3 * j + 1], cell[3 * j + 2])]++;
-  }
-  int best = 0;
-  for (int j = 0; j < T->m; ++j)
-    for (int dx = 0; dx < 2; ++dx)
-      for (int dy = 0; dy < 2; ++dy)
-        for (int dz = 0; dz < 2; ++dz) {
-          const int64_t bx = cell[3 * j] - dx, by = cell[3 * j + 1] - dy, bz = cell[3 * j + 2] - dz;
-          int s = 0;
-          for (int ex = 0; ex < 2; ++ex)
-            for (int ey = 0; ey < 2; ++ey)
-              for (int ez = 0; ez < 2; ++ez) {
-                auto f = cnt.find(key(bx + ex, by + ey, bz + ez));
-                if (f != cnt.end()) s += f->second;
-              }
-          best = std::max(best, s);
-        }
+  const int best = points_in_cube_bound(T->host.data(), (int64_t)T->m, T->bbmin, delta);
   T->capY[fbits(delta)] = best;
   return best;
 }

@@ -33,7 +33,7 @@ def _rank(rank, world, port, out):
 def test_two_gloo_ranks_take_the_slowest_rank():
     world = 2
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.start_processes(_rank, args=(world, port, out), nprocs=world, start_method="spawn", join=True)
     for r in range(world):
