@@ -748,6 +748,11 @@ def test_invalid_arguments_leave_the_context_usable(ctx):
     st, _ = capi.dses_register(ctx.h, ctx.problem(t, p.X, capi.hopf_grid(1), small_cap))
     assert st == capi.DSES_ERR_INVALID_ARG
     assert capi.dses_set_option(ctx.h, "no_such_option", 1) == capi.DSES_ERR_INVALID_ARG
+    # empty clouds are refused, not registered
+    st, _ = capi.dses_register(ctx.h, ctx.problem(t, p.X[:0], capi.hopf_grid(1), gpu_params(p)))
+    assert st == capi.DSES_ERR_INVALID_ARG
+    with pytest.raises(capi.DsesError):
+        ctx.create_target(p.Y[:0], grid_cap=2 * p.tau)
     r = ctx.register(ctx.problem(t, p.X, capi.hopf_grid(1), gpu_params(p)))
     assert r.status == 0
     ctx.destroy_target(t)
