@@ -1223,9 +1223,17 @@ __global__ void __launch_bounds__(kPassThreads, 1) vote_kernel(PassLaunch L) {
 // One warp per rotation: inlier count (Eq. 3) at t* and, on the fused path,
 // the robust cost from the distance grid and the argmin key.
 constexpr int kCountPts = 2;  // source points per lane and iteration of count_kernel
+constexpr int kCountThreads = 256;
+// Per warp: queries the distance-grid bounds leave undecided, searched 32 at a
+// time (one per lane) instead of by the few lanes that hold them. Up to 31
+// wait between iterations and an iteration adds up to 32 kCountPts.
+constexpr int kCountQueue = 32 + 32 * kCountPts;
 
-__global__ void __launch_bounds__(256) count_kernel(PassLaunch L) {
+__global__ void __launch_bounds__(kCountThreads) count_kernel(PassLaunch L) {
+  __shared__ float4 s_queue[kCountThreads / 32][kCountQueue];
   const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  float4* queue = s_queue[threadIdx.x >> 5];
   const int warps = (gridDim.x * blockDim.x) >> 5;
   const int total = L.rot_prefix[L.n_probs];
   for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < total; g += warps) {
@@ -1248,13 +1256,15 @@ __global__ void __launch_bounds__(256) count_kernel(PassLaunch L) {
     // kCountPts source points per lane and iteration: all their distance-grid
     // loads are in flight together (the kernel waits on L2 latency)
     const float e_far = d.eps + d.grid_err, e_near = d.eps - d.grid_err;
-    for (int i = lane; i < d.N; i += 32 * kCountPts) {
+    int nq = 0;  // queued undecided queries (the same in every lane)
+    for (int i0 = 0; i0 < d.N; i0 += 32 * kCountPts) {  // the same trip count in every lane
+      const int i = i0 + lane;
       float qx[kCountPts], qy[kCountPts], qz[kCountPts], dg[kCountPts];
       bool valid[kCountPts], far[kCountPts], near[kCountPts];
 #pragma unroll
       for (int k = 0; k < kCountPts; ++k) {
         valid[k] = i + 32 * k < d.N;
-        const size_t ik = (size_t)(valid[k] ? i + 32 * k : i);
+        const size_t ik = (size_t)(valid[k] ? i + 32 * k : i0);
         const float x = __ldg(d.X + 3 * ik), y = __ldg(d.X + 3 * ik + 1), z = __ldg(d.X + 3 * ik + 2);
         qx[k] = fmaf(R[0], x, fmaf(R[1], y, R[2] * z)) + tx;
         qy[k] = fmaf(R[3], x, fmaf(R[4], y, R[5] * z)) + ty;
@@ -1268,11 +1278,26 @@ __global__ void __launch_bounds__(256) count_kernel(PassLaunch L) {
         dg[k] = grid_lookup_decide(d, qx[k], qy[k], qz[k], e_far, e_near, &far[k], &near[k]);
 #pragma unroll
       for (int k = 0; k < kCountPts; ++k) {
-        if (!valid[k]) continue;
-        cnt += (far[k] ? false : (near[k] ? true : has_inlier(d, qx[k], qy[k], qz[k]))) ? 1 : 0;
-        if (grid_cost) csum += robust_rho(d.metric, dg[k], d.eps, d.tau, d.huber_h, d.p_exp);
+        cnt += (valid[k] && !far[k] && near[k]) ? 1 : 0;
+        const bool undecided = valid[k] && !far[k] && !near[k];
+        const uint32_t m = __ballot_sync(0xffffffffu, undecided);
+        if (undecided) queue[nq + __popc(m & lt)] = make_float4(qx[k], qy[k], qz[k], 0.f);
+        nq += __popc(m);
+        if (valid[k] && grid_cost) csum += robust_rho(d.metric, dg[k], d.eps, d.tau, d.huber_h, d.p_exp);
       }
+      __syncwarp();
+      while (nq >= 32) {  // the exact cell search, every lane on a queued query
+        nq -= 32;
+        const float4 q = queue[nq + lane];
+        cnt += has_inlier(d, q.x, q.y, q.z) ? 1 : 0;
+      }
+      __syncwarp();  // queue reads done before the next pushes
     }
+    if (lane < nq) {
+      const float4 q = queue[lane];
+      cnt += has_inlier(d, q.x, q.y, q.z) ? 1 : 0;
+    }
+    __syncwarp();  // before the next rotation's pushes
 #pragma unroll
     for (int k = 16; k > 0; k >>= 1) {
       cnt += __shfl_xor_sync(0xffffffffu, cnt, k);
@@ -1348,7 +1373,7 @@ cudaError_t launch_vote(const PassLaunch& L, int points_per_thread, int sparse, 
 cudaError_t launch_count(const PassLaunch& L, int total_rot, cudaStream_t s) {
   const int blocks = (int)std::min<long long>(((long long)total_rot * 32 + 255) / 256, 148LL * 16);
   g_launches.fetch_add(1, std::memory_order_relaxed);
-  count_kernel<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(L);
+  count_kernel<<<blocks > 0 ? blocks : 1, kCountThreads, 0, s>>>(L);
   return cudaGetLastError();
 }
 
